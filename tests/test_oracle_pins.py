@@ -1,0 +1,516 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage or theory it relies on.  They are chosen so
+that a plausible slip anywhere in the oracle -- a wrong weight or sign, a
+dropped term, a transposed index, a force applied to the wrong particle or
+component -- fails at least one of them.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import lbinputs
+from oracle import analysis as oan
+from oracle import ref
+
+CS2 = 1.0 / 3.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- lattice
+def test_lattice_isotropy():
+    """D3Q19 (Sec. II): weights sum to 1; second and fourth moments are
+    isotropic with c_s^2 = 1/3 (textbook lattice conditions)."""
+    c, w, opp = ref.lattice()
+    c = c.astype(np.float64)
+    assert abs(w.sum() - 1.0) < 1e-15
+    M2 = np.einsum("i,ia,ib->ab", w, c, c)
+    assert np.allclose(M2, CS2 * np.eye(3), atol=1e-15)
+    M4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    d = np.eye(3)
+    iso = CS2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    assert np.allclose(M4, iso, atol=1e-15)
+    for i in range(19):
+        assert np.all(c[opp[i]] == -c[i])
+    assert sorted(map(tuple, c.astype(int))) == sorted(
+        {v for v in itertools.product((-1, 0, 1), repeat=3) if sum(map(abs, v)) <= 2})
+
+
+def _feq_hermite(rho, u, c, w):
+    """Third-order Hermite expansion of the Maxwellian on the lattice built
+    from the tensor Hermite polynomials H0..H3 (an independent construction
+    of Eq. Equil)."""
+    c = c.astype(np.float64)
+    d = np.eye(3)
+    out = np.zeros(19)
+    for i in range(19):
+        ci = c[i]
+        H1 = ci
+        H2 = np.outer(ci, ci) - CS2 * d
+        H3 = np.einsum("a,b,c->abc", ci, ci, ci) - CS2 * (
+            np.einsum("a,bc->abc", ci, d) + np.einsum("b,ac->abc", ci, d) + np.einsum("c,ab->abc", ci, d))
+        a1 = u
+        a2 = np.outer(u, u)
+        a3 = np.einsum("a,b,c->abc", u, u, u)
+        out[i] = w[i] * rho * (1.0 + np.dot(H1, a1) / CS2 + np.sum(H2 * a2) / (2 * CS2 ** 2)
+                               + np.sum(H3 * a3) / (6 * CS2 ** 3))
+    return out
+
+
+def test_feq_is_third_order_hermite():
+    c, w, _ = ref.lattice()
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        rho = 0.2 + rng.random()
+        u = 0.2 * (rng.random(3) - 0.5)
+        assert np.allclose(ref.feq(rho, u), _feq_hermite(rho, u, c, w), rtol=0, atol=1e-15)
+
+
+def test_feq_moments():
+    """Mass and momentum of Eq. Equil are exact (the cubic terms cancel in the
+    first moment because the D3Q19 fourth moment is isotropic); the second
+    moment is rho (c_s^2 I + u u)."""
+    c, w, _ = ref.lattice()
+    c = c.astype(np.float64)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho = 0.1 + rng.random()
+        u = 0.3 * (rng.random(3) - 0.5)
+        f = ref.feq(rho, u)
+        assert abs(f.sum() - rho) < 1e-15
+        assert np.allclose(f @ c, rho * u, atol=1e-16)
+        assert np.allclose(np.einsum("i,ia,ib->ab", f, c, c), rho * (CS2 * np.eye(3) + np.outer(u, u)), atol=1e-15)
+
+
+def test_splitmix64_reference_vector():
+    vals = [int(l) for l in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt")) if l.strip() and not l.startswith("#")]
+    assert [ref.splitmix64(1234567, k) for k in range(5)] == vals
+    u = [ref.unit(1234567, k) for k in range(5)]
+    assert u == [(v >> 11) / 2.0 ** 53 for v in vals]
+
+
+# ----------------------------------------------------------- conservation
+def _total_momentum(o):
+    ob = o.observe()
+    return ob["mom_fluid"] + ob["mom_part"]
+
+
+def test_mass_conserved_without_particles():
+    """BGK collision and periodic streaming conserve each component's mass
+    (Eq. eq:boltz; Sigma_i f^eq = rho)."""
+    shape = (12, 10, 8)
+    o = ref.Oracle(nx=12, ny=10, nz=8, n_particles=0, g_br=0.2, tau=(1.0, 0.8))
+    o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=2))
+    m0 = o.observe()["mass"]
+    o.step(60)
+    m1 = o.observe()["mass"]
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-13)
+    # and no net momentum appears from the pairwise Shan-Chen force
+    assert np.all(np.abs(o.observe()["mom_fluid"]) < 1e-12)
+
+
+def test_mass_conserved_static_particles():
+    """Bounce-back returns every population to the fluid (Eq. eqn_bounce-back):
+    resting, fixed spheres conserve each component's mass exactly."""
+    shape = (16, 16, 16)
+    P = lbinputs.spheres(shape, 3.0, 3, seed=5, min_gap=1.0)
+    o = ref.Oracle(nx=16, ny=16, nz=16, n_particles=3, radius=3.0, g_br=0.12, color=0.03,
+                   fixed_particles=1)
+    o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=3), particles=P)
+    m0 = o.observe()["mass"]
+    o.step(40)
+    m1 = o.observe()["mass"]
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-13)
+
+
+@pytest.mark.parametrize("vel_mode", [0, 1])
+def test_total_momentum_conserved_with_moving_particles(vel_mode):
+    """Fluid + particle momentum is conserved exactly when every particle
+    force carries the sign that balances the fluid's change: momentum
+    exchange (Eq. eqn_ladd_bewegtewand), cover / uncover
+    (Eq. eqn_ladd_vernichtenunderzeugen), the shell Shan-Chen force
+    (Eq. eqn_shan_chen_particle) and the pairwise MD forces."""
+    shape = (20, 18, 16)
+    P = lbinputs.spheres(shape, 3.2, 4, seed=11, min_gap=0.3, vmax=0.04, wmax=0.02)
+    o = ref.Oracle(nx=20, ny=18, nz=16, n_particles=4, radius=3.2, g_br=0.15, color=0.04,
+                   particle_density=3.0, vel_mode=vel_mode, mass_corr_c0=5.0)
+    o.set_colors(np.array([0.04, -0.03, 0.0, 0.05]))
+    o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=12), particles=P)
+    p0 = _total_momentum(o)
+    scale = o.observe()["mass"].sum() * 0.04
+    o.step(60)
+    ob = o.observe()
+    assert ob["n_cover"] > 0 and ob["n_uncover"] > 0
+    p1 = _total_momentum(o)
+    assert np.all(np.abs(p1 - p0) < 1e-11 * scale)
+
+
+def test_momentum_balance_detects_wrong_sign():
+    """Control for the test above: the particle momentum alone changes, so
+    conservation is not trivially satisfied."""
+    shape = (20, 18, 16)
+    P = lbinputs.spheres(shape, 3.2, 4, seed=11, min_gap=0.3, vmax=0.04, wmax=0.02)
+    o = ref.Oracle(nx=20, ny=18, nz=16, n_particles=4, radius=3.2, g_br=0.15, color=0.04,
+                   particle_density=3.0)
+    o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=12), particles=P)
+    mp0 = o.observe()["mom_part"].copy()
+    o.step(20)
+    mp1 = o.observe()["mom_part"]
+    assert np.max(np.abs(mp1 - mp0)) > 1e-3
+
+
+# -------------------------------------------------- Shan-Chen force stencil
+def _wave_growth(g, weights, tau, steps=3000, rho_bar=0.7, n=32):
+    """Amplitude ratio of a small antisymmetric composition wave."""
+    x = np.arange(n)
+    eps = 1e-4
+    dr = eps * np.sin(2 * np.pi * x / n)
+    rho = np.stack([rho_bar + dr, rho_bar - dr])
+    o = ref.Oracle(nx=n, ny=1, nz=1, n_particles=0, g_br=g, sc_weight=weights, tau=(tau, tau))
+    o.init_fields(rho)
+    o.step(steps)
+    r = o.rho()
+    phi = r[0] - r[1]
+    amp = 2 * abs(np.sum(phi * np.sin(2 * np.pi * x / n))) / n
+    return amp / (2 * eps)
+
+
+@pytest.mark.parametrize("weights,A,tau", [((1.0, 1.0), 10.0, 1.0), ((2.0, 1.0), 12.0, 1.0),
+                                           ((2.0, 1.0), 12.0, 0.8)])
+def test_spinodal_threshold(weights, A, tau):
+    """Linear stability of the scheme of Sec. II about a 50:50 mixture.  The
+    velocity shift tau F / rho makes the composition flux of a component
+    tau F^c - c_s^2 (tau - 1/2) grad rho^c, and linearising
+    Eq. eqn_shan-chen-F with Eq. eqn_ref_dens gives F^r = g A Psi Psi' grad
+    (rho^r - rho_bar), A = sum_i W_i c_ix^2, Psi' = exp(-rho/rho0).  A long
+    wave therefore grows iff tau g A Psi Psi' > c_s^2 (tau - 1/2).  Bracketing
+    the threshold at +-5% pins the force sign, the Psi form, the split of the
+    link weights between axis and diagonal links, and the velocity shift
+    (the tau dependence).  The long-wave threshold lies 1% above the formula
+    at this wavelength (k = 2 pi / 32), inside the bracket."""
+    rho = 0.7
+    pp = (1.0 - np.exp(-rho)) * np.exp(-rho)
+    gc = CS2 * (tau - 0.5) / (tau * A * pp)
+    assert _wave_growth(1.05 * gc, weights, tau) > 1.0
+    assert _wave_growth(0.95 * gc, weights, tau) < 1.0
+
+
+# ------------------------------------------------------------ bounce-back
+def test_poiseuille_magic_tau():
+    """Plane Poiseuille flow between static bounce-back walls (Eq.
+    eqn_bounce-back).  The BGK solution is a parabola with curvature -g/nu,
+    nu = c_s^2 (tau - 1/2) (Sec. II), and for (tau - 1/2)^2 = 3/16 it
+    vanishes exactly half-way between the last fluid and the first wall node
+    (He et al., J. Stat. Phys. 87, 115 (1997); Ginzburg & d'Humieres,
+    PRE 68, 066614 (2003))."""
+    nz = 18
+    tau = 0.5 + np.sqrt(3.0 / 16.0)
+    g = 1e-6
+    walls = np.full((nz, 1, 1), -1, np.int32)
+    walls[0] = walls[nz - 1] = -2
+    o = ref.Oracle(nx=1, ny=1, nz=nz, n_particles=0, g_br=0.0, tau=(tau, tau),
+                   body_force=(g, 0.0, 0.0))
+    rho = np.full((2, nz), 0.5)
+    o.init_fields(rho, walls=walls.reshape(-1))
+    o.step(12000)
+    u = o.velocity()[0].reshape(nz)
+    z = np.arange(1, nz - 1, dtype=np.float64)
+    uf = u[1:nz - 1] + 0.5 * g  # physical velocity includes half the force per unit mass
+    coef = np.polyfit(z, uf, 2)
+    nu = CS2 * (tau - 0.5)
+    assert abs(coef[0] * 2 / (-g / nu) - 1.0) < 1e-6
+    roots = np.sort(np.roots(coef).real)
+    assert abs(roots[0] - 0.5) < 1e-5 and abs(roots[1] - (nz - 1.5)) < 1e-5
+    resid = uf - np.polyval(coef, z)
+    assert np.max(np.abs(resid)) < 1e-9 * np.max(uf)
+
+
+def _comoving_error(U):
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (7.3, 8.1, 7.6)
+    P[0, 3:6] = U
+    o = ref.Oracle(nx=16, ny=16, nz=16, n_particles=1, radius=4.0, g_br=0.0,
+                   fixed_particles=1)
+    u = np.tile(np.asarray(U, float).reshape(3, 1), (1, 16 ** 3))
+    o.init_fields(np.full((2, 16 ** 3), 0.6), u=u, particles=P)
+    o.step(1)
+    st = o.get_state()
+    fluid = st["owner"] == -1
+    vel = o.velocity()[:, fluid]
+    mass_err = np.max(np.abs(st["f"].sum(axis=(0, 1))[fluid] - 1.2))
+    return np.max(np.abs(vel - np.asarray(U, float)[:, None])), mass_err
+
+
+def test_moving_wall_term_galilean():
+    """A sphere moving with the surrounding uniform flow leaves it
+    undisturbed up to the cubic terms of Eq. Equil: the moving-wall term
+    6 zeta_j rho u_s.c_j of Eq. eqn_ladd_bewegtewand cancels the odd linear
+    part of f^eq_j - f^eq_opp(j) exactly, so the remaining disturbance scales
+    as |U|^3.  (The literal uniform 1/6 would leave an O(|U|) error on the
+    axis links.)"""
+    U = np.array([0.02, -0.015, 0.01])
+    e1, m1 = _comoving_error(U)
+    e2, m2 = _comoving_error(U / 2)
+    assert 7.0 < e1 / e2 < 9.0 and 7.0 < m1 / m2 < 9.0
+    e3, m3 = _comoving_error(U / 20)
+    assert e3 < 1e-9 and m3 < 2e-9
+
+
+def test_static_sphere_in_fluid_at_rest():
+    """No flow appears around a resting sphere in a resting fluid, and the
+    bounce-back force on a sphere centred on a node is zero by symmetry."""
+    o = ref.Oracle(nx=14, ny=14, nz=14, n_particles=1, radius=3.5, g_br=0.0)
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (7.0, 7.0, 7.0)
+    o.init_fields(np.full((2, 14 ** 3), 0.6), particles=P)
+    o.step(5)
+    assert np.max(np.abs(o.velocity())) < 1e-15
+    F, T = o.particle_forces()
+    assert np.max(np.abs(F)) < 1e-12 and np.max(np.abs(T)) < 1e-12
+
+
+def test_drag_and_torque_oppose_motion():
+    """A prescribed translation or rotation of a sphere in fluid at rest is
+    resisted: F.U < 0 and T.omega < 0 (Eqs. eqn_bounce-back-force and the
+    torque D with r from the centre to the reflection site)."""
+    for U, W in (((0.02, 0, 0), (0, 0, 0)), ((0, 0, 0), (0, 0, 0.01)), ((0, 0.01, 0), (0.005, 0, 0))):
+        P = np.zeros((1, 9))
+        P[0, 0:3] = (8.2, 7.9, 8.4)
+        P[0, 3:6] = U
+        P[0, 6:9] = W
+        o = ref.Oracle(nx=16, ny=16, nz=16, n_particles=1, radius=4.0, g_br=0.0,
+                       fixed_particles=1)
+        o.init_fields(np.full((2, 16 ** 3), 0.6), particles=P)
+        o.step(30)
+        F, T = o.particle_forces()
+        if np.any(U):
+            assert np.dot(F[0], U) < 0
+        if np.any(W):
+            assert np.dot(T[0], W) < 0
+
+
+# -------------------------------------------------------- cover / uncover
+def test_refill_density_and_momentum():
+    """Uncovered nodes are refilled with rho_new^c = mean rho^c over the
+    neighbours that were fluid (Eq. eqn_rho_neu) and f = f^eq(rho_new, u_s)
+    so that sum_i f = rho_new and sum_i f c = rho_new u_s, u_s = U + w x r;
+    covered nodes lose all fluid.  Checked by brute force on the node lists."""
+    shape = (14, 13, 12)
+    nx, ny, nz = shape
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (6.3, 6.6, 5.8)
+    P[0, 3:6] = (0.3, -0.2, 0.25)   # large, to move across nodes in one MD step
+    P[0, 6:9] = (0.02, 0.01, -0.03)
+    o = ref.Oracle(nx=nx, ny=ny, nz=nz, n_particles=1, radius=3.4, g_br=0.1,
+                   particle_density=50.0)
+    o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=21), particles=P)
+    o.step(1)                   # moves the particle: X += U
+    before = o.get_state()
+    rho_b = o.rho()
+    o.debug_remap()
+    after = o.get_state()
+    c, w, _ = ref.lattice()
+    X = before["particles"][0, 0:3]
+    U = before["particles"][0, 3:6]
+    W = before["particles"][0, 6:9]
+    L = np.array(shape, float)
+    unc = np.nonzero((before["owner"] == 0) & (after["owner"] == -1))[0]
+    cov = np.nonzero((before["owner"] == -1) & (after["owner"] == 0))[0]
+    assert len(unc) > 0 and len(cov) > 0
+    for n in unc:
+        x, y, z = n % nx, (n // nx) % ny, n // (nx * ny)
+        r = np.array([x, y, z], float) - X
+        r -= L * np.round(r / L)
+        us = U + np.cross(W, r)
+        for comp in range(2):
+            vals = []
+            for i in range(1, 19):
+                m = ((x + c[i, 0]) % nx) + nx * (((y + c[i, 1]) % ny) + ny * ((z + c[i, 2]) % nz))
+                if before["owner"][m] == -1:
+                    vals.append(rho_b[comp, m])
+            f = after["f"][comp, :, n]
+            assert abs(f.sum() - np.mean(vals)) < 1e-14
+            assert np.allclose(f @ c, np.mean(vals) * us, atol=1e-14)
+    for n in cov:
+        assert np.all(after["f"][:, :, n] == 0.0)
+
+
+def test_mass_correction_direction():
+    """Eq. masscorr: when the fluid has gained mass the refill is scaled
+    down, when it has lost mass scaled up, linearly in C0."""
+    shape = (14, 13, 12)
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (6.3, 6.6, 5.8)
+    P[0, 3:6] = (0.3, -0.2, 0.25)
+    res = {}
+    for c0, dm in ((0.0, 0.0), (20.0, +0.05), (20.0, -0.05), (40.0, -0.05)):
+        o = ref.Oracle(nx=14, ny=13, nz=12, n_particles=1, radius=3.4, g_br=0.1,
+                       particle_density=50.0, mass_corr_c0=c0)
+        o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=21), particles=P)
+        o.step(1)
+        st = o.get_state()
+        mass = o.observe()["mass"]
+        st["meta"][1] = mass[0] - dm * 14 * 13 * 12   # pretend the initial mass differed
+        st["meta"][2] = mass[1] - dm * 14 * 13 * 12
+        o.set_state(st)
+        unc_before = st["owner"] == 0
+        o.debug_remap()
+        after = o.get_state()
+        unc = np.nonzero(unc_before & (after["owner"] == -1))[0]
+        res[(c0, dm)] = after["f"][0][:, unc].sum(axis=0)
+    base = res[(0.0, 0.0)]
+    up = res[(20.0, +0.05)] / base
+    down = res[(20.0, -0.05)] / base
+    down2 = res[(40.0, -0.05)] / base
+    assert np.all(up < 1.0) and np.all(down > 1.0)
+    assert np.allclose(down2 - 1.0, 2 * (down - 1.0), rtol=1e-12)
+
+
+# ------------------------------------------------------ colour and symmetry
+def _interface_particle(color, swap=False):
+    n = 16
+    rho = lbinputs.lamellae((n, n, n), axis=2, rho_major=0.7, rho_minor=0.05)
+    if swap:
+        rho = rho[::-1].copy()
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (7.5, 7.5, n / 2 - 0.5)
+    o = ref.Oracle(nx=n, ny=n, nz=n, n_particles=1, radius=3.5, g_br=0.2, color=color,
+                   fixed_particles=1)
+    o.init_fields(rho, particles=P)
+    o.step(1)
+    return o.particle_forces()[0][0]
+
+
+def test_colour_sign_and_red_blue_symmetry():
+    """Sec. IV: positive colour adds red virtual fluid, which pulls the
+    particle into the red phase (here z < n/2); negative colour into the
+    blue.  With zero colour the mirror-symmetric set-up gives no normal
+    force (theta = 90 deg).  Swapping red and blue together with the sign of
+    the colour mirrors the force."""
+    f0 = _interface_particle(0.0)
+    assert abs(f0[2]) < 1e-13
+    fp = _interface_particle(+0.05)
+    fm = _interface_particle(-0.05)
+    assert fp[2] < -1e-6 and fm[2] > 1e-6
+    fsw = _interface_particle(-0.05, swap=True)
+    assert abs(fsw[2] - fp[2]) < 1e-12 * max(1.0, abs(fp[2])) + 1e-14
+
+
+def test_virtual_fluid_removes_density_halo():
+    """Fig. 1: with the shell filled by virtual fluid the total density next
+    to a particle stays at the bulk value; with an empty particle (the
+    original algorithm) a layer of increased density forms."""
+    n = 20
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (10.0, 10.0, 10.0)
+    out = {}
+    for vf in (1, 0):
+        o = ref.Oracle(nx=n, ny=n, nz=n, n_particles=1, radius=4.0, g_br=0.08,
+                       virtual_fluid=vf, fixed_particles=1)
+        o.init_fields(np.full((2, n ** 3), 0.35), particles=P)
+        o.step(300)
+        r = o.rho().sum(axis=0).reshape(n, n, n)
+        owner = o.get_state()["owner"].reshape(n, n, n)
+        zz, yy, xx = np.indices((n, n, n))
+        d = np.sqrt((xx - 10.0) ** 2 + (yy - 10.0) ** 2 + (zz - 10.0) ** 2)
+        near = (owner == -1) & (d < 5.5)
+        far = (owner == -1) & (d > 8.5)
+        out[vf] = r[near].mean() / r[far].mean() - 1.0
+    assert abs(out[1]) < 0.005
+    assert out[0] > 3 * abs(out[1]) and out[0] > 0.005
+
+
+# ---------------------------------------------------------------- MD forces
+def test_hertz_force_is_minus_gradient():
+    """Eq. eq:hertz: the contact force is -dV/dr of V = K (2R - r)^{5/2}."""
+    R, K = 5.0, 1.7
+    for d in (9.2, 9.7, 9.95):
+        Fp = ref.pair_force((d, 0, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), nx=64, ny=64, nz=64,
+                            radius=R, k_hertz=K, lub_cut=-1.0)
+        V = lambda r: K * (2 * R - r) ** 2.5
+        h = 1e-6
+        dVdr = (V(d + h) - V(d - h)) / (2 * h)
+        assert abs(Fp[0] - (-dVdr)) < 1e-6 * abs(dVdr)
+        assert Fp[1] == 0 and Fp[2] == 0
+    assert np.all(ref.pair_force((10.01, 0, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), nx=64, ny=64, nz=64,
+                                 radius=R, lub_cut=-1.0) == 0)
+
+
+def test_lubrication_properties():
+    """Eq. eqn_ladd_lubrikation: acts only below the cut-off gap, vanishes
+    continuously there, is clamped below h_min, opposes the relative normal
+    velocity, and is linear in it; the minimum image is used across the
+    periodic boundary."""
+    R = 5.0
+    kw = dict(nx=64, ny=64, nz=64, radius=R, k_hertz=0.0)
+    approach = ((0, 0, 0), (-0.01, 0, 0))   # p at +x moves toward q
+    f = lambda d, U=approach: ref.pair_force((d, 0, 0), (0, 0, 0), U[1], U[0], **kw)[0]
+    assert f(10.0 + 0.7) == 0.0
+    assert abs(f(10.0 + 2.0 / 3.0 - 1e-9)) < 1e-9
+    assert f(10.3) > 0                       # repulsive when approaching
+    assert f(10.05) == f(10.1) == f(10.0)    # clamped at h_min
+    assert abs(f(10.3, ((0, 0, 0), (-0.02, 0, 0))) - 2 * f(10.3)) < 1e-15
+    sep = ((0, 0, 0), (0.01, 0, 0))
+    assert f(10.3, sep) == -f(10.3)
+    tang = ((0, 0, 0), (0, 0.01, 0))
+    assert f(10.3, tang) == 0.0
+    # across the periodic boundary: p at x = 63, q at x = 9.7 -> gap 0.7 - 1 = ...
+    Fw = ref.pair_force((63.0, 0, 0), (9.2, 0, 0), (0.01, 0, 0), (0, 0, 0), **kw)
+    assert Fw[0] < 0                          # p sits at -1 relative to q, approaching: pushed to -x
+
+
+# ------------------------------------------------------------ seeded init
+def test_seeded_init_placement_and_noise():
+    """Random sequential addition gives non-overlapping spheres (minimum
+    image distance >= 2R) with the count from the volume fraction, and node
+    densities within rho_init +- a."""
+    o = ref.Oracle(nx=32, ny=32, nz=32, n_particles=-1, volume_fraction=0.13, radius=4.0,
+                   noise_amp=0.01)
+    assert o.np == int(np.floor(0.13 * 32 ** 3 / (4 / 3 * np.pi * 64) + 0.5))
+    o.init_from_seed(7)
+    st = o.get_state()
+    X = st["particles"][:, 0:3]
+    L = 32.0
+    for a, b in itertools.combinations(range(o.np), 2):
+        d = X[a] - X[b]
+        d -= L * np.round(d / L)
+        assert np.dot(d, d) >= 64.0 - 1e-12
+    r = o.rho()
+    fl = st["owner"] == -1
+    assert np.all(np.abs(r[:, fl] - 0.7) <= 0.01 + 1e-15)
+    assert abs(r[:, fl].mean() - 0.7) < 1e-3
+    # every node within R of a centre is solid, every other node is fluid
+    zz, yy, xx = np.indices((32, 32, 32))
+    pos = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(float)
+    inside = np.zeros(32 ** 3, bool)
+    for q in range(o.np):
+        d = pos - X[q]
+        d -= L * np.round(d / L)
+        inside |= (d ** 2).sum(1) <= 16.0
+    assert np.array_equal(inside, st["owner"] >= 0)
+
+
+# --------------------------------------------------------------- analysis
+def test_domain_size_of_sine_pattern():
+    """Eq. eq:domsize on single and mixed Fourier modes.  A product of sines
+    has all its power at |k_i| = 2 pi / lam_i, so L_i = lam_i; a sum of three
+    sines of equal amplitude puts a third of the power on each axis, so
+    <k_x^2> = (2 pi / lam_x)^2 / 3 and L_x = lam_x sqrt(3)."""
+    n = 32
+    z, y, x = np.indices((n, n, 24))
+    phi1 = np.sin(2 * np.pi * x / 8.0) * np.sin(2 * np.pi * y / 16.0) * np.sin(2 * np.pi * z / 32.0)
+    assert np.allclose(oan.domain_size(phi1), (8.0, 16.0, 32.0), atol=1e-9)
+    phi = np.sin(2 * np.pi * x / 8.0) + np.sin(2 * np.pi * y / 16.0) + np.sin(2 * np.pi * z / 32.0)
+    assert np.allclose(oan.domain_size(phi), np.sqrt(3.0) * np.array([8.0, 16.0, 32.0]), atol=1e-9)
+
+
+def test_interface_height_and_angle():
+    """Eq. eqn_contactangle_calculation with the interface at the linearly
+    interpolated zero of phi."""
+    col = np.array([1.0, 0.6, 0.2, -0.2, -0.6])
+    assert abs(oan.interface_height(col) - 2.5) < 1e-15
+    assert abs(oan.contact_angle(-2.93, 10.0) - 107.04) < 0.01
+    assert oan.contact_angle(0.0, 5.0) == 90.0
