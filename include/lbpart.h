@@ -1,0 +1,194 @@
+/*
+ * lbpart.h -- C ABI of the GB300 (sm_103a) library for the two-component
+ * Shan-Chen D3Q19 BGK lattice Boltzmann fluid with suspended spherical
+ * particles of Jansen & Harting, "From Bijels to Pickering emulsions: a
+ * lattice Boltzmann study" (arXiv:1004.4414).
+ *
+ * What one time step computes (lb_step), in the paper's order:
+ *   - particle remap: nodes a sphere newly covers lose their fluid and its
+ *     momentum to the particle; nodes it uncovers are refilled with the mean
+ *     density of their fluid neighbours at the surface velocity
+ *     (Sec. III; Sec. IV, Eqs. eqn_rho_neu, eqn_ladd_vernichtenunderzeugen,
+ *     optional Eq. masscorr);
+ *   - virtual fluid on the outer solid shell with the particle colour
+ *     (Sec. IV, the rho_new^r / rho_new^b equations);
+ *   - Shan-Chen force with Psi = rho0 (1 - exp(-rho / rho0))
+ *     (Eqs. eqn_shan-chen-F, eqn_ref_dens) and its sum on each particle
+ *     (Eq. eqn_shan_chen_particle);
+ *   - BGK collision with the cubic equilibrium at the shifted velocity
+ *     (Eqs. eq:boltz, Equil, Sec. II), streaming with moving-wall
+ *     bounce-back and momentum exchange (Eqs. eqn_bounce-back,
+ *     eqn_ladd_bewegtewand);
+ *   - particle MD with Hertz contact and lubrication, leap-frog
+ *     (Eqs. eq:hertz, eqn_ladd_lubrikation, Sec. III).
+ *
+ * Conventions
+ *   - Every call returns LB_OK (0) or a negative LB_E* code; no call aborts
+ *     or prints.  lb_strerror gives a text.
+ *   - Node index n = x + nx*(y + ny*z); populations f[c][i][n] with
+ *     c = 0 red, 1 blue and the direction order 0 rest; 1..6 = +x,-x,+y,-y,
+ *     +z,-z; 7..18 = (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),
+ *     (-1,0,-1),(+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1).
+ *   - Particles: 9 doubles each, X[3], U[3], omega[3]; particle indices are
+ *     per box, 0..n_particles-1.  owner[n] = -1 fluid, -2 static wall,
+ *     p >= 0 solid node of particle p.
+ *   - Host pointers are plain host memory (pageable or pinned); the library
+ *     copies what it needs before the call returns unless stated otherwise.
+ *   - A handle is not thread-safe; one host thread drives it at a time.
+ *   - All device work goes to the CUDA stream given to lb_create.
+ */
+#ifndef LBPART_H
+#define LBPART_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define LB_OK 0
+#define LB_EINVAL (-1)     /* invalid argument or configuration */
+#define LB_ENOMEM (-2)     /* workspace too small */
+#define LB_ECUDA (-3)      /* a CUDA runtime call failed */
+#define LB_EUNSTABLE (-4)  /* device detected a non-finite density or |u| >= 0.5 */
+#define LB_EPLACE (-5)     /* random sequential addition could not place the spheres */
+#define LB_ETIMEOUT (-6)   /* reserved: a bounded device wait gave up */
+#define LB_EOVERFLOW (-7)  /* a fixed-capacity device list overflowed */
+
+/* population storage (the collision always runs in FP32, or FP64 for LB_FP64) */
+#define LB_FP64 0      /* FP64 populations and arithmetic (parity mode) */
+#define LB_FP32 1      /* FP32 populations and arithmetic */
+#define LB_FP16_DEV 2  /* f_i (i>0) stored as FP16 deviations (f_i - zeta_i rho_ref)/zeta_i, rest population FP32 */
+#define LB_BF16_DEV 3  /* as LB_FP16_DEV with BF16 */
+
+/* One periodic box.  Densities follow the paper's symbols. */
+typedef struct {
+    int32_t nx, ny, nz;          /* lattice size, each >= 1 */
+    int32_t n_particles;         /* exact particle count; < 0: round(volume_fraction N / (4/3 pi R^3)) */
+    double tau[2];               /* BGK relaxation times tau^r, tau^b (> 1/2) */
+    double g_br;                 /* Shan-Chen coupling g_br = g_rb; g_rr = g_bb = 0 */
+    double rho0;                 /* reference density of Psi */
+    double sc_weight[2];         /* link weights of the force stencil: axis, diagonal */
+    double rho_init[2];          /* mean initial density per component */
+    double noise_amp;            /* seeded init: rho^c = rho_init^c + U(-a, a) per node */
+    double volume_fraction;      /* alpha, used when n_particles < 0 */
+    double radius;               /* sphere radius r_par (all particles) */
+    double particle_density;     /* m = rho_p 4/3 pi R^3, J = 2/5 m R^2 */
+    double color;                /* particle colour Delta rho; used when contact_angle_deg is NaN */
+    double contact_angle_deg;    /* if finite: Delta rho = (theta - 90) / 442 (fit of Fig. 4b) */
+    double k_hertz;              /* K_Hertz of Eq. eq:hertz */
+    double lub_cut;              /* lubrication below this gap */
+    double lub_min;              /* gap where lubrication is clamped */
+    double mass_corr_c0;         /* C0 of Eq. masscorr (0 = off) */
+    double body_force[3];        /* uniform acceleration of the fluid (tests; 0 in the paper's runs) */
+    int32_t vel_mode;            /* 0: Shan-Chen common velocity in f^eq, 1: each component's own velocity */
+    int32_t fixed_particles;     /* 1: particles keep X, U, omega (prescribed motion; tests) */
+    int32_t precision;           /* LB_FP64 / LB_FP32 / LB_FP16_DEV / LB_BF16_DEV, same for all boxes */
+    int32_t reserved;            /* must be 0 */
+} lb_params;
+
+/* Observables of one box (lb_observables). */
+typedef struct {
+    int64_t step;                /* time steps taken since init */
+    double mass[2];              /* sum of populations over fluid nodes, per component */
+    double mom_fluid[3];         /* sum over fluid nodes of sum_c sum_i f_i c_i */
+    double mom_part[3];          /* sum over particles of m U (0 when particles are fixed) */
+    double max_u;                /* max over fluid nodes of |j| / rho (both components) */
+    int64_t n_cover, n_uncover;  /* cover / uncover events since init */
+    int64_t n_fluid, n_solid;    /* current node counts */
+    int32_t error;               /* sticky device error (LB_OK or LB_E*) */
+    int32_t n_particles;
+} lb_obs;
+
+typedef struct lb_handle lb_handle;
+
+/* Device workspace needed for n_boxes boxes: bytes out.  LB_EINVAL on bad
+ * parameters.  The caller allocates it (e.g. torch.empty on the device) and
+ * keeps it alive until lb_destroy; the library never allocates device
+ * memory for the lattice. */
+int lb_workspace_bytes(const lb_params* boxes, int32_t n_boxes, size_t* bytes);
+
+/* Create a handle for n_boxes independent boxes stepped together (the
+ * batched sweep).  d_workspace: device pointer, 256-byte aligned, at least
+ * lb_workspace_bytes bytes.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream).  The parameters are copied.  No state is initialised
+ * until lb_init_from_seed / lb_init_fields / lb_import_state. */
+int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t bytes,
+              void* cuda_stream, lb_handle** out);
+
+/* Seeded synthetic initial state of every box (box b uses seed + b):
+ * spheres by random sequential addition (minimum-image centre distance
+ * >= 2R, at most 10^6 candidates, LB_EPLACE otherwise), node densities
+ * rho_init^c + U(-a, a), f = f^eq(rho, 0) on fluid nodes.  The random
+ * numbers come from SplitMix64 (Steele, Lea & Flood 2014): stream k of seed
+ * s is seeded with output k of SplitMix64(s); stream 0 places spheres
+ * (three draws per candidate centre), stream 1 + c gives the noise of
+ * component c at node n (its n-th output).  Synchronous. */
+int lb_init_from_seed(lb_handle* h, uint64_t seed);
+
+/* Initial state of one box from macroscopic fields (host arrays):
+ * rho[2][N], u[3][N] (NULL: fluid at rest), particles[n_particles][9],
+ * walls[N] (NULL: none; -2 marks a static wall node).  f = f^eq(rho, u) on
+ * fluid nodes; nodes within R of a centre are solid.  Synchronous. */
+int lb_init_fields(lb_handle* h, int32_t box, const double* rho, const double* u,
+                   const double* particles, const int32_t* walls);
+
+/* Advance every box by n >= 0 steps; asynchronous on the stream (CUDA-graph
+ * replays).  Returns launch errors, or the sticky device error seen by an
+ * earlier call that has completed. */
+int lb_step(lb_handle* h, int64_t n);
+
+/* Wait for the stream; return the sticky device error (LB_OK if none). */
+int lb_sync(lb_handle* h);
+
+/* Observables of one box; synchronises the stream. */
+int lb_observables(lb_handle* h, int32_t box, lb_obs* out);
+
+/* Full state of one box in canonical order (host arrays, any may be NULL):
+ * f[2][19][N] FP64 (0 on solid nodes), owner[N], particles[np][9],
+ * meta[4] = {step, initial mass red, initial mass blue, n_particles}.
+ * Synchronises the stream. */
+int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double* particles,
+                    double* meta);
+
+/* Replace the state of one box (same layout as lb_export_state; f, owner,
+ * particles and meta are required).  Synchronous. */
+int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* owner,
+                    const double* particles, const double* meta);
+
+/* Densities rho[2][N] of one box (sum of populations, 0 on solid nodes). */
+int lb_export_rho(lb_handle* h, int32_t box, double* rho);
+
+/* Per-particle colour Delta rho of one box (host array of n_particles). */
+int lb_set_particle_colors(lb_handle* h, int32_t box, const double* colors);
+
+/* Fluid-coupling force and torque on each particle of one box in the last
+ * step (momentum exchange, cover/uncover, Shan-Chen), before the MD pair
+ * forces: F[np][3], T[np][3].  Synchronises. */
+int lb_particle_forces(lb_handle* h, int32_t box, double* F, double* T);
+
+/* Number of particles and lattice nodes of a box. */
+int lb_box_info(lb_handle* h, int32_t box, int32_t* n_particles, int64_t* n_nodes);
+
+/* Block shape of the fused step kernel: ty rows of 32 nodes per CTA (4, 8
+ * or 16) and cz planes marched per CTA (>= 1).  Rebuilds the launch plan
+ * and graphs.  Used by the autotuner. */
+int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz);
+
+/* Kernel timing.  When enabled, lb_step launches the kernels one by one and
+ * brackets every launch of the fused stream-collide kernel with CUDA events
+ * on the handle's stream; lb_kernel_time returns the summed milliseconds and
+ * the launch count since the last reset and resets them.  Synchronises. */
+int lb_set_profiling(lb_handle* h, int32_t on);
+int lb_kernel_time(lb_handle* h, double* ms_fused, int64_t* launches_fused, int64_t* launches_total);
+
+/* Destroy the handle (does not free the caller's workspace). */
+void lb_destroy(lb_handle* h);
+
+const char* lb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

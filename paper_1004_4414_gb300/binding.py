@@ -1,0 +1,303 @@
+"""Thin Python binding of the C ABI in include/lbpart.h (argument marshalling
+only; every step of the method runs in the library's sm_103a kernels).
+
+PyTorch provides the device workspace (one uint8 tensor the library lays
+its arrays out in) and the CUDA stream.  The shared library must have been
+built (``paper_1004_4414_gb300.build.build()``); importing it fails loudly
+otherwise -- there is no CPU fallback.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbpart.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_EPLACE, LB_ETIMEOUT, LB_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6, -7
+LB_FP64, LB_FP32, LB_FP16_DEV, LB_BF16_DEV = 0, 1, 2, 3
+PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "fp16": LB_FP16_DEV, "bf16": LB_BF16_DEV}
+
+
+class LbParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("n_particles", C.c_int32),
+        ("tau", C.c_double * 2),
+        ("g_br", C.c_double),
+        ("rho0", C.c_double),
+        ("sc_weight", C.c_double * 2),
+        ("rho_init", C.c_double * 2),
+        ("noise_amp", C.c_double),
+        ("volume_fraction", C.c_double),
+        ("radius", C.c_double),
+        ("particle_density", C.c_double),
+        ("color", C.c_double),
+        ("contact_angle_deg", C.c_double),
+        ("k_hertz", C.c_double),
+        ("lub_cut", C.c_double),
+        ("lub_min", C.c_double),
+        ("mass_corr_c0", C.c_double),
+        ("body_force", C.c_double * 3),
+        ("vel_mode", C.c_int32),
+        ("fixed_particles", C.c_int32),
+        ("precision", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+class LbObs(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64),
+        ("mass", C.c_double * 2),
+        ("mom_fluid", C.c_double * 3),
+        ("mom_part", C.c_double * 3),
+        ("max_u", C.c_double),
+        ("n_cover", C.c_int64),
+        ("n_uncover", C.c_int64),
+        ("n_fluid", C.c_int64),
+        ("n_solid", C.c_int64),
+        ("error", C.c_int32),
+        ("n_particles", C.c_int32),
+    ]
+
+
+# Defaults follow the paper's runs: tau = 1, g_br = 0.08, rho0 = 1, R = 5,
+# particle density 1, lubrication below a gap of 2/3 clamped at 1/10.
+DEFAULTS = dict(
+    nx=32, ny=32, nz=32, n_particles=0, tau=(1.0, 1.0), g_br=0.08, rho0=1.0,
+    sc_weight=(2.0, 1.0), rho_init=(0.7, 0.7), noise_amp=0.01, volume_fraction=0.0,
+    radius=5.0, particle_density=1.0, color=0.0, contact_angle_deg=math.nan,
+    k_hertz=100.0, lub_cut=2.0 / 3.0, lub_min=0.1, mass_corr_c0=0.0,
+    body_force=(0.0, 0.0, 0.0), vel_mode=0, fixed_particles=0, precision=LB_FP32, reserved=0,
+)
+
+ABI_FUNCTIONS = (
+    "lb_workspace_bytes", "lb_create", "lb_init_from_seed", "lb_init_fields", "lb_step", "lb_sync",
+    "lb_observables", "lb_export_state", "lb_import_state", "lb_export_rho", "lb_set_particle_colors",
+    "lb_particle_forces", "lb_box_info", "lb_set_tiling", "lb_set_profiling", "lb_kernel_time",
+    "lb_destroy", "lb_strerror",
+)
+
+_lib = None
+
+
+class LbError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, strerror(code), code))
+
+
+def load_library(path=LIB_PATH):
+    """Load the shared library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: run paper_1004_4414_gb300.build.build()" % path)
+    L = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    P = C.POINTER(LbParams)
+    L.lb_workspace_bytes.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
+    L.lb_create.argtypes = [P, C.c_int32, vp, C.c_size_t, vp, C.POINTER(vp)]
+    L.lb_init_from_seed.argtypes = [vp, C.c_uint64]
+    L.lb_init_fields.argtypes = [vp, C.c_int32, dp, dp, dp, ip]
+    L.lb_step.argtypes = [vp, C.c_int64]
+    L.lb_sync.argtypes = [vp]
+    L.lb_observables.argtypes = [vp, C.c_int32, C.POINTER(LbObs)]
+    L.lb_export_state.argtypes = [vp, C.c_int32, dp, ip, dp, dp]
+    L.lb_import_state.argtypes = [vp, C.c_int32, dp, ip, dp, dp]
+    L.lb_export_rho.argtypes = [vp, C.c_int32, dp]
+    L.lb_set_particle_colors.argtypes = [vp, C.c_int32, dp]
+    L.lb_particle_forces.argtypes = [vp, C.c_int32, dp, dp]
+    L.lb_box_info.argtypes = [vp, C.c_int32, ip, C.POINTER(C.c_int64)]
+    L.lb_set_tiling.argtypes = [vp, C.c_int32, C.c_int32]
+    L.lb_set_profiling.argtypes = [vp, C.c_int32]
+    L.lb_kernel_time.argtypes = [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.lb_destroy.argtypes = [vp]
+    L.lb_destroy.restype = None
+    L.lb_strerror.argtypes = [C.c_int]
+    L.lb_strerror.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def strerror(code):
+    if _lib is None:
+        return "error"
+    return _lib.lb_strerror(code).decode()
+
+
+def _ck(rc, where):
+    if rc != LB_OK:
+        raise LbError(rc, where)
+
+
+def make_params(**kw):
+    d = dict(DEFAULTS)
+    unknown = set(kw) - set(d)
+    if unknown:
+        raise KeyError("unknown parameters: %s" % sorted(unknown))
+    d.update(kw)
+    if isinstance(d["precision"], str):
+        d["precision"] = PRECISIONS[d["precision"]]
+    p = LbParams()
+    for k, v in d.items():
+        if isinstance(v, (tuple, list)):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def workspace_bytes(boxes):
+    L = load_library()
+    arr = (LbParams * len(boxes))(*boxes)
+    n = C.c_size_t(0)
+    _ck(L.lb_workspace_bytes(arr, len(boxes), C.byref(n)), "lb_workspace_bytes")
+    return n.value
+
+
+class Simulation:
+    """A batch of periodic boxes stepped together on one GPU.
+
+    boxes: a dict of parameters (one box) or a list of dicts.
+    """
+
+    def __init__(self, boxes, device=None, stream=None):
+        import torch
+
+        L = load_library()
+        if isinstance(boxes, dict):
+            boxes = [boxes]
+        self._params = [make_params(**b) for b in boxes]
+        self.nb = len(self._params)
+        arr = (LbParams * self.nb)(*self._params)
+        n = C.c_size_t(0)
+        _ck(L.lb_workspace_bytes(arr, self.nb, C.byref(n)), "lb_workspace_bytes")
+        self.device = torch.device(device or "cuda")
+        self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws = base + (-base) % 256
+        # a stream of its own: CUDA graphs cannot be captured on the legacy
+        # default stream
+        self.stream = stream or torch.cuda.Stream(self.device)
+        h = C.c_void_p()
+        _ck(L.lb_create(arr, self.nb, C.c_void_p(self._ws), n.value, C.c_void_p(self.stream.cuda_stream),
+                        C.byref(h)), "lb_create")
+        self._h = h
+        self.dims = [(p.nx, p.ny, p.nz) for p in self._params]
+        self.n_particles = []
+        self.n_nodes = []
+        for b in range(self.nb):
+            npart, nn = C.c_int32(0), C.c_int64(0)
+            _ck(L.lb_box_info(self._h, b, C.byref(npart), C.byref(nn)), "lb_box_info")
+            self.n_particles.append(npart.value)
+            self.n_nodes.append(nn.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().lb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- initial state ------------------------------------------------------
+    def init_from_seed(self, seed):
+        _ck(load_library().lb_init_from_seed(self._h, int(seed)), "lb_init_from_seed")
+
+    def init_fields(self, box, rho, u=None, particles=None, walls=None):
+        N = self.n_nodes[box]
+        rho = np.ascontiguousarray(rho, np.float64).reshape(2, N)
+        up = None if u is None else np.ascontiguousarray(u, np.float64).reshape(3, N)
+        npb = self.n_particles[box]
+        parts = np.zeros((max(npb, 1), 9)) if particles is None else \
+            np.ascontiguousarray(particles, np.float64).reshape(-1, 9)
+        wl = None if walls is None else np.ascontiguousarray(walls, np.int32).reshape(N)
+        _ck(load_library().lb_init_fields(self._h, box, _dp(rho), None if up is None else _dp(up), _dp(parts),
+                                          None if wl is None else _ip(wl)), "lb_init_fields")
+
+    # -- stepping -------------------------------------------------------------
+    def step(self, n=1):
+        _ck(load_library().lb_step(self._h, int(n)), "lb_step")
+
+    def sync(self):
+        _ck(load_library().lb_sync(self._h), "lb_sync")
+
+    # -- state ------------------------------------------------------------------
+    def observables(self, box=0):
+        o = LbObs()
+        _ck(load_library().lb_observables(self._h, box, C.byref(o)), "lb_observables")
+        return dict(step=o.step, mass=np.array(o.mass[:]), mom_fluid=np.array(o.mom_fluid[:]),
+                    mom_part=np.array(o.mom_part[:]), max_u=o.max_u, n_cover=o.n_cover,
+                    n_uncover=o.n_uncover, n_fluid=o.n_fluid, n_solid=o.n_solid, error=o.error,
+                    n_particles=o.n_particles)
+
+    def export_state(self, box=0, f=True):
+        N = self.n_nodes[box]
+        fa = np.zeros((2, 19, N)) if f else None
+        owner = np.zeros(N, np.int32)
+        parts = np.zeros((max(self.n_particles[box], 1), 9))
+        meta = np.zeros(4)
+        _ck(load_library().lb_export_state(self._h, box, None if fa is None else _dp(fa), _ip(owner), _dp(parts),
+                                           _dp(meta)), "lb_export_state")
+        return dict(f=fa, owner=owner, particles=parts[: self.n_particles[box]], meta=meta)
+
+    def import_state(self, box, st):
+        f = np.ascontiguousarray(st["f"], np.float64)
+        owner = np.ascontiguousarray(st["owner"], np.int32)
+        parts = np.ascontiguousarray(st["particles"], np.float64).reshape(-1, 9)
+        if parts.shape[0] == 0:
+            parts = np.zeros((1, 9))
+        meta = np.ascontiguousarray(st["meta"], np.float64)
+        _ck(load_library().lb_import_state(self._h, box, _dp(f), _ip(owner), _dp(parts), _dp(meta)),
+            "lb_import_state")
+
+    def rho(self, box=0):
+        r = np.zeros((2, self.n_nodes[box]))
+        _ck(load_library().lb_export_rho(self._h, box, _dp(r)), "lb_export_rho")
+        return r
+
+    def phi(self, box=0):
+        nx, ny, nz = self.dims[box]
+        r = self.rho(box)
+        return (r[0] - r[1]).reshape(nz, ny, nx)
+
+    def set_colors(self, box, colors):
+        c = np.ascontiguousarray(colors, np.float64)
+        _ck(load_library().lb_set_particle_colors(self._h, box, _dp(c)), "lb_set_particle_colors")
+
+    def particle_forces(self, box=0):
+        npb = max(self.n_particles[box], 1)
+        F = np.zeros((npb, 3))
+        T = np.zeros((npb, 3))
+        _ck(load_library().lb_particle_forces(self._h, box, _dp(F), _dp(T)), "lb_particle_forces")
+        return F[: self.n_particles[box]], T[: self.n_particles[box]]
+
+    # -- tuning and timing ------------------------------------------------------------
+    def set_tiling(self, ty, cz):
+        _ck(load_library().lb_set_tiling(self._h, int(ty), int(cz)), "lb_set_tiling")
+
+    def set_profiling(self, on):
+        _ck(load_library().lb_set_profiling(self._h, 1 if on else 0), "lb_set_profiling")
+
+    def kernel_time(self):
+        ms = C.c_double(0)
+        nf, nt = C.c_int64(0), C.c_int64(0)
+        _ck(load_library().lb_kernel_time(self._h, C.byref(ms), C.byref(nf), C.byref(nt)), "lb_kernel_time")
+        return ms.value, nf.value, nt.value

@@ -1,0 +1,946 @@
+// lb_api.cu -- host side of the C ABI declared in include/lbpart.h: the
+// handle, the layout of the caller's device workspace, the tile plan of
+// the fused step kernel, CUDA-graph capture of the time step, seeded and
+// field initialisation, canonical export / import, and the observables.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lbpart.h"
+#include "lb_aux.cuh"
+#include "lb_ops.h"
+
+using namespace lbp;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int SMALL_GRID = 304, SMALL_BLOCK = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        off = align_up(off);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+const LbOps* ops_for(int prec) {
+    switch (prec) {
+        case LB_FP64: return &lb_ops_fp64;
+        case LB_FP32: return &lb_ops_fp32;
+        case LB_FP16_DEV: return &lb_ops_fp16;
+        case LB_BF16_DEV: return &lb_ops_bf16;
+        default: return nullptr;
+    }
+}
+
+int derive_np(const lb_params& p) {
+    if (p.n_particles >= 0) return p.n_particles;
+    const double N = (double)p.nx * p.ny * p.nz;
+    const double v = 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
+    return (int)std::floor(p.volume_fraction * N / v + 0.5);
+}
+
+double box_color(const lb_params& p) {
+    // Delta rho from the linear fit theta = 442 Delta rho + 90 (Fig. 4b)
+    if (std::isfinite(p.contact_angle_deg)) return (p.contact_angle_deg - 90.0) / 442.0;
+    return p.color;
+}
+
+int validate(const lb_params* bx, int nb) {
+    if (!bx || nb <= 0) return LB_EINVAL;
+    for (int b = 0; b < nb; b++) {
+        const lb_params& p = bx[b];
+        if (p.nx < 1 || p.ny < 1 || p.nz < 1) return LB_EINVAL;
+        if ((double)p.nx * p.ny * p.nz >= 2147483647.0) return LB_EINVAL;
+        if (!(p.tau[0] > 0.5) || !(p.tau[1] > 0.5)) return LB_EINVAL;
+        if (!(p.rho0 > 0.0) || !(p.radius > 0.0) || !(p.particle_density > 0.0)) return LB_EINVAL;
+        if (!(p.rho_init[0] > 0.0) || !(p.rho_init[1] > 0.0)) return LB_EINVAL;
+        if (p.precision != bx[0].precision || !ops_for(p.precision)) return LB_EINVAL;
+        if (p.vel_mode != 0 && p.vel_mode != 1) return LB_EINVAL;
+        if (p.reserved != 0) return LB_EINVAL;
+        if (derive_np(p) < 0) return LB_EINVAL;
+        if (!(p.lub_min >= 0.0)) return LB_EINVAL;
+    }
+    return LB_OK;
+}
+
+struct CellGeom {
+    int nc[3];
+    double len[3];
+};
+CellGeom cell_geom(const lb_params& p) {
+    // cells at least 2R + 2 wide: neighbour list for node claims (centre
+    // distance <= 2R + 2) and lubrication (gap < lub_cut <= 2) fit in +-1 cell
+    CellGeom g;
+    const double cmin = 2.0 * p.radius + 2.0 + (p.lub_cut > 2.0 ? p.lub_cut - 2.0 : 0.0);
+    const int L[3] = {p.nx, p.ny, p.nz};
+    for (int a = 0; a < 3; a++) {
+        int n = (int)std::floor(L[a] / cmin);
+        if (n < 1) n = 1;
+        g.nc[a] = n;
+        g.len[a] = (double)L[a] / n;
+    }
+    return g;
+}
+
+int ev_cap_for(const lb_params& p, int np) {
+    // per step a sphere moving less than one node changes at most the nodes
+    // of a shell of width one around its surface
+    const double R = p.radius;
+    const double per = 4.0 * M_PI * (R + 1.5) * (R + 1.5) * 1.5 + 64.0;
+    return (int)(np * per) + 1024;
+}
+
+}  // namespace
+
+struct lb_handle {
+    int nb = 0;
+    std::vector<lb_params> params;
+    const LbOps* ops = nullptr;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+
+    std::vector<BoxDev> hbox;
+    BoxDev* d_boxes = nullptr;
+    TileDev* d_tiles = nullptr;
+    int max_tiles = 0, ntiles = 0, ty = 8, cz = 32;
+    Shared sh{};
+    int NP = 0, total_cells = 0;
+    std::vector<int> pstart, npb, cell_off;
+    std::vector<int> has_walls;
+    double* stage = nullptr;
+    size_t stage_doubles = 0;
+    double* obs_buf = nullptr;   // [OBS_BLOCKS * OBS_W + OBS_W]
+    double* mass_tmp = nullptr;  // [2]
+    int64_t t = 0;
+    bool initialised = false;
+
+    cudaGraphExec_t g1[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t g6 = nullptr;
+    bool graphs_ok = false;
+
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    int ev_used = 0;
+    double prof_ms = 0.0;
+    int64_t prof_fused = 0, prof_total = 0, launches_since = 0;
+
+    int* h_err = nullptr;  // pinned mirror of the device error word
+    cudaEvent_t err_ev = nullptr;
+    bool err_pending = false;
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? LB_OK : LB_ECUDA; }
+#define CK(x)                                          \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return LB_ECUDA;        \
+    } while (0)
+
+// Lay out the workspace (base == nullptr: only count bytes).
+size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
+    Carver cv;
+    cv.base = base;
+    const LbOps* ops = ops_for(bx[0].precision);
+    const size_t rs = ops->real_size;
+    const bool dev = bx[0].precision == LB_FP16_DEV || bx[0].precision == LB_BF16_DEV;
+    int NP = 0, cells = 0, maxN = 0, maxTiles = 0, evcap = 0;
+    std::vector<BoxDev> hb(nb);
+    for (int b = 0; b < nb; b++) {
+        const lb_params& p = bx[b];
+        const int N = p.nx * p.ny * p.nz;
+        BoxDev& B = hb[b];
+        memset(&B, 0, sizeof(B));
+        B.nx = p.nx;
+        B.ny = p.ny;
+        B.nz = p.nz;
+        B.N = N;
+        if (dev) {
+            B.f = cv.take<uint16_t>((size_t)2 * 18 * N);
+            B.f0 = cv.take<float>((size_t)2 * N);
+        } else {
+            B.f = cv.take<char>((size_t)2 * 19 * N * rs);
+        }
+        for (int k = 0; k < 3; k++) B.rho[k] = cv.take<char>((size_t)2 * N * rs);
+        B.flags = cv.take<uint8_t>(N);
+        B.owner = cv.take<int32_t>(N);
+        B.evmark = cv.take<int32_t>(N);
+        B.mass_acc = cv.take<double>(4);
+        const int np = derive_np(p);
+        B.pstart = NP;
+        B.np = np;
+        NP += np;
+        CellGeom cg = cell_geom(p);
+        for (int a = 0; a < 3; a++) {
+            B.nc[a] = cg.nc[a];
+            B.cell_len[a] = cg.len[a];
+        }
+        B.cell_off = cells;
+        cells += cg.nc[0] * cg.nc[1] * cg.nc[2];
+        maxN = N > maxN ? N : maxN;
+        maxTiles += ((p.nx + 31) / 32) * ((p.ny + 3) / 4) * p.nz;
+        evcap += ev_cap_for(p, np);
+    }
+    Shared sh{};
+    const int NPa = NP > 0 ? NP : 1;
+    sh.part = cv.take<PartState>(NPa);
+    sh.force = cv.take<double>((size_t)NPa * 6);
+    sh.force_last = cv.take<double>((size_t)NPa * 6);
+    sh.color = cv.take<double>(NPa);
+    sh.pbox = cv.take<int>(NPa);
+    sh.cell_count = cv.take<int>(cells);
+    sh.cell_start = cv.take<int>(cells);
+    sh.cell_cursor = cv.take<int>(cells);
+    sh.cell_list = cv.take<int>(NPa);
+    sh.nlist = cv.take<int>((size_t)NPa * NL_MAX);
+    sh.nlist_n = cv.take<int>(NPa);
+    sh.events = cv.take<int4>(evcap);
+    sh.ev_rho = cv.take<double>((size_t)evcap * 2);
+    sh.ev_count = cv.take<int>(1);
+    sh.ev_cap = evcap;
+    sh.err = cv.take<int>(1);
+    sh.counters = cv.take<unsigned long long>((size_t)nb * 2);
+    BoxDev* d_boxes = cv.take<BoxDev>(nb);
+    TileDev* d_tiles = cv.take<TileDev>(maxTiles);
+    const size_t stage_doubles = (size_t)5 * maxN + (size_t)9 * NPa + 64;
+    double* stage = cv.take<double>(stage_doubles);
+    double* obs = cv.take<double>((size_t)OBS_BLOCKS * OBS_W + OBS_W);
+    double* mtmp = cv.take<double>(2);
+    if (h && base) {
+        h->hbox = hb;
+        h->sh = sh;
+        h->d_boxes = d_boxes;
+        h->d_tiles = d_tiles;
+        h->max_tiles = maxTiles;
+        h->NP = NP;
+        h->total_cells = cells;
+        h->stage = stage;
+        h->stage_doubles = stage_doubles;
+        h->obs_buf = obs;
+        h->mass_tmp = mtmp;
+    }
+    return align_up(cv.off);
+}
+
+void fill_params(lb_handle* h) {
+    for (int b = 0; b < h->nb; b++) {
+        const lb_params& p = h->params[b];
+        BoxDev& B = h->hbox[b];
+        B.has_walls = h->has_walls[b];
+        B.vel_mode = p.vel_mode;
+        B.fixed = p.fixed_particles;
+        for (int c = 0; c < 2; c++) {
+            B.tau[c] = p.tau[c];
+            B.inv_tau[c] = 1.0 / p.tau[c];
+            B.rho_ref[c] = p.rho_init[c];
+            B.rho_init[c] = p.rho_init[c];
+        }
+        B.g = p.g_br;
+        B.rho0 = p.rho0;
+        B.scw_axis = p.sc_weight[0];
+        B.scw_diag = p.sc_weight[1];
+        for (int a = 0; a < 3; a++) B.body[a] = p.body_force[a];
+        B.radius = p.radius;
+        B.mass = p.particle_density * 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
+        B.inertia = 0.4 * B.mass * p.radius * p.radius;
+        B.k_hertz = p.k_hertz;
+        B.lub_cut = p.lub_cut;
+        B.lub_min = p.lub_min;
+        B.nu = (1.0 / 3.0) * (0.5 * (p.tau[0] + p.tau[1]) - 0.5);
+        B.c0 = p.mass_corr_c0;
+    }
+}
+
+int upload_boxes(lb_handle* h) {
+    CK(cudaMemcpyAsync(h->d_boxes, h->hbox.data(), sizeof(BoxDev) * h->nb, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int build_tiles(lb_handle* h) {
+    std::vector<TileDev> tl;
+    for (int b = 0; b < h->nb; b++) {
+        const BoxDev& B = h->hbox[b];
+        for (int z0 = 0; z0 < B.nz; z0 += h->cz)
+            for (int y0 = 0; y0 < B.ny; y0 += h->ty)
+                for (int x0 = 0; x0 < B.nx; x0 += 32) {
+                    TileDev t;
+                    t.box = b;
+                    t.x0 = x0;
+                    t.y0 = y0;
+                    t.z0 = z0;
+                    t.w = B.nx - x0 < 32 ? B.nx - x0 : 32;
+                    t.h = B.ny - y0 < h->ty ? B.ny - y0 : h->ty;
+                    t.d = B.nz - z0 < h->cz ? B.nz - z0 : h->cz;
+                    t.pad = 0;
+                    tl.push_back(t);
+                }
+    }
+    if ((int)tl.size() > h->max_tiles) return LB_ENOMEM;
+    h->ntiles = (int)tl.size();
+    CK(cudaMemcpyAsync(h->d_tiles, tl.data(), sizeof(TileDev) * tl.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+// all kernels of one time step t
+int enqueue_step(lb_handle* h, int64_t t, bool prof) {
+    cudaStream_t st = h->stream;
+    const int par = (int)(t & 1), rc = (int)(t % 3), rn = (int)((t + 1) % 3), rz = (int)((t + 2) % 3);
+    const int mcur = (int)(t & 1), mnext = (int)((t + 1) & 1);
+    const int NP = h->NP;
+    int launches = 0;
+    k_step_begin<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->nb, h->sh, h->total_cells, mnext);
+    launches++;
+    if (NP > 0) {
+        const int pg = (NP + 255) / 256;
+        k_cell_count<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_cell_scan<<<h->nb, 1024, 0, st>>>(h->d_boxes, h->sh);
+        k_cell_fill<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_nlist<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_remap_detect<<<(NP + DETECT_WARPS - 1) / DETECT_WARPS, 32 * DETECT_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_remap_mark<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->sh);
+        CK(cudaGetLastError());
+        CK(h->ops->remap_apply(par, st, h->d_boxes, h->sh, rc, mcur));
+        CK(h->ops->remap_finish(st, h->d_boxes, h->sh, rc));
+        CK(h->ops->shell_density(st, h->d_boxes, h->sh, rc, NP));
+        launches += 9;
+    }
+    for (int b = 0; b < h->nb; b++)
+        if (h->has_walls[b]) {
+            CK(h->ops->wall_shell(st, h->d_boxes, b, rc));
+            launches++;
+        }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+        if (h->ev_used + 2 > (int)h->evpool.size()) {
+            for (int k = 0; k < 64; k++) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                h->evpool.push_back(e);
+            }
+        }
+        e0 = h->evpool[h->ev_used++];
+        e1 = h->evpool[h->ev_used++];
+        CK(cudaEventRecord(e0, st));
+    }
+    CK(h->ops->step(par, h->ty, h->ntiles, st, h->d_boxes, h->d_tiles, h->sh, rc, rn, rz, mnext));
+    launches++;
+    if (prof) {
+        CK(cudaEventRecord(e1, st));
+        h->prof_fused++;
+    }
+    if (NP > 0) {
+        const int pg = (NP + 255) / 256;
+        k_md_forces<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+        launches += 2;
+    }
+    h->launches_since = launches;
+    if (prof) h->prof_total += launches;
+    CK(cudaGetLastError());
+    return LB_OK;
+}
+
+void destroy_graphs(lb_handle* h) {
+    for (auto& g : h->g1)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (h->g6) {
+        cudaGraphExecDestroy(h->g6);
+        h->g6 = nullptr;
+    }
+    h->graphs_ok = false;
+}
+
+int capture(lb_handle* h, int64_t t0, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LB_OK;
+    for (int k = 0; k < nsteps && rc == LB_OK; k++) rc = enqueue_step(h, t0 + k, false);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc != LB_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return LB_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_rc(e);
+}
+
+int build_graphs(lb_handle* h) {
+    destroy_graphs(h);
+    for (int k = 0; k < 6; k++) {
+        int rc = capture(h, k, 1, &h->g1[k]);
+        if (rc != LB_OK) return rc;
+    }
+    int rc = capture(h, 0, 6, &h->g6);
+    if (rc != LB_OK) return rc;
+    h->graphs_ok = true;
+    return LB_OK;
+}
+
+int map_err(int bits) {
+    if (bits & ERR_OVERFLOW) return LB_EOVERFLOW;
+    if (bits & (ERR_UNSTABLE | ERR_FAST_PARTICLE)) return LB_EUNSTABLE;
+    return LB_OK;
+}
+
+int read_err(lb_handle* h) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, h->sh.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return map_err(v);
+}
+
+// Random sequential addition of the spheres of one box (host; stream 0 of
+// the box seed): candidate centre = L * u for three successive draws,
+// accepted when every earlier centre is at least 2R away (minimum image).
+// A cell grid only speeds up the search; decisions are those of the plain
+// all-pairs test.
+int rsa_place(const lb_params& p, int np, uint64_t s0, std::vector<double>& parts) {
+    parts.assign((size_t)np * 9, 0.0);
+    const double L[3] = {(double)p.nx, (double)p.ny, (double)p.nz};
+    const double dmin2 = 4.0 * p.radius * p.radius;
+    int gc[3];
+    for (int a = 0; a < 3; a++) {
+        gc[a] = (int)std::floor(L[a] / (2.0 * p.radius));
+        if (gc[a] < 1) gc[a] = 1;
+    }
+    std::vector<std::vector<int>> grid((size_t)gc[0] * gc[1] * gc[2]);
+    auto cell = [&](const double* c, int a) {
+        int v = (int)(c[a] / L[a] * gc[a]);
+        return v < 0 ? 0 : (v >= gc[a] ? gc[a] - 1 : v);
+    };
+    auto mi = [](double d, double Lx) { return d > 0.5 * Lx ? d - Lx : (d < -0.5 * Lx ? d + Lx : d); };
+    uint64_t draw = 0;
+    int placed = 0;
+    for (int64_t attempt = 0; placed < np; attempt++) {
+        if (attempt >= 1000000) return LB_EPLACE;
+        double c[3];
+        for (int a = 0; a < 3; a++) c[a] = L[a] * sm64_unit(s0, draw++);
+        bool ok = true;
+        int ci[3];
+        for (int a = 0; a < 3; a++) ci[a] = cell(c, a);
+        const int rng[3] = {gc[0] >= 3 ? 1 : gc[0], gc[1] >= 3 ? 1 : gc[1], gc[2] >= 3 ? 1 : gc[2]};
+        for (int dz = (gc[2] >= 3 ? -1 : 0); dz <= (gc[2] >= 3 ? 1 : gc[2] - 1) && ok; dz++)
+            for (int dy = (gc[1] >= 3 ? -1 : 0); dy <= (gc[1] >= 3 ? 1 : gc[1] - 1) && ok; dy++)
+                for (int dx = (gc[0] >= 3 ? -1 : 0); dx <= (gc[0] >= 3 ? 1 : gc[0] - 1) && ok; dx++) {
+                    const int cx_ = gc[0] >= 3 ? (ci[0] + dx + gc[0]) % gc[0] : dx;
+                    const int cy_ = gc[1] >= 3 ? (ci[1] + dy + gc[1]) % gc[1] : dy;
+                    const int cz_ = gc[2] >= 3 ? (ci[2] + dz + gc[2]) % gc[2] : dz;
+                    for (int q : grid[(size_t)cx_ + gc[0] * ((size_t)cy_ + gc[1] * cz_)]) {
+                        const double ddx = mi(c[0] - parts[9 * q + 0], L[0]);
+                        const double ddy = mi(c[1] - parts[9 * q + 1], L[1]);
+                        const double ddz = mi(c[2] - parts[9 * q + 2], L[2]);
+                        const double a2 = ddx * ddx, b2 = ddy * ddy, c2 = ddz * ddz;
+                        if ((a2 + b2) + c2 < dmin2) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+        (void)rng;
+        if (!ok) continue;
+        for (int a = 0; a < 3; a++) parts[9 * placed + a] = c[a];
+        grid[(size_t)cell(c, 0) + gc[0] * ((size_t)cell(c, 1) + gc[1] * cell(c, 2))].push_back(placed);
+        placed++;
+    }
+    return LB_OK;
+}
+
+// status, populations and density of box b at t = 0
+int init_box(lb_handle* h, int b, const double* parts_host, const int32_t* walls_host, const double* rho_dev,
+             const double* u_dev, uint64_t s_red, uint64_t s_blue, double noise) {
+    cudaStream_t st = h->stream;
+    BoxDev& B = h->hbox[b];
+    const int N = B.N, np = B.np;
+    // particles
+    if (np > 0) {
+        std::vector<PartState> ps(np);
+        std::vector<int> pb(np, b);
+        std::vector<double> col(np, box_color(h->params[b]));
+        for (int q = 0; q < np; q++)
+            for (int a = 0; a < 3; a++) {
+                ps[q].X[a] = parts_host[9 * q + a];
+                ps[q].U[a] = parts_host[9 * q + 3 + a];
+                ps[q].W[a] = parts_host[9 * q + 6 + a];
+            }
+        CK(cudaMemcpyAsync(h->sh.part + B.pstart, ps.data(), sizeof(PartState) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->sh.pbox + B.pstart, pb.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->sh.color + B.pstart, col.data(), sizeof(double) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(h->sh.force + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * np, st));
+        CK(cudaMemsetAsync(h->sh.force_last + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * np, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    // walls (owner -2) or fluid
+    h->has_walls[b] = 0;
+    if (walls_host) {
+        std::vector<int32_t> own(N);
+        for (int n = 0; n < N; n++) {
+            own[n] = walls_host[n] == OWN_WALL ? OWN_WALL : OWN_FLUID;
+            if (own[n] == OWN_WALL) h->has_walls[b] = 1;
+        }
+        CK(cudaMemcpyAsync(B.owner, own.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        k_fill<int32_t><<<SMALL_GRID * 4, 256, 0, st>>>(B.owner, OWN_FLUID, (size_t)N);
+    }
+    // claims: smallest distance, then lowest index (scratch in the stage;
+    // rho_dev / u_dev must not overlap it: they are placed after it)
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(h->stage);
+    int* idb = reinterpret_cast<int*>(h->stage + N);
+    k_fill<unsigned long long><<<SMALL_GRID * 4, 256, 0, st>>>(key, 0x7FF0000000000000ull, (size_t)N);
+    k_fill<int><<<SMALL_GRID * 4, 256, 0, st>>>(idb, 0x7fffffff, (size_t)N);
+    h->hbox[b].has_walls = h->has_walls[b];
+    fill_params(h);
+    int rc = upload_boxes(h);
+    if (rc != LB_OK) return rc;
+    if (np > 0) {
+        const int g = (np + 3) / 4;
+        k_claim<1><<<g, 128, 0, st>>>(h->d_boxes, h->sh, b, key, idb);
+        k_claim<2><<<g, 128, 0, st>>>(h->d_boxes, h->sh, b, key, idb);
+    }
+    k_owner_from_claims<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, b, idb);
+    k_shell_all<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, b);
+    CK(cudaGetLastError());
+    // density ring, marks
+    for (int k = 0; k < 3; k++) CK(cudaMemsetAsync(B.rho[k], 0, (size_t)2 * N * h->ops->real_size, st));
+    CK(cudaMemsetAsync(B.evmark, 0, sizeof(int32_t) * N, st));
+    CK(cudaMemsetAsync(h->mass_tmp, 0, 2 * sizeof(double), st));
+    CK(h->ops->init_pop(st, h->d_boxes, b, rho_dev, u_dev, s_red, s_blue, noise, 0, h->mass_tmp));
+    double m[2];
+    CK(cudaMemcpyAsync(m, h->mass_tmp, sizeof(m), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    B.mass0[0] = m[0];
+    B.mass0[1] = m[1];
+    double ma[4] = {m[0], m[1], 0.0, 0.0};
+    CK(cudaMemcpyAsync(B.mass_acc, ma, sizeof(ma), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->sh.counters + 2 * b, 0, 2 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(h->sh.err, 0, sizeof(int), st));
+    rc = upload_boxes(h);
+    if (rc != LB_OK) return rc;
+    return LB_OK;
+}
+
+int after_init(lb_handle* h, int64_t t) {
+    h->t = t;
+    h->initialised = true;
+    h->err_pending = false;
+    // graphs bake in the per-box wall flags, so they are rebuilt here; the
+    // legacy default stream cannot be captured, steps then launch directly
+    destroy_graphs(h);
+    if (h->stream == nullptr) return LB_OK;
+    return build_graphs(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_strerror(int code) {
+    switch (code) {
+        case LB_OK: return "ok";
+        case LB_EINVAL: return "invalid argument";
+        case LB_ENOMEM: return "workspace too small";
+        case LB_ECUDA: return "CUDA runtime error";
+        case LB_EUNSTABLE: return "unstable: non-finite density, |u| >= 0.5, or a particle faster than 1 node/step";
+        case LB_EPLACE: return "random sequential addition could not place the spheres";
+        case LB_ETIMEOUT: return "bounded device wait gave up";
+        case LB_EOVERFLOW: return "a fixed-capacity device list overflowed";
+        default: return "unknown error";
+    }
+}
+
+int lb_workspace_bytes(const lb_params* boxes, int32_t n_boxes, size_t* bytes) {
+    if (!bytes) return LB_EINVAL;
+    int rc = validate(boxes, n_boxes);
+    if (rc != LB_OK) return rc;
+    *bytes = layout(nullptr, boxes, n_boxes, nullptr);
+    return LB_OK;
+}
+
+int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t bytes, void* cuda_stream,
+              lb_handle** out) {
+    if (!out) return LB_EINVAL;
+    *out = nullptr;
+    int rc = validate(boxes, n_boxes);
+    if (rc != LB_OK) return rc;
+    if (!d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return LB_EINVAL;
+    const size_t need = layout(nullptr, boxes, n_boxes, nullptr);
+    if (bytes < need) return LB_ENOMEM;
+    lb_handle* h = new lb_handle();
+    h->nb = n_boxes;
+    h->params.assign(boxes, boxes + n_boxes);
+    h->ops = ops_for(boxes[0].precision);
+    h->stream = (cudaStream_t)cuda_stream;
+    h->ws = (char*)d_workspace;
+    h->ws_bytes = bytes;
+    h->has_walls.assign(n_boxes, 0);
+    layout(h, boxes, n_boxes, h->ws);
+    fill_params(h);
+    if (h->ops->setup() != cudaSuccess || cudaHostAlloc((void**)&h->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming) != cudaSuccess) {
+        lb_destroy(h);
+        return LB_ECUDA;
+    }
+    *h->h_err = 0;
+    // default tiling: 8 rows per CTA; z chunks so that there are >= 4 waves of CTAs on 152 SMs
+    h->ty = 8;
+    long long cols = 0;
+    int maxnz = 1;
+    for (auto& p : h->params) {
+        cols += (long long)((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+        maxnz = p.nz > maxnz ? p.nz : maxnz;
+    }
+    int cz = maxnz;
+    while (cz > 8 && cols * ((maxnz + cz - 1) / cz) < 152 * 8) cz = (cz + 1) / 2;
+    h->cz = cz;
+    rc = upload_boxes(h);
+    if (rc == LB_OK) rc = build_tiles(h);
+    if (rc == LB_OK) {
+        CK(cudaMemsetAsync(h->sh.err, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(h->sh.counters, 0, sizeof(unsigned long long) * 2 * h->nb, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    if (rc != LB_OK) {
+        lb_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+int lb_init_from_seed(lb_handle* h, uint64_t seed) {
+    if (!h) return LB_EINVAL;
+    for (int b = 0; b < h->nb; b++) {
+        const uint64_t sb = seed + (uint64_t)b;
+        const uint64_t s0 = sm64(sb, 0), s_red = sm64(sb, 1), s_blue = sm64(sb, 2);
+        std::vector<double> parts;
+        int rc = rsa_place(h->params[b], h->hbox[b].np, s0, parts);
+        if (rc != LB_OK) return rc;
+        rc = init_box(h, b, parts.data(), nullptr, nullptr, nullptr, s_red, s_blue, h->params[b].noise_amp);
+        if (rc != LB_OK) return rc;
+    }
+    return after_init(h, 0);
+}
+
+int lb_init_fields(lb_handle* h, int32_t box, const double* rho, const double* u, const double* particles,
+                   const int32_t* walls) {
+    if (!h || box < 0 || box >= h->nb || !rho) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    if (B.np > 0 && !particles) return LB_EINVAL;
+    const size_t N = (size_t)B.N;
+    // The node status is built first (its claim scratch occupies the first
+    // 1.5 N doubles of the stage) with uniform rho_init populations; then
+    // the fields are copied into the stage (rho at [0, 2N), u at [2N, 5N))
+    // and the populations are rebuilt from them.
+    double* rho_dev = h->stage;
+    double* u_dev = u ? h->stage + 2 * N : nullptr;
+    int rc;
+    {
+        cudaStream_t st = h->stream;
+        rc = init_box(h, box, particles, walls, nullptr, nullptr, 0, 0, 0.0);
+        if (rc != LB_OK) return rc;
+        CK(cudaMemcpyAsync(rho_dev, rho, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, st));
+        if (u) CK(cudaMemcpyAsync(u_dev, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(h->mass_tmp, 0, 2 * sizeof(double), st));
+        CK(h->ops->init_pop(st, h->d_boxes, box, rho_dev, u_dev, 0, 0, 0.0, 0, h->mass_tmp));
+        double m[2];
+        CK(cudaMemcpyAsync(m, h->mass_tmp, sizeof(m), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        BoxDev& Bw = h->hbox[box];
+        Bw.mass0[0] = m[0];
+        Bw.mass0[1] = m[1];
+        double ma[4] = {m[0], m[1], 0.0, 0.0};
+        CK(cudaMemcpyAsync(Bw.mass_acc, ma, sizeof(ma), cudaMemcpyHostToDevice, st));
+        rc = upload_boxes(h);
+        if (rc != LB_OK) return rc;
+    }
+    return after_init(h, 0);
+}
+
+int lb_step(lb_handle* h, int64_t n) {
+    if (!h || n < 0) return LB_EINVAL;
+    if (!h->initialised) return LB_EINVAL;
+    // report a device error seen by an earlier call that has finished
+    if (h->err_pending && cudaEventQuery(h->err_ev) == cudaSuccess) {
+        h->err_pending = false;
+        int e = map_err(*h->h_err);
+        if (e != LB_OK) return e;
+    }
+    if (n == 0) return LB_OK;
+    while (n > 0) {
+        if (h->prof || !h->graphs_ok) {
+            int rc = enqueue_step(h, h->t, h->prof);
+            if (rc != LB_OK) return rc;
+            h->t++;
+            n--;
+        } else if (h->t % 6 == 0 && n >= 6) {
+            CK(cudaGraphLaunch(h->g6, h->stream));
+            h->t += 6;
+            n -= 6;
+        } else {
+            CK(cudaGraphLaunch(h->g1[h->t % 6], h->stream));
+            h->t++;
+            n--;
+        }
+    }
+    CK(cudaMemcpyAsync(h->h_err, h->sh.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->err_ev, h->stream));
+    h->err_pending = true;
+    return LB_OK;
+}
+
+int lb_sync(lb_handle* h) {
+    if (!h) return LB_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    return read_err(h);
+}
+
+int lb_observables(lb_handle* h, int32_t box, lb_obs* out) {
+    if (!h || !out || box < 0 || box >= h->nb) return LB_EINVAL;
+    memset(out, 0, sizeof(*out));
+    const BoxDev& B = h->hbox[box];
+    cudaStream_t st = h->stream;
+    const int par = (int)(h->t & 1);
+    CK(h->ops->obs_partial(st, h->d_boxes, box, par, h->obs_buf));
+    double* fin = h->obs_buf + (size_t)OBS_BLOCKS * OBS_W;
+    k_obs_final<<<1, 32, 0, st>>>(h->obs_buf, OBS_BLOCKS, fin);
+    CK(cudaGetLastError());
+    double v[OBS_W];
+    CK(cudaMemcpyAsync(v, fin, sizeof(v), cudaMemcpyDeviceToHost, st));
+    unsigned long long cnt[2];
+    CK(cudaMemcpyAsync(cnt, h->sh.counters + 2 * box, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    std::vector<PartState> ps(B.np > 0 ? B.np : 1);
+    if (B.np > 0)
+        CK(cudaMemcpyAsync(ps.data(), h->sh.part + B.pstart, sizeof(PartState) * B.np, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->step = h->t;
+    out->mass[0] = v[0];
+    out->mass[1] = v[1];
+    for (int a = 0; a < 3; a++) out->mom_fluid[a] = v[2 + a];
+    out->max_u = v[5];
+    out->n_fluid = (int64_t)v[6];
+    out->n_solid = (int64_t)v[7];
+    if (!h->params[box].fixed_particles)
+        for (int q = 0; q < B.np; q++)
+            for (int a = 0; a < 3; a++) out->mom_part[a] += B.mass * ps[q].U[a];
+    out->n_cover = (int64_t)cnt[0];
+    out->n_uncover = (int64_t)cnt[1];
+    out->n_particles = B.np;
+    out->error = read_err(h);
+    return LB_OK;
+}
+
+int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double* particles, double* meta) {
+    if (!h || box < 0 || box >= h->nb) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    cudaStream_t st = h->stream;
+    const int par = (int)(h->t & 1);
+    CK(cudaStreamSynchronize(st));
+    if (f) {
+        for (int c = 0; c < 2; c++)
+            for (int i = 0; i < 19; i++) {
+                CK(h->ops->export_dir(st, h->d_boxes, box, c, i, par, h->stage));
+                CK(cudaMemcpyAsync(f + ((size_t)c * 19 + i) * B.N, h->stage, sizeof(double) * B.N,
+                                   cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            }
+    }
+    if (owner) {
+        CK(cudaMemcpyAsync(owner, B.owner, sizeof(int32_t) * B.N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int n = 0; n < B.N; n++)
+            if (owner[n] >= 0) owner[n] -= B.pstart;
+    }
+    if (particles && B.np > 0) {
+        std::vector<PartState> ps(B.np);
+        CK(cudaMemcpyAsync(ps.data(), h->sh.part + B.pstart, sizeof(PartState) * B.np, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int q = 0; q < B.np; q++)
+            for (int a = 0; a < 3; a++) {
+                particles[9 * q + a] = ps[q].X[a];
+                particles[9 * q + 3 + a] = ps[q].U[a];
+                particles[9 * q + 6 + a] = ps[q].W[a];
+            }
+    }
+    if (meta) {
+        meta[0] = (double)h->t;
+        meta[1] = B.mass0[0];
+        meta[2] = B.mass0[1];
+        meta[3] = (double)B.np;
+    }
+    return LB_OK;
+}
+
+int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* owner, const double* particles,
+                    const double* meta) {
+    if (!h || box < 0 || box >= h->nb || !f || !owner || !meta) return LB_EINVAL;
+    BoxDev& B = h->hbox[box];
+    if (B.np > 0 && !particles) return LB_EINVAL;
+    if ((int)meta[3] != B.np) return LB_EINVAL;
+    const int64_t t = (int64_t)meta[0];
+    if (t < 0) return LB_EINVAL;
+    if (h->nb > 1 && h->initialised && t != h->t) return LB_EINVAL;
+    cudaStream_t st = h->stream;
+    const int N = B.N;
+    if (B.np > 0) {
+        std::vector<PartState> ps(B.np);
+        std::vector<int> pb(B.np, box);
+        std::vector<double> col(B.np, box_color(h->params[box]));
+        for (int q = 0; q < B.np; q++)
+            for (int a = 0; a < 3; a++) {
+                ps[q].X[a] = particles[9 * q + a];
+                ps[q].U[a] = particles[9 * q + 3 + a];
+                ps[q].W[a] = particles[9 * q + 6 + a];
+            }
+        CK(cudaMemcpyAsync(h->sh.part + B.pstart, ps.data(), sizeof(PartState) * B.np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->sh.pbox + B.pstart, pb.data(), sizeof(int) * B.np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->sh.color + B.pstart, col.data(), sizeof(double) * B.np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(h->sh.force + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * B.np, st));
+        CK(cudaMemsetAsync(h->sh.force_last + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * B.np, st));
+    }
+    std::vector<int32_t> own(N);
+    h->has_walls[box] = 0;
+    for (int n = 0; n < N; n++) {
+        const int o = owner[n];
+        if (o >= B.np || o < -2) return LB_EINVAL;
+        own[n] = o >= 0 ? o + B.pstart : o;
+        if (o == OWN_WALL) h->has_walls[box] = 1;
+    }
+    CK(cudaMemcpyAsync(B.owner, own.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    B.mass0[0] = meta[1];
+    B.mass0[1] = meta[2];
+    fill_params(h);
+    int rc = upload_boxes(h);
+    if (rc != LB_OK) return rc;
+    k_flags_from_owner<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, box);
+    k_shell_all<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, box);
+    CK(cudaGetLastError());
+    const int par = (int)(t & 1), rcs = (int)(t % 3);
+    for (int c = 0; c < 2; c++)
+        for (int i = 0; i < 19; i++) {
+            CK(cudaMemcpyAsync(h->stage, f + ((size_t)c * 19 + i) * N, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+            CK(h->ops->import_dir(st, h->d_boxes, box, c, i, par, h->stage));
+        }
+    for (int k = 0; k < 3; k++) CK(cudaMemsetAsync(B.rho[k], 0, (size_t)2 * N * h->ops->real_size, st));
+    CK(cudaMemsetAsync(B.evmark, 0, sizeof(int32_t) * N, st));
+    CK(cudaMemsetAsync(h->mass_tmp, 0, 2 * sizeof(double), st));
+    CK(h->ops->rho_from_pop(st, h->d_boxes, box, par, rcs, nullptr, h->mass_tmp));
+    CK(cudaMemcpyAsync(B.mass_acc + 2 * par, h->mass_tmp, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(h->sh.counters + 2 * box, 0, 2 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(h->sh.err, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    return after_init(h, t);
+}
+
+int lb_export_rho(lb_handle* h, int32_t box, double* rho) {
+    if (!h || !rho || box < 0 || box >= h->nb) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    cudaStream_t st = h->stream;
+    CK(h->ops->rho_from_pop(st, h->d_boxes, box, (int)(h->t & 1), -1, h->stage, nullptr));
+    CK(cudaMemcpyAsync(rho, h->stage, sizeof(double) * 2 * B.N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return LB_OK;
+}
+
+int lb_set_particle_colors(lb_handle* h, int32_t box, const double* colors) {
+    if (!h || !colors || box < 0 || box >= h->nb) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    if (B.np == 0) return LB_OK;
+    CK(cudaMemcpyAsync(h->sh.color + B.pstart, colors, sizeof(double) * B.np, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_particle_forces(lb_handle* h, int32_t box, double* F, double* T) {
+    if (!h || box < 0 || box >= h->nb) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    if (B.np == 0) return LB_OK;
+    std::vector<double> v((size_t)B.np * 6);
+    CK(cudaMemcpyAsync(v.data(), h->sh.force_last + (size_t)B.pstart * 6, sizeof(double) * 6 * B.np,
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int q = 0; q < B.np; q++)
+        for (int a = 0; a < 3; a++) {
+            if (F) F[3 * q + a] = v[6 * q + a];
+            if (T) T[3 * q + a] = v[6 * q + 3 + a];
+        }
+    return LB_OK;
+}
+
+int lb_box_info(lb_handle* h, int32_t box, int32_t* n_particles, int64_t* n_nodes) {
+    if (!h || box < 0 || box >= h->nb) return LB_EINVAL;
+    if (n_particles) *n_particles = h->hbox[box].np;
+    if (n_nodes) *n_nodes = h->hbox[box].N;
+    return LB_OK;
+}
+
+int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz) {
+    if (!h || (ty != 4 && ty != 8 && ty != 16) || cz < 1) return LB_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    h->ty = ty;
+    h->cz = cz;
+    int rc = build_tiles(h);
+    if (rc != LB_OK) return rc;
+    destroy_graphs(h);
+    if (h->initialised && h->stream) return build_graphs(h);
+    return LB_OK;
+}
+
+int lb_set_profiling(lb_handle* h, int32_t on) {
+    if (!h) return LB_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    h->prof = on != 0;
+    h->ev_used = 0;
+    h->prof_ms = 0.0;
+    h->prof_fused = 0;
+    h->prof_total = 0;
+    return LB_OK;
+}
+
+int lb_kernel_time(lb_handle* h, double* ms_fused, int64_t* launches_fused, int64_t* launches_total) {
+    if (!h) return LB_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    double ms = 0.0;
+    for (int k = 0; k + 1 < h->ev_used; k += 2) {
+        float v = 0.f;
+        CK(cudaEventElapsedTime(&v, h->evpool[k], h->evpool[k + 1]));
+        ms += v;
+    }
+    if (ms_fused) *ms_fused = ms;
+    if (launches_fused) *launches_fused = h->prof_fused;
+    if (launches_total) *launches_total = h->prof_total;
+    h->ev_used = 0;
+    h->prof_fused = 0;
+    h->prof_total = 0;
+    return LB_OK;
+}
+
+void lb_destroy(lb_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    for (auto e : h->evpool) cudaEventDestroy(e);
+    if (h->err_ev) cudaEventDestroy(h->err_ev);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    delete h;
+}
+
+}  // extern "C"

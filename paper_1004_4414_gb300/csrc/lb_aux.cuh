@@ -1,0 +1,267 @@
+// lb_aux.cuh -- kernels outside the time step: node status from particle
+// positions, initial populations, canonical export / import of the state,
+// densities, and the observables reduction.
+#pragma once
+#include "lb_common.cuh"
+#include "lb_particles.cuh"
+
+namespace lbp {
+
+template <class T>
+static __global__ void k_fill(T* __restrict__ p, T v, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Claim of the nodes inside each sphere for a state with no previous status:
+// pass 1 keeps the smallest squared distance per node (FP64 bits, which
+// order like the values for non-negative numbers), pass 2 the lowest
+// particle index among the particles at that distance.
+template <int PASS>
+static __global__ void k_claim(const BoxDev* __restrict__ boxes, Shared sh, int b, unsigned long long* __restrict__ key,
+                        int* __restrict__ idbuf) {
+    const BoxDev& B = boxes[b];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lp = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (lp >= B.np) return;
+    const int p = B.pstart + lp;
+    const PartState ps = sh.part[p];
+    const double R = B.radius, R2 = R * R;
+    const int dims[3] = {B.nx, B.ny, B.nz};
+    int lo[3], span[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = (int)floor(ps.X[a] - R);
+        span[a] = (int)floor(ps.X[a] + R) - lo[a] + 1;
+        if (span[a] > dims[a]) span[a] = dims[a];
+    }
+    const int total = span[0] * span[1] * span[2];
+    for (int idx = lane; idx < total; idx += 32) {
+        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+        const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
+        const double d2 = dist2_nc(mimg((double)gx - ps.X[0], B.nx), mimg((double)gy - ps.X[1], B.ny),
+                                   mimg((double)gz - ps.X[2], B.nz));
+        if (d2 > R2) continue;
+        const int n = gx + B.nx * (gy + B.ny * gz);
+        if (B.owner[n] == OWN_WALL) continue;
+        const unsigned long long k = (unsigned long long)__double_as_longlong(d2);
+        if (PASS == 1) atomicMin(&key[n], k);
+        else if (key[n] == k) atomicMin(&idbuf[n], p);
+    }
+}
+
+static __global__ void k_owner_from_claims(const BoxDev* __restrict__ boxes, int b, const int* __restrict__ idbuf) {
+    const BoxDev& B = boxes[b];
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        if (B.owner[n] == OWN_WALL) {
+            B.flags[n] = FL_SOLID;
+            continue;
+        }
+        const int id = idbuf[n];
+        B.owner[n] = id == 0x7fffffff ? OWN_FLUID : id;
+        B.flags[n] = id == 0x7fffffff ? 0 : FL_SOLID;
+    }
+}
+
+static __global__ void k_shell_all(const BoxDev* __restrict__ boxes, int b) {
+    const BoxDev& B = boxes[b];
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) shell_update(B, n);
+}
+
+// owner map given by the caller (global particle indices already applied)
+static __global__ void k_flags_from_owner(const BoxDev* __restrict__ boxes, int b) {
+    const BoxDev& B = boxes[b];
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x)
+        B.flags[n] = B.owner[n] == OWN_FLUID ? 0 : FL_SOLID;
+}
+
+// f = f^eq(rho, u) on fluid nodes in the even-step layout (own slots);
+// rho from a field [2][N] or from SplitMix64 noise; u from a field [3][N]
+// or zero.  The density ring slot rc gets rho on fluid nodes, 0 elsewhere.
+template <class P>
+static __global__ void k_init_pop(const BoxDev* __restrict__ boxes, int b, const double* __restrict__ rho_field,
+                           const double* __restrict__ u_field, uint64_t s_red, uint64_t s_blue, double noise,
+                           int rc, double* __restrict__ mass_out) {
+    using R = typename P::real;
+    const BoxDev& B = boxes[b];
+    const Pop<P> pop(B);
+    R* rcur = reinterpret_cast<R*>(B.rho[rc]);
+    double m0 = 0.0, m1 = 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        if (B.flags[n] & FL_SOLID) {
+            rcur[n] = R(0);
+            rcur[(size_t)B.N + n] = R(0);
+            continue;
+        }
+        double rho[2];
+        if (rho_field) {
+            rho[0] = rho_field[n];
+            rho[1] = rho_field[(size_t)B.N + n];
+        } else {
+            // noise U(-a, a): output n of the red / blue noise streams
+            rho[0] = B.rho_init[0] + noise * (2.0 * sm64_unit(s_red, (uint64_t)n) - 1.0);
+            rho[1] = B.rho_init[1] + noise * (2.0 * sm64_unit(s_blue, (uint64_t)n) - 1.0);
+        }
+        const R ux = u_field ? (R)u_field[n] : R(0);
+        const R uy = u_field ? (R)u_field[(size_t)B.N + n] : R(0);
+        const R uz = u_field ? (R)u_field[(size_t)2 * B.N + n] : R(0);
+        for (int c = 0; c < 2; c++) {
+            const R r = (R)rho[c];
+            R resid = R(0), sent = R(0);
+            for (int i = 1; i < 19; i++) {
+                const R fe = feq_rt<R>(i, r, ux, uy, uz);
+                const R q = pop.store(c, i, n, fe);
+                resid += fe - q;
+                sent += q;
+            }
+            const R q0 = pop.store(c, 0, n, feq_rt<R>(0, r, ux, uy, uz) + resid);
+            sent += q0;
+            rcur[(size_t)c * B.N + n] = sent;
+            if (c == 0) m0 += (double)sent;
+            else m1 += (double)sent;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+        m1 += __shfl_xor_sync(0xffffffffu, m1, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&mass_out[0], m0);
+        atomicAdd(&mass_out[1], m1);
+    }
+}
+
+// populations of node n at the coming step of parity par
+template <class P>
+__device__ __forceinline__ typename P::real load_node_pop(const BoxDev& B, const Pop<P>& pop, int par, int c, int i,
+                                                          int n) {
+    if (par == 0 || i == 0) return pop.load(c, i, n);
+    const int s = nbr_index(B, n, -cx(i), -cy(i), -cz(i));
+    if (B.flags[s] & FL_SOLID) return pop.load(c, i, n);
+    return pop.load(c, opp(i), s);
+}
+
+template <class P>
+static __global__ void k_export_dir(const BoxDev* __restrict__ boxes, int b, int c, int i, int par, double* __restrict__ out) {
+    const BoxDev& B = boxes[b];
+    const Pop<P> pop(B);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x)
+        out[n] = (B.flags[n] & FL_SOLID) ? 0.0 : (double)load_node_pop<P>(B, pop, par, c, i, n);
+}
+
+template <class P>
+static __global__ void k_import_dir(const BoxDev* __restrict__ boxes, int b, int c, int i, int par, const double* __restrict__ in) {
+    using R = typename P::real;
+    const BoxDev& B = boxes[b];
+    const Pop<P> pop(B);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        if (B.flags[n] & FL_SOLID) continue;
+        const R v = (R)in[n];
+        if (par == 0 || i == 0) {
+            pop.store(c, i, n, v);
+        } else {
+            const int s = nbr_index(B, n, -cx(i), -cy(i), -cz(i));
+            if (B.flags[s] & FL_SOLID) pop.store(c, i, n, v);
+            else pop.store(c, opp(i), s, v);
+        }
+    }
+}
+
+// rho^c = sum_i f_i on fluid nodes (0 on solid) into ring slot rc and/or a
+// double array; fluid mass into mass_out
+template <class P>
+static __global__ void k_rho_from_pop(const BoxDev* __restrict__ boxes, int b, int par, int rc, double* __restrict__ out,
+                               double* __restrict__ mass_out) {
+    using R = typename P::real;
+    const BoxDev& B = boxes[b];
+    const Pop<P> pop(B);
+    R* rcur = rc >= 0 ? reinterpret_cast<R*>(B.rho[rc]) : nullptr;
+    double m0 = 0.0, m1 = 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        R r[2] = {R(0), R(0)};
+        if (!(B.flags[n] & FL_SOLID))
+            for (int c = 0; c < 2; c++)
+                for (int i = 0; i < 19; i++) r[c] += load_node_pop<P>(B, pop, par, c, i, n);
+        if (rcur) {
+            rcur[n] = r[0];
+            rcur[(size_t)B.N + n] = r[1];
+        }
+        if (out) {
+            out[n] = (double)r[0];
+            out[(size_t)B.N + n] = (double)r[1];
+        }
+        m0 += (double)r[0];
+        m1 += (double)r[1];
+    }
+    if (mass_out) {
+        for (int off = 16; off > 0; off >>= 1) {
+            m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+            m1 += __shfl_xor_sync(0xffffffffu, m1, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&mass_out[0], m0);
+            atomicAdd(&mass_out[1], m1);
+        }
+    }
+}
+
+// ------------------------------------------------------------ observables
+// Per block: mass[2], fluid momentum[3], max |u|, fluid and solid node
+// counts -> partials[block][8]; a second single-block pass reduces them.
+constexpr int OBS_W = 8;
+constexpr int OBS_BLOCKS = 304;
+template <class P>
+static __global__ void __launch_bounds__(256) k_obs_partial(const BoxDev* __restrict__ boxes, int b, int par,
+                                                     double* __restrict__ partials) {
+    using R = typename P::real;
+    const BoxDev& B = boxes[b];
+    const Pop<P> pop(B);
+    double v[OBS_W] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        if (B.flags[n] & FL_SOLID) {
+            v[7] += 1.0;
+            continue;
+        }
+        double rt = 0, jt[3] = {0, 0, 0};
+        for (int c = 0; c < 2; c++)
+            for (int i = 0; i < 19; i++) {
+                const double f = (double)load_node_pop<P>(B, pop, par, c, i, n);
+                v[c] += f;
+                rt += f;
+                jt[0] += f * cx(i);
+                jt[1] += f * cy(i);
+                jt[2] += f * cz(i);
+            }
+        v[2] += jt[0];
+        v[3] += jt[1];
+        v[4] += jt[2];
+        const double um = sqrt(jt[0] * jt[0] + jt[1] * jt[1] + jt[2] * jt[2]) / rt;
+        v[5] = fmax(v[5], um);
+        v[6] += 1.0;
+    }
+    __shared__ double s[8][OBS_W];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < OBS_W; k++) {
+        double x = v[k];
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_xor_sync(0xffffffffu, x, off);
+            x = (k == 5) ? fmax(x, o) : x + o;
+        }
+        if (lane == 0) s[wid][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < OBS_W) {
+        const int k = threadIdx.x;
+        double x = s[0][k];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) x = (k == 5) ? fmax(x, s[w][k]) : x + s[w][k];
+        partials[blockIdx.x * OBS_W + k] = x;
+    }
+}
+
+static __global__ void k_obs_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= OBS_W) return;
+    double x = 0.0;
+    for (int i = 0; i < nblocks; i++) x = (k == 5) ? fmax(x, partials[i * OBS_W + k]) : x + partials[i * OBS_W + k];
+    out[k] = x;
+}
+
+}  // namespace lbp

@@ -1,0 +1,252 @@
+// lb_common.cuh -- shared device definitions of the sm_103a library:
+// D3Q19 lattice, box and tile descriptors, population storage policies,
+// SplitMix64 and the cubic equilibrium.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbp {
+
+// ---------------------------------------------------------------- lattice
+// D3Q19 (Sec. II): rest, 6 axis links, 12 face diagonals in opposite pairs
+// (odd i, i + 1).  The order is the library's canonical export order.
+__host__ __device__ constexpr int cx(int i) {
+    constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return v[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+    constexpr int v[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return v[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+    constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return v[i];
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr bool is_axis(int i) { return i >= 1 && i <= 6; }
+// lattice weights zeta_i: 1/3, 1/18 (axis), 1/36 (diagonal)
+template <class R>
+__host__ __device__ constexpr R wgt(int i) {
+    return i == 0 ? R(1) / R(3) : (i <= 6 ? R(1) / R(18) : R(1) / R(36));
+}
+
+// flag bits of a node
+constexpr uint8_t FL_SOLID = 1;   // inside a particle or a static wall
+constexpr uint8_t FL_SHELL = 2;   // solid with at least one fluid neighbour
+constexpr int32_t OWN_FLUID = -1, OWN_WALL = -2;
+
+// sticky device error bits
+constexpr int ERR_UNSTABLE = 1, ERR_OVERFLOW = 2, ERR_FAST_PARTICLE = 4;
+
+// ---------------------------------------------------------------- particles
+struct PartState {        // per particle, FP64
+    double X[3], U[3], W[3];
+};
+
+// ------------------------------------------------------------ descriptors
+// Everything a kernel needs to know about one box.  Lives in device memory.
+struct BoxDev {
+    int nx, ny, nz;
+    int N;                      // nx*ny*nz (< 2^31)
+    void* f;                    // populations (layout: StorePolicy)
+    float* f0;                  // rest slot for 16-bit deviation storage
+    void* rho[3];               // density ring: [2][N] of real each
+    uint8_t* flags;             // [N]
+    int32_t* owner;             // [N] global particle index, -1 fluid, -2 wall
+    int32_t* evmark;            // [N] old owner + 3 while a remap is applied, else 0
+    int pstart, np;             // global index range of this box's particles
+    int has_walls;
+    int vel_mode;
+    int fixed;
+    int pad0;
+    double tau[2], inv_tau[2];
+    double g, rho0, scw_axis, scw_diag;
+    double rho_ref[2];          // reference density of the deviation storage
+    double body[3];
+    double radius, mass, inertia, k_hertz, lub_cut, lub_min, nu;
+    double c0, rho_init[2];
+    double mass0[2];            // initial fluid mass
+    double* mass_acc;           // [2 slots][2 components] fluid mass produced by the step kernel
+    int nc[3];                  // cells per axis
+    int cell_off;               // offset into the global cell arrays
+    double cell_len[3];
+    uint8_t* vf_dummy;
+};
+
+struct TileDev {                // one CTA work item of the fused step kernel
+    int box;
+    int x0, y0, z0;
+    int w, h, d;
+    int pad;
+};
+
+// Global per-step work lists and scratch (device memory).
+struct Shared {
+    PartState* part;            // [NP]
+    double* force;              // [NP][6] F, T accumulators
+    double* force_last;         // [NP][6] coupling forces of the last step
+    double* color;              // [NP]
+    int* pbox;                  // [NP] box of each particle
+    int* cell_count;            // [total cells]
+    int* cell_start;            // [total cells + 1 per box]
+    int* cell_cursor;
+    int* cell_list;             // [NP]
+    int* nlist;                 // [NP][NL_MAX] neighbours within 2R (claims)
+    int* nlist_n;               // [NP]
+    int4* events;               // [cap] (node, box, old owner, new owner)
+    double* ev_rho;             // [cap][2] refill density
+    int* ev_count;              // [1]
+    int ev_cap;
+    int* err;                   // [1] sticky error bits
+    unsigned long long* counters; // [n_boxes][2] n_cover, n_uncover
+};
+
+constexpr int NL_MAX = 32;
+
+// ------------------------------------------------------------ SplitMix64
+// Steele, Lea & Flood (OOPSLA 2014): output n of a generator seeded with s
+// is mix(s + (n + 1) * 0x9E3779B97F4A7C15).
+__host__ __device__ inline uint64_t sm64(uint64_t s, uint64_t n) {
+    uint64_t z = s + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ inline double sm64_unit(uint64_t s, uint64_t n) {
+    return (double)(sm64(s, n) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ------------------------------------------------------------ equilibrium
+// Eq. Equil with c_s^2 = 1/3:
+//   zeta_i rho [1 + 3 cu + 9/2 (cu)^2 - 3/2 u^2 + 9/2 (cu)^3 - 9/2 u^2 cu].
+template <class R, int I>
+__device__ __forceinline__ R feq_dir(R rho, R ux, R uy, R uz, R uu) {
+    R cu = R(cx(I)) * ux + R(cy(I)) * uy + R(cz(I)) * uz;
+    R t = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu + R(4.5) * cu * cu * cu - R(4.5) * uu * cu;
+    return wgt<R>(I) * rho * t;
+}
+template <class R>
+__device__ __forceinline__ R feq_rt(int i, R rho, R ux, R uy, R uz) {
+    R uu = ux * ux + uy * uy + uz * uz;
+    R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
+    R t = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu + R(4.5) * cu * cu * cu - R(4.5) * uu * cu;
+    return wgt<R>(i) * rho * t;
+}
+
+// ----------------------------------------------------- storage policies
+// Populations of component c, direction i at node n.
+//   FP64 / FP32: one array [2][19][N] of double / float.
+//   FP16 / BF16 deviations: [2][18][N] 16-bit values d = f/zeta_i - rho_ref^c
+//   for i = 1..18, and the rest population in a separate FP32 array [2][N].
+struct P64 {
+    using real = double;
+    using st = double;
+    static constexpr bool dev = false;
+    static constexpr int id = 0;
+};
+struct P32 {
+    using real = float;
+    using st = float;
+    static constexpr bool dev = false;
+    static constexpr int id = 1;
+};
+struct P16 {
+    using real = float;
+    using st = __half;
+    static constexpr bool dev = true;
+    static constexpr int id = 2;
+};
+struct PB16 {
+    using real = float;
+    using st = __nv_bfloat16;
+    static constexpr bool dev = true;
+    static constexpr int id = 3;
+};
+
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class S>
+__device__ __forceinline__ S from_f(float v);
+template <>
+__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <class P>
+struct Pop {
+    using R = typename P::real;
+    using S = typename P::st;
+    S* base;
+    float* f0;
+    size_t N;
+    R ref[2];
+    __device__ __forceinline__ Pop(const BoxDev& b) {
+        base = reinterpret_cast<S*>(b.f);
+        f0 = b.f0;
+        N = (size_t)b.N;
+        ref[0] = (R)b.rho_ref[0];
+        ref[1] = (R)b.rho_ref[1];
+    }
+    __device__ __forceinline__ R load(int c, int i, int n) const {
+        if constexpr (P::dev) {
+            if (i == 0) return f0[(size_t)c * N + n];
+            float d = to_f(base[((size_t)c * 18 + (i - 1)) * N + n]);
+            return wgt<float>(i) * (ref[c] + d);
+        } else {
+            return base[((size_t)c * 19 + i) * N + n];
+        }
+    }
+    // stores v, returns the value the next load will see
+    __device__ __forceinline__ R store(int c, int i, int n, R v) const {
+        if constexpr (P::dev) {
+            if (i == 0) {
+                f0[(size_t)c * N + n] = v;
+                return v;
+            }
+            S q = from_f<S>(v * (1.0f / wgt<float>(i)) - ref[c]);
+            base[((size_t)c * 18 + (i - 1)) * N + n] = q;
+            return wgt<float>(i) * (ref[c] + to_f(q));
+        } else {
+            base[((size_t)c * 19 + i) * N + n] = v;
+            return v;
+        }
+    }
+    // the value store(c, i, n, v) would leave, without storing
+    __device__ __forceinline__ R quant(int c, int i, R v) const {
+        if constexpr (P::dev) {
+            if (i == 0) return v;
+            S q = from_f<S>(v * (1.0f / wgt<float>(i)) - ref[c]);
+            return wgt<float>(i) * (ref[c] + to_f(q));
+        } else {
+            return v;
+        }
+    }
+};
+
+template <class P>
+__host__ __device__ constexpr size_t pop_bytes(size_t N) {
+    return P::dev ? (size_t)2 * 18 * N * 2 : (size_t)2 * 19 * N * sizeof(typename P::st);
+}
+
+// ------------------------------------------------------------ helpers
+__device__ __forceinline__ int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+// minimum image of a displacement along an axis of length L
+__device__ __forceinline__ double mimg(double d, double L) {
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+// squared distance without contraction, so that the inside/outside test of
+// a node is decided exactly as in a plain sequential evaluation
+__device__ __forceinline__ double dist2_nc(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ void set_err(int* err, int bits) { atomicOr(err, bits); }
+
+}  // namespace lbp

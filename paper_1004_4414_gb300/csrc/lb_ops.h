@@ -1,0 +1,32 @@
+// lb_ops.h -- launchers of the precision-dependent kernels, one table per
+// population storage type (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include "lb_common.cuh"
+
+namespace lbp {
+
+struct LbOps {
+    int id;
+    size_t real_size;
+    cudaError_t (*setup)();
+    size_t (*step_smem)(int ty);
+    cudaError_t (*step)(int par, int ty, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
+                        Shared sh, int rc, int rn, int rz, int mslot);
+    cudaError_t (*remap_apply)(int par, cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int mslot_cur);
+    cudaError_t (*remap_finish)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc);
+    cudaError_t (*shell_density)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int NP);
+    cudaError_t (*wall_shell)(cudaStream_t st, const BoxDev* boxes, int b, int rc);
+    cudaError_t (*init_pop)(cudaStream_t st, const BoxDev* boxes, int b, const double* rho_field,
+                            const double* u_field, uint64_t s_red, uint64_t s_blue, double noise, int rc,
+                            double* mass_out);
+    cudaError_t (*export_dir)(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, double* out);
+    cudaError_t (*import_dir)(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, const double* in);
+    cudaError_t (*rho_from_pop)(cudaStream_t st, const BoxDev* boxes, int b, int par, int rc, double* out,
+                                double* mass_out);
+    cudaError_t (*obs_partial)(cudaStream_t st, const BoxDev* boxes, int b, int par, double* partials);
+};
+
+extern const LbOps lb_ops_fp64, lb_ops_fp32, lb_ops_fp16, lb_ops_bf16;
+
+}  // namespace lbp

@@ -1,0 +1,636 @@
+// lb_particles.cuh -- particle-side kernels of one time step: cell list and
+// neighbour list, remap of the spheres onto the lattice (cover / uncover,
+// Sec. III and Sec. IV), the virtual fluid of the shell with particle colour
+// (Sec. IV), and the MD update with Hertz contact and lubrication (Sec. III).
+//
+// All kernels work on the particles of every box at once (one launch per
+// phase for the whole batch); a particle knows its box through pbox[].
+#pragma once
+#include "lb_common.cuh"
+#include "lb_step_kernel.cuh"
+
+namespace lbp {
+
+// ------------------------------------------------------------ cell list
+__device__ __forceinline__ int cell_of(const BoxDev& B, const double X[3]) {
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int v = (int)(X[a] / B.cell_len[a]);
+        c[a] = v < 0 ? 0 : (v >= B.nc[a] ? B.nc[a] - 1 : v);
+    }
+    return B.cell_off + c[0] + B.nc[0] * (c[1] + B.nc[1] * c[2]);
+}
+
+// visit every particle in the cells around X (each cell once)
+template <class F>
+__device__ __forceinline__ void for_near(const BoxDev& B, const Shared& sh, const double X[3], F fn) {
+    int c[3], lo[3], nr[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int v = (int)(X[a] / B.cell_len[a]);
+        c[a] = v < 0 ? 0 : (v >= B.nc[a] ? B.nc[a] - 1 : v);
+        if (B.nc[a] >= 3) {
+            lo[a] = c[a] - 1;
+            nr[a] = 3;
+        } else {
+            lo[a] = 0;
+            nr[a] = B.nc[a];
+        }
+    }
+    for (int k2 = 0; k2 < nr[2]; k2++)
+        for (int k1 = 0; k1 < nr[1]; k1++)
+            for (int k0 = 0; k0 < nr[0]; k0++) {
+                const int cc = B.cell_off + wrapi(lo[0] + k0, B.nc[0]) +
+                               B.nc[0] * (wrapi(lo[1] + k1, B.nc[1]) + B.nc[1] * wrapi(lo[2] + k2, B.nc[2]));
+                const int s0 = sh.cell_start[cc], s1 = s0 + sh.cell_count[cc];
+                for (int s = s0; s < s1; s++) fn(sh.cell_list[s]);
+            }
+}
+
+static __global__ void k_step_begin(const BoxDev* __restrict__ boxes, int nb, Shared sh, int total_cells, int mslot_next) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = tid; i < total_cells; i += gridDim.x * blockDim.x) sh.cell_count[i] = 0;
+    if (tid == 0) *sh.ev_count = 0;
+    if (tid < nb) {
+        boxes[tid].mass_acc[mslot_next * 2 + 0] = 0.0;
+        boxes[tid].mass_acc[mslot_next * 2 + 1] = 0.0;
+    }
+}
+
+static __global__ void k_cell_count(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    atomicAdd(&sh.cell_count[cell_of(B, sh.part[p].X)], 1);
+}
+
+// one block per box: exclusive scan of the cell counts (offset by the box's
+// first particle), cursors = starts
+static __global__ void k_cell_scan(const BoxDev* __restrict__ boxes, Shared sh) {
+    const BoxDev& B = boxes[blockIdx.x];
+    const int ncell = B.nc[0] * B.nc[1] * B.nc[2];
+    __shared__ int s_tmp[1024];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) s_carry = B.pstart;
+    __syncthreads();
+    for (int base = 0; base < ncell; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < ncell ? sh.cell_count[B.cell_off + i] : 0;
+        s_tmp[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < blockDim.x; off <<= 1) {
+            int t = threadIdx.x >= off ? s_tmp[threadIdx.x - off] : 0;
+            __syncthreads();
+            s_tmp[threadIdx.x] += t;
+            __syncthreads();
+        }
+        const int incl = s_tmp[threadIdx.x];
+        if (i < ncell) {
+            const int st = s_carry + incl - v;
+            sh.cell_start[B.cell_off + i] = st;
+            sh.cell_cursor[B.cell_off + i] = st;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry += incl;
+        __syncthreads();
+    }
+}
+
+static __global__ void k_cell_fill(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    const int pos = atomicAdd(&sh.cell_cursor[cell_of(B, sh.part[p].X)], 1);
+    sh.cell_list[pos] = p;
+}
+
+// neighbours whose spheres could share or take over a node of p:
+// centre distance <= 2R + 2 (a node owned before the move lies within
+// R + |U| <= R + 1 of the new centre)
+static __global__ void k_nlist(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    const PartState ps = sh.part[p];
+    const double lim = 2.0 * B.radius + 2.0, lim2 = lim * lim;
+    int cnt = 0;
+    for_near(B, sh, ps.X, [&](int q) {
+        if (q == p) return;
+        const PartState& pq = sh.part[q];
+        const double dx = mimg(pq.X[0] - ps.X[0], B.nx), dy = mimg(pq.X[1] - ps.X[1], B.ny),
+                     dz = mimg(pq.X[2] - ps.X[2], B.nz);
+        if (dx * dx + dy * dy + dz * dz <= lim2) {
+            if (cnt < NL_MAX) sh.nlist[(size_t)p * NL_MAX + cnt] = q;
+            cnt++;
+        }
+    });
+    if (cnt > NL_MAX) set_err(sh.err, ERR_OVERFLOW);
+    sh.nlist_n[p] = cnt < NL_MAX ? cnt : NL_MAX;
+}
+
+// ------------------------------------------------------------- remap
+// Warp per particle p: scan the nodes around X_p and record every node whose
+// solid/fluid status or owner changes.  A node belongs to the particle whose
+// centre is nearest among those within R (|x - X|^2 <= R^2, minimum image);
+// ties go to the lower index.  Events: covered (fluid -> p), uncovered
+// (p -> fluid), transfer (q -> p, no fluid involved).
+constexpr int DETECT_WARPS = 4;
+static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    __shared__ double s_nx[DETECT_WARPS][NL_MAX][3];
+    __shared__ int s_nid[DETECT_WARPS][NL_MAX];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * DETECT_WARPS + wib;
+    if (p >= NP) return;  // the whole warp leaves together
+    const int b = sh.pbox[p];
+    const BoxDev& B = boxes[b];
+    const PartState ps = sh.part[p];
+    const double R = B.radius, R2 = R * R;
+    const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
+    const int nn = sh.nlist_n[p];
+    for (int k = lane; k < nn; k += 32) {
+        const int q = sh.nlist[(size_t)p * NL_MAX + k];
+        s_nid[wib][k] = q;
+        for (int a = 0; a < 3; a++) s_nx[wib][k][a] = sh.part[q].X[a];
+    }
+    __syncwarp();
+    const int half = (int)ceil(R) + 2;
+    int lo[3], span[3];
+    const int dims[3] = {B.nx, B.ny, B.nz};
+    for (int a = 0; a < 3; a++) {
+        lo[a] = (int)floor(ps.X[a]) - half;
+        span[a] = 2 * half + 1;
+        if (span[a] > dims[a]) span[a] = dims[a];
+    }
+    const int total = span[0] * span[1] * span[2];
+    const float Rf2o = (float)((R + 1.5) * (R + 1.5));
+    const float R2f = (float)R2;
+    // FP32 distances decide unless they fall within `band` of R^2, where the
+    // FP64 value (evaluated without contraction) decides
+    const float band = (float)(0.02 + 2e-3 * R2);
+    const float Xf[3] = {(float)ps.X[0], (float)ps.X[1], (float)ps.X[2]};
+    const float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
+    auto mimgf = [](float d, float Lx) { return d > 0.5f * Lx ? d - Lx : (d < -0.5f * Lx ? d + Lx : d); };
+    for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        int ev_old = 0, ev_new = 0, node = 0;
+        bool have = false;
+        if (idx < total) {
+            const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+            const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
+            const float fx = mimgf((float)gx - Xf[0], Lf[0]), fy = mimgf((float)gy - Xf[1], Lf[1]),
+                        fz = mimgf((float)gz - Xf[2], Lf[2]);
+            const float d2f = fx * fx + fy * fy + fz * fz;
+            auto exact_d2 = [&](const double* C) {
+                return dist2_nc(mimg((double)gx - C[0], L[0]), mimg((double)gy - C[1], L[1]),
+                                mimg((double)gz - C[2], L[2]));
+            };
+            if (d2f <= Rf2o) {
+                const int n = gx + B.nx * (gy + B.ny * gz);
+                const int own = B.owner[n];
+                if (own != OWN_WALL) {
+                    double d2p = -1.0;
+                    bool inside;
+                    if (fabsf(d2f - R2f) > band) {
+                        inside = d2f < R2f;
+                    } else {
+                        d2p = exact_d2(ps.X);
+                        inside = d2p <= R2;
+                    }
+                    if (inside || own == p) {
+                        bool other = false, anyone = false;
+                        for (int k = 0; k < nn; k++) {
+                            const float ex = mimgf((float)gx - (float)s_nx[wib][k][0], Lf[0]);
+                            const float ey = mimgf((float)gy - (float)s_nx[wib][k][1], Lf[1]);
+                            const float ez = mimgf((float)gz - (float)s_nx[wib][k][2], Lf[2]);
+                            if (ex * ex + ey * ey + ez * ez > R2f + band) continue;
+                            const double d2q = exact_d2(s_nx[wib][k]);
+                            if (d2q <= R2) {
+                                anyone = true;
+                                if (inside) {
+                                    if (d2p < 0.0) d2p = exact_d2(ps.X);
+                                    const int q = s_nid[wib][k];
+                                    if (d2q < d2p || (d2q == d2p && q < p)) other = true;
+                                }
+                            }
+                        }
+                        const bool claim = inside && !other;
+                        if (claim && own != p) {
+                            have = true;
+                            ev_old = own;
+                            ev_new = p;
+                        } else if (!claim && own == p && !anyone) {
+                            have = true;
+                            ev_old = p;
+                            ev_new = OWN_FLUID;
+                        }
+                        node = n;
+                    }
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, have);
+        if (m) {
+            int basepos = 0;
+            if (lane == 0) basepos = atomicAdd(sh.ev_count, __popc(m));
+            basepos = __shfl_sync(0xffffffffu, basepos, 0);
+            if (have) {
+                const int pos = basepos + __popc(m & ((1u << lane) - 1u));
+                if (pos < sh.ev_cap) sh.events[pos] = make_int4(node, b, ev_old, ev_new);
+                else set_err(sh.err, ERR_OVERFLOW);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int ev_total(const Shared& sh) {
+    const int c = *sh.ev_count;
+    return c < sh.ev_cap ? c : sh.ev_cap;
+}
+
+// new status of every event node; the old owner is kept in evmark (+3)
+static __global__ void k_remap_mark(const BoxDev* __restrict__ boxes, Shared sh) {
+    const int cnt = ev_total(sh);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const int4 ev = sh.events[e];
+        const BoxDev& B = boxes[ev.y];
+        B.evmark[ev.x] = ev.z + 3;
+        B.owner[ev.x] = ev.w;
+        B.flags[ev.x] = ev.w != OWN_FLUID ? FL_SOLID : 0;
+    }
+}
+
+__device__ __forceinline__ int nbr_index(const BoxDev& B, int n, int dx, int dy, int dz) {
+    const int x = n % B.nx, y = (n / B.nx) % B.ny, z = n / (B.nx * B.ny);
+    return wrapi(x + dx, B.nx) + B.nx * (wrapi(y + dy, B.ny) + B.ny * wrapi(z + dz, B.nz));
+}
+__device__ __forceinline__ int ev_old_owner(const BoxDev& B, int n) {
+    const int m = B.evmark[n];
+    return m ? m - 3 : B.owner[n];
+}
+__device__ __forceinline__ bool old_solid(const BoxDev& B, int n) {
+    const int m = B.evmark[n];
+    if (m) return (m - 3) != OWN_FLUID;
+    return B.flags[n] & FL_SOLID;
+}
+__device__ __forceinline__ bool new_solid(const BoxDev& B, int n) { return B.flags[n] & FL_SOLID; }
+// a marked node whose solid/fluid status changed (not a transfer)
+__device__ __forceinline__ bool status_event(const BoxDev& B, int n) {
+    const int m = B.evmark[n];
+    if (!m) return false;
+    return ((m - 3) != OWN_FLUID) != (bool)(B.flags[n] & FL_SOLID);
+}
+
+// refill of an uncovered node (Eqs. eqn_rho_neu and masscorr): mean density
+// of the neighbours that were fluid, times the mass-correction factor; the
+// surface velocity of the particle that left it.
+template <class R>
+struct Refill {
+    R rho[2];
+    R us[3];
+    double r[3];
+};
+template <class R>
+__device__ Refill<R> refill_of(const BoxDev& B, const Shared& sh, int n, int q, const R* rcur, int mslot_cur) {
+    Refill<R> o;
+    double corr[2] = {1.0, 1.0};
+    if (B.c0 != 0.0) {
+        const double rsum = B.rho_init[0] + B.rho_init[1];
+        for (int c = 0; c < 2; c++)
+            corr[c] = 1.0 - B.c0 * (rsum / B.rho_init[c]) * (B.mass_acc[mslot_cur * 2 + c] - B.mass0[c]) / (double)B.N;
+    }
+    for (int c = 0; c < 2; c++) {
+        R sum = R(0);
+        int cnt = 0;
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            const int m = nbr_index(B, n, cx(i), cy(i), cz(i));
+            if (!old_solid(B, m)) {
+                sum += rcur[(size_t)c * B.N + m];
+                cnt++;
+            }
+        }
+        const R rbar = cnt ? sum / (R)cnt : (R)B.rho_init[c];
+        o.rho[c] = (R)((double)rbar * corr[c]);
+    }
+    const int x = n % B.nx, y = (n / B.nx) % B.ny, z = n / (B.nx * B.ny);
+    const PartState ps = sh.part[q];
+    o.r[0] = mimg((double)x - ps.X[0], B.nx);
+    o.r[1] = mimg((double)y - ps.X[1], B.ny);
+    o.r[2] = mimg((double)z - ps.X[2], B.nz);
+    o.us[0] = (R)(ps.U[0] + ps.W[1] * o.r[2] - ps.W[2] * o.r[1]);
+    o.us[1] = (R)(ps.U[1] + ps.W[2] * o.r[0] - ps.W[0] * o.r[2]);
+    o.us[2] = (R)(ps.U[2] + ps.W[0] * o.r[1] - ps.W[1] * o.r[0]);
+    return o;
+}
+
+__device__ __forceinline__ void add_force_torque(const Shared& sh, int p, const double r[3], const double F[3]) {
+    double t[3];
+    cross3(r, F, t);
+    for (int a = 0; a < 3; a++) {
+        atomicAdd(&sh.force[(size_t)p * 6 + a], F[a]);
+        atomicAdd(&sh.force[(size_t)p * 6 + 3 + a], t[a]);
+    }
+}
+
+__device__ __forceinline__ void node_rel(const BoxDev& B, const Shared& sh, int n, int p, double r[3]) {
+    const int x = n % B.nx, y = (n / B.nx) % B.ny, z = n / (B.nx * B.ny);
+    const PartState& ps = sh.part[p];
+    r[0] = mimg((double)x - ps.X[0], B.nx);
+    r[1] = mimg((double)y - ps.X[1], B.ny);
+    r[2] = mimg((double)z - ps.X[2], B.nz);
+}
+
+// Cover / uncover.  PAR is the parity of the coming fused step.  Before an
+// even step each node holds its populations in its own slots.  Before an
+// odd step the population of a node that streams in from neighbour z sits
+// in z's slot when both were fluid and in the node's own slot otherwise;
+// when the status of a link end changes, the link's two slots are
+// rearranged so the odd step finds every population where the new status
+// says it is.  The link is handled once: by its lower-index end when both
+// ends changed.
+template <class P, int PAR>
+static __global__ void k_remap_apply(const BoxDev* __restrict__ boxes, Shared sh, int rc, int mslot_cur) {
+    using R = typename P::real;
+    const int cnt = ev_total(sh);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const int4 ev = sh.events[e];
+        const int w = ev.x, old = ev.z, nw = ev.w;
+        if (old != OWN_FLUID && nw != OWN_FLUID) continue;  // transfer between particles
+        const BoxDev& B = boxes[ev.y];
+        const Pop<P> pop(B);
+        const R* rcur = reinterpret_cast<const R*>(B.rho[rc]);
+        const bool covered = (old == OWN_FLUID);
+        double mom_w[3] = {0, 0, 0};
+        Refill<R> rf;
+        if (!covered) {
+            rf = refill_of<R>(B, sh, w, old, rcur, mslot_cur);
+            sh.ev_rho[(size_t)e * 2 + 0] = (double)rf.rho[0];
+            sh.ev_rho[(size_t)e * 2 + 1] = (double)rf.rho[1];
+            atomicAdd(&sh.counters[ev.y * 2 + 1], 1ull);
+        } else {
+            atomicAdd(&sh.counters[ev.y * 2 + 0], 1ull);
+        }
+        if (PAR == 0) {
+            for (int c = 0; c < 2; c++) {
+                if (covered) {
+#pragma unroll
+                    for (int i = 1; i < 19; i++) {
+                        const R v = pop.load(c, i, w);
+                        mom_w[0] += (double)v * cx(i);
+                        mom_w[1] += (double)v * cy(i);
+                        mom_w[2] += (double)v * cz(i);
+                    }
+                } else {
+                    R resid = R(0);
+#pragma unroll
+                    for (int i = 1; i < 19; i++) {
+                        const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
+                        resid += fe - pop.store(c, i, w, fe);
+                    }
+                    pop.store(c, 0, w, feq_rt<R>(0, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
+                }
+            }
+        } else {
+            const int wx = w % B.nx, wy = (w / B.nx) % B.ny, wz = w / (B.nx * B.ny);
+            for (int i = 1; i < 19; i++) {
+                const int z = wrapi(wx + cx(i), B.nx) + B.nx * (wrapi(wy + cy(i), B.ny) + B.ny * wrapi(wz + cz(i), B.nz));
+                const bool zev = status_event(B, z);
+                if (zev && z < w) continue;
+                const bool wo = covered, wn = !covered;
+                const bool zo = !old_solid(B, z), zn = !new_solid(B, z);
+                Refill<R> rz;
+                const bool z_unc = zev && !zo && zn;
+                if (z_unc) rz = refill_of<R>(B, sh, z, ev_old_owner(B, z), rcur, mslot_cur);
+                double mom_z[3] = {0, 0, 0};
+                for (int c = 0; c < 2; c++) {
+                    // a = w, population f_opp(i)(w); b = z, population f_i(z);
+                    // slots sa = A[opp(i)][w], sb = A[i][z]
+                    R va = R(0), vb = R(0);
+                    if (wo) va = zo ? pop.load(c, i, z) : pop.load(c, opp(i), w);
+                    else va = feq_rt<R>(opp(i), rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
+                    if (zo) vb = wo ? pop.load(c, opp(i), w) : pop.load(c, i, z);
+                    else if (zn) vb = feq_rt<R>(i, rz.rho[c], rz.us[0], rz.us[1], rz.us[2]);
+                    if (wo && !wn) {
+                        mom_w[0] += (double)va * cx(opp(i));
+                        mom_w[1] += (double)va * cy(opp(i));
+                        mom_w[2] += (double)va * cz(opp(i));
+                    }
+                    if (zo && !zn) {
+                        mom_z[0] += (double)vb * cx(i);
+                        mom_z[1] += (double)vb * cy(i);
+                        mom_z[2] += (double)vb * cz(i);
+                    }
+                    if (wn && zn) {
+                        pop.store(c, i, z, va);
+                        pop.store(c, opp(i), w, vb);
+                    } else if (wn) {
+                        pop.store(c, opp(i), w, va);
+                    } else if (zn) {
+                        pop.store(c, i, z, vb);
+                    }
+                }
+                if (zo && !zn && zev) {
+                    const int pz = B.owner[z];
+                    double r[3];
+                    node_rel(B, sh, z, pz, r);
+                    add_force_torque(sh, pz, r, mom_z);
+                }
+            }
+            if (!covered) {
+                for (int c = 0; c < 2; c++) {
+                    R resid = R(0);
+#pragma unroll
+                    for (int i = 1; i < 19; i++) {
+                        const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
+                        resid += fe - pop.quant(c, i, fe);
+                    }
+                    pop.store(c, 0, w, feq_rt<R>(0, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
+                }
+            }
+        }
+        if (covered) {
+            double r[3];
+            node_rel(B, sh, w, nw, r);
+            add_force_torque(sh, nw, r, mom_w);
+        } else {
+            // the particle loses the momentum of the created fluid
+            // (Eq. eqn_ladd_vernichtenunderzeugen, sign from conservation)
+            const double rs = (double)rf.rho[0] + (double)rf.rho[1];
+            const double F[3] = {-rs * (double)rf.us[0], -rs * (double)rf.us[1], -rs * (double)rf.us[2]};
+            add_force_torque(sh, old, rf.r, F);
+        }
+    }
+}
+
+__device__ __forceinline__ void shell_update(const BoxDev& B, int n) {
+    const uint8_t f = B.flags[n];
+    if (!(f & FL_SOLID)) return;
+    bool shl = false;
+#pragma unroll
+    for (int i = 1; i < 19; i++)
+        if (!(B.flags[nbr_index(B, n, cx(i), cy(i), cz(i))] & FL_SOLID)) shl = true;
+    B.flags[n] = FL_SOLID | (shl ? FL_SHELL : 0);
+}
+
+template <class R>
+static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared sh, int rc) {
+    const int cnt = ev_total(sh);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const int4 ev = sh.events[e];
+        const BoxDev& B = boxes[ev.y];
+        const int w = ev.x;
+        R* rcur = reinterpret_cast<R*>(B.rho[rc]);
+        if (ev.z == OWN_FLUID) {
+            rcur[w] = R(0);
+            rcur[(size_t)B.N + w] = R(0);
+        } else if (ev.w == OWN_FLUID) {
+            rcur[w] = (R)sh.ev_rho[(size_t)e * 2 + 0];
+            rcur[(size_t)B.N + w] = (R)sh.ev_rho[(size_t)e * 2 + 1];
+        }
+        B.evmark[w] = 0;
+        shell_update(B, w);
+#pragma unroll
+        for (int i = 1; i < 19; i++) shell_update(B, nbr_index(B, w, cx(i), cy(i), cz(i)));
+    }
+}
+
+// ------------------------------------------------------- virtual fluid
+// Shell nodes get the mean density of their fluid neighbours plus the
+// particle colour on red (Delta rho > 0) or blue (Delta rho < 0) (Sec. IV).
+template <class R>
+static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh, int rc, int NP) {
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 4 + wib;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    const PartState ps = sh.part[p];
+    R* rcur = reinterpret_cast<R*>(B.rho[rc]);
+    const double R_ = B.radius;
+    const double col = sh.color[p];
+    const int half = (int)ceil(R_) + 1;
+    int lo[3], span[3];
+    const int dims[3] = {B.nx, B.ny, B.nz};
+    for (int a = 0; a < 3; a++) {
+        lo[a] = (int)floor(ps.X[a]) - half;
+        span[a] = 2 * half + 1;
+        if (span[a] > dims[a]) span[a] = dims[a];
+    }
+    const int total = span[0] * span[1] * span[2];
+    const float lim = (float)((R_ + 0.5) * (R_ + 0.5));
+    for (int idx = lane; idx < total; idx += 32) {
+        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+        const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
+        const float dx = (float)mimg((double)gx - ps.X[0], B.nx), dy = (float)mimg((double)gy - ps.X[1], B.ny),
+                    dz = (float)mimg((double)gz - ps.X[2], B.nz);
+        if (dx * dx + dy * dy + dz * dz > lim) continue;
+        const int n = gx + B.nx * (gy + B.ny * gz);
+        if (!(B.flags[n] & FL_SHELL) || B.owner[n] != p) continue;
+        R s0 = R(0), s1 = R(0);
+        int cnt = 0;
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            const int m = wrapi(gx + cx(i), B.nx) + B.nx * (wrapi(gy + cy(i), B.ny) + B.ny * wrapi(gz + cz(i), B.nz));
+            if (!(B.flags[m] & FL_SOLID)) {
+                s0 += rcur[m];
+                s1 += rcur[(size_t)B.N + m];
+                cnt++;
+            }
+        }
+        R r0 = s0 / (R)cnt, r1 = s1 / (R)cnt;
+        if (col > 0.0) r0 += (R)col;
+        else if (col < 0.0) r1 += (R)(-col);
+        rcur[n] = r0;
+        rcur[(size_t)B.N + n] = r1;
+    }
+}
+
+// shell nodes of static walls (colour 0); only boxes that have walls
+template <class R>
+static __global__ void k_wall_shell(const BoxDev* __restrict__ boxes, int b, int rc) {
+    const BoxDev& B = boxes[b];
+    R* rcur = reinterpret_cast<R*>(B.rho[rc]);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        if (B.owner[n] != OWN_WALL || !(B.flags[n] & FL_SHELL)) continue;
+        R s0 = R(0), s1 = R(0);
+        int cnt = 0;
+        for (int i = 1; i < 19; i++) {
+            const int m = nbr_index(B, n, cx(i), cy(i), cz(i));
+            if (!(B.flags[m] & FL_SOLID)) {
+                s0 += rcur[m];
+                s1 += rcur[(size_t)B.N + m];
+                cnt++;
+            }
+        }
+        rcur[n] = s0 / (R)cnt;
+        rcur[(size_t)B.N + n] = s1 / (R)cnt;
+    }
+}
+
+// --------------------------------------------------------------- MD
+// Pair force on p from q, r = X_p - X_q (minimum image):
+//   Hertz (Eq. eq:hertz): -dV/dr = 5/2 K (2R - r)^{3/2} along r_hat, r < 2R;
+//   lubrication (Eq. eqn_ladd_lubrikation): -6 pi nu R^4/(2R)^2 r_hat
+//   [r_hat.(U_p - U_q)] (1/h - 1/h_c) for gap h < h_c, h clamped at h_min.
+__device__ __forceinline__ void pair_force(const BoxDev& B, const PartState& a, const PartState& b, double F[3]) {
+    const double R = B.radius;
+    double r[3] = {mimg(a.X[0] - b.X[0], B.nx), mimg(a.X[1] - b.X[1], B.ny), mimg(a.X[2] - b.X[2], B.nz)};
+    const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (d <= 0.0) return;
+    const double rh[3] = {r[0] / d, r[1] / d, r[2] / d};
+    if (d < 2.0 * R) {
+        const double ov = 2.0 * R - d;
+        const double mag = 2.5 * B.k_hertz * ov * sqrt(ov);
+        for (int k = 0; k < 3; k++) F[k] += mag * rh[k];
+    }
+    const double h = d - 2.0 * R;
+    if (h < B.lub_cut) {
+        const double he = h < B.lub_min ? B.lub_min : h;
+        const double du = rh[0] * (a.U[0] - b.U[0]) + rh[1] * (a.U[1] - b.U[1]) + rh[2] * (a.U[2] - b.U[2]);
+        const double mag = -6.0 * M_PI * B.nu * R * R * R * R / (4.0 * R * R) * du * (1.0 / he - 1.0 / B.lub_cut);
+        for (int k = 0; k < 3; k++) F[k] += mag * rh[k];
+    }
+}
+
+// coupling forces of the step are saved, then the pair forces are added
+static __global__ void k_md_forces(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    double* fp = &sh.force[(size_t)p * 6];
+    double F[3] = {fp[0], fp[1], fp[2]};
+    for (int a = 0; a < 6; a++) sh.force_last[(size_t)p * 6 + a] = fp[a];
+    const PartState ps = sh.part[p];
+    for_near(B, sh, ps.X, [&](int q) {
+        if (q == p) return;
+        pair_force(B, ps, sh.part[q], F);
+    });
+    fp[0] = F[0];
+    fp[1] = F[1];
+    fp[2] = F[2];
+}
+
+// leap-frog: U += F/m, omega += T/J, X += U (periodic); accumulators zeroed
+static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    double* fp = &sh.force[(size_t)p * 6];
+    PartState ps = sh.part[p];
+    if (!B.fixed) {
+        const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
+        for (int a = 0; a < 3; a++) {
+            ps.U[a] += fp[a] / B.mass;
+            ps.W[a] += fp[3 + a] / B.inertia;
+            double xn = ps.X[a] + ps.U[a];
+            xn -= L[a] * floor(xn / L[a]);
+            if (xn >= L[a]) xn -= L[a];
+            ps.X[a] = xn;
+        }
+        if (!(ps.U[0] * ps.U[0] + ps.U[1] * ps.U[1] + ps.U[2] * ps.U[2] < 1.0)) set_err(sh.err, ERR_FAST_PARTICLE);
+        sh.part[p] = ps;
+    }
+    for (int a = 0; a < 6; a++) fp[a] = 0.0;
+}
+
+}  // namespace lbp

@@ -1,0 +1,105 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/lbpart.h declares, sizes workspaces and rejects invalid parameters
+without touching a GPU."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbpart.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1004_4414_gb300 import build, binding
+
+    build.build()
+    return binding.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for f in ("lb_create", "lb_init_from_seed", "lb_step", "lb_observables", "lb_destroy"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1004_4414_gb300 import binding
+
+    names = declared_functions()
+    assert set(names) == set(binding.ABI_FUNCTIONS)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_workspace_bytes_scale_with_precision(lib):
+    from paper_1004_4414_gb300 import binding
+
+    sizes = {}
+    for prec in ("fp64", "fp32", "fp16", "bf16"):
+        p = binding.make_params(nx=64, ny=64, nz=64, precision=prec)
+        sizes[prec] = binding.workspace_bytes([p])
+    N = 64 ** 3
+    # populations dominate: 2 x 19 x 8 / 4 bytes, or 2 x 18 x 2 + 2 x 4 bytes
+    assert sizes["fp64"] - sizes["fp32"] >= 2 * 19 * 4 * N
+    assert sizes["fp16"] == sizes["bf16"]
+    assert sizes["fp32"] - sizes["fp16"] >= (2 * 19 * 4 - 2 * 18 * 2 - 2 * 4) * N
+
+
+def test_invalid_parameters_rejected(lib):
+    from paper_1004_4414_gb300 import binding
+
+    n = C.c_size_t(0)
+    for bad in (dict(nx=0), dict(tau=(0.5, 1.0)), dict(precision=7), dict(reserved=1), dict(radius=0.0),
+                dict(rho_init=(0.0, 0.7))):
+        p = binding.make_params(**bad)
+        arr = (binding.LbParams * 1)(p)
+        assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_EINVAL
+    # mixed precisions in one batch are rejected
+    arr = (binding.LbParams * 2)(binding.make_params(precision="fp32"), binding.make_params(precision="fp16"))
+    assert lib.lb_workspace_bytes(arr, 2, C.byref(n)) == binding.LB_EINVAL
+    # create without a workspace is rejected before any CUDA call
+    h = C.c_void_p()
+    arr = (binding.LbParams * 1)(binding.make_params())
+    assert lib.lb_create(arr, 1, None, 0, None, C.byref(h)) == binding.LB_EINVAL
+    assert lib.lb_step(None, 1) == binding.LB_EINVAL
+
+
+def test_strerror(lib):
+    assert lib.lb_strerror(0) == b"ok"
+    assert b"unstable" in lib.lb_strerror(-4)
+
+
+def test_params_struct_matches_header():
+    """The ctypes mirror lists the header's lb_params fields in order."""
+    from paper_1004_4414_gb300 import binding
+
+    src = open(HEADER).read()
+    body = src[src.index("typedef struct {"):src.index("} lb_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl or decl.startswith("typedef"):
+            decl = decl.replace("typedef struct {", "").strip()
+        if not decl:
+            continue
+        parts = decl.split(None, 1)
+        for v in parts[1].split(","):
+            names.append(re.sub(r"\[.*\]", "", v).strip())
+    assert names == [f[0] for f in binding.LbParams._fields_]
+
+
+def test_contact_angle_mapping_default_is_nan():
+    from paper_1004_4414_gb300 import binding
+
+    assert math.isnan(binding.make_params().contact_angle_deg)

@@ -1,0 +1,306 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Both sides start from the same seeded inputs (lbinputs) and are compared
+element by element: populations, node owners (bit-exact), particle state.
+FP64 mode must agree to rounding (1e-12 absolute on populations of order
+0.05, a few hundred steps); FP32 within 1e-5 relative after 100 steps on a
+non-chaotic case; 16-bit deviation storage within the tolerance derived in
+the test from its unit roundoff.
+"""
+import numpy as np
+import pytest
+
+import lbinputs
+from oracle import ref
+
+pytestmark = pytest.mark.gpu
+
+GPU_ONLY = ("precision", "contact_angle_deg")
+ORACLE_ONLY = ("virtual_fluid", "seed")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1004_4414_gb300 import build
+
+    build.build()
+    ref.lib()
+
+
+def pair(precision="fp64", **params):
+    from paper_1004_4414_gb300 import Simulation
+
+    o = ref.Oracle(**{k: v for k, v in params.items() if k not in GPU_ONLY})
+    s = Simulation(dict({k: v for k, v in params.items() if k not in ORACLE_ONLY}, precision=precision))
+    return o, s
+
+
+def compare(o, s, box=0, ftol=1e-12, ptol=1e-12, rel=False):
+    a, b = s.export_state(box), o.get_state()
+    assert np.array_equal(a["owner"], b["owner"]), "owners differ at %d nodes" % np.sum(a["owner"] != b["owner"])
+    if rel:
+        scale = np.maximum(np.abs(b["f"]), 1e-3)
+        err = np.max(np.abs(a["f"] - b["f"]) / scale)
+    else:
+        err = np.max(np.abs(a["f"] - b["f"]))
+    assert err < ftol, "populations differ by %g" % err
+    if b["particles"].size:
+        perr = np.max(np.abs(a["particles"] - b["particles"]))
+        assert perr < ptol, "particles differ by %g" % perr
+    assert a["meta"][0] == b["meta"][0]
+    return err
+
+
+@pytest.mark.parametrize("shape", [(16, 12, 10), (40, 9, 7), (8, 8, 8), (33, 17, 5)])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_fluid_only_fp64(shape, steps):
+    """Two-component Shan-Chen fluid without particles; ragged tiles, both
+    AA parities, boxes smaller than a tile (periodic wrap inside one CTA)."""
+    nx, ny, nz = shape
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=0, g_br=0.15, tau=(1.0, 0.8))
+    rho = lbinputs.mixture(shape, amp=0.05, seed=1)
+    o.init_fields(rho)
+    s.init_fields(0, rho)
+    compare(o, s)
+    o.step(steps)
+    s.step(steps)
+    compare(o, s)
+
+
+@pytest.mark.parametrize("vel_mode", [0, 1])
+def test_fluid_with_velocity_field_and_body_force(vel_mode):
+    shape = (20, 16, 12)
+    nx, ny, nz = shape
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=0, g_br=0.1, vel_mode=vel_mode, body_force=(1e-5, -2e-5, 0.0))
+    rho = lbinputs.mixture(shape, amp=0.05, seed=3)
+    u = 0.02 * np.random.default_rng(4).standard_normal((3, nx * ny * nz))
+    o.init_fields(rho, u=u)
+    s.init_fields(0, rho, u=u)
+    o.step(9)
+    s.step(9)
+    compare(o, s)
+
+
+@pytest.mark.parametrize("steps", [1, 4, 11])
+def test_static_particles_fp64(steps):
+    """Fixed spheres: bounce-back, shell virtual fluid with colour, Shan-Chen
+    force on the particles."""
+    shape = (24, 20, 18)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 3.5, 3, seed=7, min_gap=1.0, vmax=0.02, wmax=0.01)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=3, radius=3.5, g_br=0.12, color=0.04, fixed_particles=1)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=8)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    o.step(steps)
+    s.step(steps)
+    compare(o, s)
+    Fo, To = o.particle_forces()
+    Fs, Ts = s.particle_forces()
+    assert np.max(np.abs(Fo - Fs)) < 1e-10 and np.max(np.abs(To - Ts)) < 1e-9
+
+
+@pytest.mark.parametrize("vel_mode,c0", [(0, 0.0), (1, 5.0)])
+def test_moving_particles_with_events_fp64(vel_mode, c0):
+    """Moving, rotating spheres: cover / uncover on both AA parities,
+    momentum exchange, MD with Hertz and lubrication, optional mass
+    correction; owners must match bit for bit."""
+    shape = (26, 22, 20)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 3.3, 5, seed=12, min_gap=0.4, vmax=0.06, wmax=0.03)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=5, radius=3.3, g_br=0.12, color=-0.03,
+                particle_density=3.0, vel_mode=vel_mode, mass_corr_c0=c0)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=13)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    for k in range(6):
+        o.step(5)
+        s.step(5)
+        compare(o, s, ftol=1e-11, ptol=1e-11)
+    ob, sb = o.observe(), s.observables()
+    assert ob["n_cover"] > 0 and ob["n_uncover"] > 0
+    assert (ob["n_cover"], ob["n_uncover"]) == (sb["n_cover"], sb["n_uncover"])
+    assert np.allclose(ob["mass"], sb["mass"], rtol=1e-13)
+    assert np.allclose(ob["mom_fluid"] + ob["mom_part"], sb["mom_fluid"] + sb["mom_part"], atol=1e-10)
+
+
+def test_colors_per_particle_fp64():
+    shape = (24, 24, 16)
+    P = lbinputs.spheres(shape, 3.0, 4, seed=21, min_gap=1.0, vmax=0.03)
+    o, s = pair(nx=24, ny=24, nz=16, n_particles=4, radius=3.0, g_br=0.15, particle_density=2.0)
+    col = np.array([0.05, -0.04, 0.0, 0.02])
+    o.set_colors(col)
+    s.set_colors(0, col)
+    rho = lbinputs.lamellae(shape, axis=2, rho_major=0.7, rho_minor=0.05)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    o.step(13)
+    s.step(13)
+    compare(o, s, ftol=1e-11, ptol=1e-11)
+
+
+def test_seeded_init_matches_oracle():
+    """lb_init_from_seed and the oracle's seeded init implement the same
+    SplitMix64 streams and random sequential addition independently."""
+    params = dict(nx=32, ny=32, nz=32, n_particles=16, radius=4.0, noise_amp=0.01, rho_init=(0.7, 0.7))
+    o, s = pair(**params)
+    o.init_from_seed(1)
+    s.init_from_seed(1)
+    a, b = s.export_state(), o.get_state()
+    assert np.array_equal(a["particles"], b["particles"])
+    assert np.array_equal(a["owner"], b["owner"])
+    assert np.max(np.abs(a["f"] - b["f"])) < 1e-15
+
+
+def test_config1_32cube_200_steps_fp64():
+    """32^3, two components 0.7 / 0.7 with seeded noise, g = 0.08, 16 spheres
+    R = 4 at random non-overlapping positions, neutral wetting, 200 steps of
+    the FP64 method (particle density 2, i.e. 1.43 times the fluid density as
+    in the paper's runs)."""
+    params = dict(nx=32, ny=32, nz=32, n_particles=16, radius=4.0, noise_amp=0.01, rho_init=(0.7, 0.7),
+                  g_br=0.08, particle_density=2.0)
+    o, s = pair(**params)
+    o.init_from_seed(1)
+    s.init_from_seed(1)
+    for k in range(4):
+        o.step(50)
+        s.step(50)
+        compare(o, s, ftol=1e-10, ptol=1e-10)
+    sb = s.observables()
+    assert sb["error"] == 0 and sb["n_cover"] > 0
+
+
+def test_import_export_roundtrip_and_odd_parity():
+    """A state exported by the oracle at an odd step is imported into the
+    GPU (AA odd-parity layout) and stepped on; export returns it exactly."""
+    shape = (22, 18, 14)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 3.0, 3, seed=31, min_gap=0.5, vmax=0.05, wmax=0.02)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=3, radius=3.0, g_br=0.12, color=0.02, particle_density=2.5)
+    o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=32), particles=P)
+    o.step(7)
+    st = o.get_state()
+    s.import_state(0, st)
+    back = s.export_state(0)
+    assert np.array_equal(back["f"], st["f"]) and np.array_equal(back["owner"], st["owner"])
+    assert np.array_equal(back["particles"], st["particles"])
+    o.step(9)
+    s.step(9)
+    compare(o, s, ftol=1e-11, ptol=1e-11)
+
+
+def test_walls_poiseuille_fp64():
+    nz = 18
+    walls = np.full((nz, 4, 3), -1, np.int32)
+    walls[0] = walls[nz - 1] = -2
+    o, s = pair(nx=3, ny=4, nz=nz, n_particles=0, g_br=0.0, tau=(0.9, 0.9), body_force=(1e-5, 0.0, 0.0))
+    rho = np.full((2, 3 * 4 * nz), 0.5)
+    o.init_fields(rho, walls=walls.reshape(-1))
+    s.init_fields(0, rho, walls=walls.reshape(-1))
+    o.step(300)
+    s.step(300)
+    compare(o, s)
+
+
+@pytest.mark.parametrize("ty,cz", [(4, 3), (8, 1), (16, 5), (8, 64)])
+def test_tilings_agree(ty, cz):
+    shape = (37, 29, 23)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 3.5, 4, seed=41, min_gap=0.5, vmax=0.04, wmax=0.02)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=4, radius=3.5, g_br=0.12, color=0.03, particle_density=2.0)
+    s.set_tiling(ty, cz)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=42)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    o.step(12)
+    s.step(12)
+    compare(o, s, ftol=1e-11, ptol=1e-11)
+
+
+def test_batched_boxes_fp64():
+    """Uneven boxes stepped together in one launch per phase."""
+    from paper_1004_4414_gb300 import Simulation
+
+    specs = [dict(nx=16, ny=16, nz=16, n_particles=2, radius=3.0, color=0.03),
+             dict(nx=24, ny=20, nz=12, n_particles=3, radius=2.5, color=-0.02, g_br=0.1),
+             dict(nx=12, ny=12, nz=20, n_particles=0)]
+    s = Simulation([dict(sp, precision="fp64", particle_density=2.0) for sp in specs])
+    oracles = []
+    for b, sp in enumerate(specs):
+        shape = (sp["nx"], sp["ny"], sp["nz"])
+        P = lbinputs.spheres(shape, sp.get("radius", 5.0), sp["n_particles"], seed=50 + b, min_gap=0.5,
+                             vmax=0.04, wmax=0.02) if sp["n_particles"] else None
+        rho = lbinputs.mixture(shape, amp=0.04, seed=60 + b)
+        o = ref.Oracle(**dict(sp, particle_density=2.0))
+        o.init_fields(rho, particles=P)
+        s.init_fields(b, rho, particles=P)
+        oracles.append(o)
+    for o in oracles:
+        o.step(10)
+    s.step(10)
+    for b, o in enumerate(oracles):
+        compare(o, s, box=b, ftol=1e-11, ptol=1e-11)
+
+
+# ------------------------------------------------------------------- FP32
+def test_fp32_non_chaotic_100_steps():
+    """FP32 populations within 1e-5 relative of FP64 after 100 steps on a
+    non-chaotic case (a lamella with a resting particle, below the spinodal
+    coupling)."""
+    shape = (32, 24, 20)
+    nx, ny, nz = shape
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (15.3, 11.7, 9.6)
+    o, s = pair("fp32", nx=nx, ny=ny, nz=nz, n_particles=1, radius=4.0, g_br=0.05, color=0.02,
+                fixed_particles=1)
+    rho = lbinputs.lamellae(shape, axis=2, rho_major=0.6, rho_minor=0.3)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    o.step(100)
+    s.step(100)
+    compare(o, s, ftol=1e-5, rel=True)
+
+
+def test_fp32_mass_conserved():
+    shape = (48, 40, 36)
+    P = lbinputs.spheres(shape, 4.0, 6, seed=71, min_gap=1.0)
+    from paper_1004_4414_gb300 import Simulation
+
+    s = Simulation(dict(nx=48, ny=40, nz=36, n_particles=6, radius=4.0, g_br=0.1, color=0.03,
+                        fixed_particles=1, precision="fp32"))
+    s.init_fields(0, lbinputs.mixture(shape, amp=0.05, seed=72), particles=P)
+    m0 = s.observables()["mass"]
+    s.step(200)
+    ob = s.observables()
+    assert ob["error"] == 0
+    assert np.all(np.abs(ob["mass"] - m0) / m0 < 1e-6)
+
+
+@pytest.mark.parametrize("prec,eps", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_deviation_storage(prec, eps):
+    """16-bit deviation storage: each stored population carries a relative
+    error of at most the unit roundoff u of its deviation d = f/zeta - rho_ref,
+    so a population deviates by <= zeta |d| u per step; the FP32 rest
+    population absorbs the rounding so mass is conserved to FP32 level."""
+    shape = (32, 24, 20)
+    nx, ny, nz = shape
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (15.3, 11.7, 9.6)
+    o, s = pair(prec, nx=nx, ny=ny, nz=nz, n_particles=1, radius=4.0, g_br=0.05, color=0.02,
+                fixed_particles=1, rho_init=(0.45, 0.45))
+    rho = lbinputs.lamellae(shape, axis=2, rho_major=0.6, rho_minor=0.3)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    m0 = s.observables()["mass"]
+    steps = 50
+    o.step(steps)
+    s.step(steps)
+    a, b = s.export_state(), o.get_state()
+    assert np.array_equal(a["owner"], b["owner"])
+    # |d| <= 0.6 here; errors of successive steps are damped by BGK (tau = 1
+    # replaces f by f^eq of the local moments), so the bound is a few roundoffs
+    tol = 8 * 0.6 * eps * (1.0 / 18)
+    err = np.max(np.abs(a["f"] - b["f"]))
+    assert err < tol, (err, tol)
+    ob = s.observables()
+    assert np.all(np.abs(ob["mass"] - m0) / m0 < 2e-6)
