@@ -1,0 +1,377 @@
+"""Throughput of the particle-laden two-component Shan-Chen LB step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload c256|c128|c512|c32|batch] [--precision fp32|fp16|bf16]
+                [--variants]
+
+One "step" is one time step of the whole hot path over the workload: particle
+remap with cover/uncover, shell virtual fluid, fused stream-collide with the
+Shan-Chen force and moving bounce-back, particle force reduction and MD.
+The metric is MLUPS (lattice node updates per second, both components,
+every node of the box counted once per step) and the fraction of the
+measured HBM roofline reached by the fused stream-collide kernel.
+
+Workloads (seeded, synthetic; the paper's runs are synthetic as well):
+  c256  256^3, fluid ratio 60:40 of total density 0.7, alpha = 0.20, R = 5,
+        contact angle 77 deg (colour -0.0294), g = 0.08 (default)
+  c128  128^3, 50:50, alpha = 0.15, R = 5, 90 deg
+  c512  512^3, 50:50, alpha = 0.20, R = 5, 90 deg
+  c32   32^3, 0.7 / 0.7, 16 spheres R = 4 (parity configuration)
+  batch 64 boxes with edges from {48, 64, 96, 128}, contact angle 60-120 deg,
+        alpha 0.05-0.25, fluid ratio 50:50-70:30, one launch per phase
+
+For N > 1 (torchrun) every rank runs its own copy of the workload on its
+GPU (independent problems, no communication): weak scaling, value = all
+ranks' node updates / max-over-ranks time.  --impl reference times the FP64
+CPU oracle (the only other implementation of the method) on a bounded
+sample of the same workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PROFILES = os.path.join(ROOT, "profiles")
+KERNEL_SOURCES = ("lb_step_kernel.cuh", "lb_common.cuh")
+
+
+def workload_params(name, precision="fp32"):
+    base = dict(tau=(1.0, 1.0), g_br=0.08, rho0=1.0, sc_weight=(2.0, 1.0), noise_amp=0.01, radius=5.0,
+                particle_density=1.0, k_hertz=100.0, precision=precision)
+    if name == "c256":
+        return [dict(base, nx=256, ny=256, nz=256, n_particles=-1, volume_fraction=0.20,
+                     rho_init=(0.42, 0.28), contact_angle_deg=77.0)], 3
+    if name == "c128":
+        return [dict(base, nx=128, ny=128, nz=128, n_particles=-1, volume_fraction=0.15,
+                     rho_init=(0.35, 0.35), contact_angle_deg=90.0)], 2
+    if name == "c512":
+        return [dict(base, nx=512, ny=512, nz=512, n_particles=-1, volume_fraction=0.20,
+                     rho_init=(0.35, 0.35), contact_angle_deg=90.0)], 5
+    if name == "c32":
+        return [dict(base, nx=32, ny=32, nz=32, n_particles=16, radius=4.0, rho_init=(0.7, 0.7),
+                     particle_density=2.0, contact_angle_deg=90.0)], 1
+    if name == "batch":
+        import numpy as np
+
+        rng = np.random.default_rng(4)
+        boxes = []
+        for b in range(64):
+            L = int(rng.choice([48, 64, 96, 128]))
+            theta = float(rng.uniform(60.0, 120.0))
+            alpha = float(rng.uniform(0.05, 0.25))
+            red = float(rng.uniform(0.5, 0.7))
+            boxes.append(dict(base, nx=L, ny=L, nz=L, n_particles=-1, volume_fraction=alpha,
+                              rho_init=(0.7 * red, 0.7 * (1.0 - red)), contact_angle_deg=theta))
+        return boxes, 4
+    raise ValueError(name)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1004_4414_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, precision):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(PROFILES, "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get("%s_%s" % (workload, precision))
+        if e and e.get("kernel_hash") == kernel_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks during the timed region (200 ms period)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                   f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id(device):
+    """nvidia-smi addresses GPUs by UUID regardless of CUDA_VISIBLE_DEVICES."""
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(device).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(device.index or 0)
+
+
+def fused_bytes(sim, precision):
+    """Algorithmic bytes of one launch of the fused kernel: every fluid node
+    reads and writes 2 x 19 populations (FP32: 4 B each; 16-bit deviation
+    storage: 18 x 2 B + a 4 B rest slot per component), every node reads and
+    writes 2 densities (4 B each) and reads 1 flag byte."""
+    pop = {"fp32": 2 * 19 * 4, "fp64": 2 * 19 * 8, "fp16": 2 * (18 * 2 + 4), "bf16": 2 * (18 * 2 + 4)}[precision]
+    rs = 8 if precision == "fp64" else 4
+    total = 0
+    for b in range(sim.nb):
+        ob = sim.observables(b)
+        total += ob["n_fluid"] * pop * 2 + sim.n_nodes[b] * (2 * rs * 2 + 1)
+    return total
+
+
+def run_ours(args, rank, world, device):
+    import numpy as np
+    import torch
+
+    from paper_1004_4414_gb300 import Simulation, build
+
+    build.build()
+    boxes, seed = workload_params(args.workload, args.precision)
+    sim = Simulation(boxes, device=device)
+    sim.init_from_seed(seed + 1000 * rank)
+    nodes = sum(sim.n_nodes)
+    stream = sim.stream
+    # warm-up: the autotuner times candidate block shapes on these boxes,
+    # then W plain steps
+    from paper_1004_4414_gb300.autotune import autotune
+
+    tiling, _ = autotune(sim)
+    sim.step(args.warmup)
+    sim.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-timed region: inputs resident in HBM (the state is larger
+    # than the 129 MB L2, so no flush is needed between steps)
+    sim.set_profiling(True)
+    barrier()
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id(device)) as clk:
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    fused_ms, fused_n, total_launches = sim.kernel_time()
+    sim.set_profiling(False)
+    sim.sync()
+    clocks = clk.summary()
+    t_ms = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t_ms, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_ms.item())
+    value = nodes * world * args.steps / (ms_max * 1e-3) / 1e6
+
+    # ---- roofline of the fused kernel
+    bytes_launch = fused_bytes(sim, args.precision)
+    avg_ms = fused_ms / max(fused_n, 1)
+    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+
+    # ---- end to end through the C ABI with host buffers: import the state
+    # from pinned host memory, K steps, export it back
+    st = sim.export_state(0) if sim.nb == 1 else None
+    e2e = None
+    if st is not None:
+        pin_f = torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy()
+        pin_f[...] = st["f"]
+        st_in = dict(st, f=pin_f)
+        out_f = torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy()
+        barrier()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        sim.import_state(0, st_in)
+        sim.step(args.steps)
+        sim.sync()
+        sim.export_state(0, f_out=out_f)
+        t1 = time.perf_counter()
+        barrier()
+        dt = torch.tensor([t1 - t0], dtype=torch.float64, device=device)
+        if world > 1:
+            torch.distributed.all_reduce(dt, op=torch.distributed.ReduceOp.MAX)
+        h2d = st["f"].nbytes + st["owner"].nbytes + st["particles"].nbytes
+        e2e = {"value": nodes * world * args.steps / float(dt.item()) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": h2d / args.steps,
+               "what": "lb_import_state (pinned host state) + lb_step(K) + lb_export_state (pinned host)"}
+    ob = sim.observables(0)
+    return dict(value=value, ms=ms_max, fused_ms=avg_ms, fused_n=fused_n, bytes=bytes_launch, achieved=achieved,
+                peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=total_launches, nodes=nodes,
+                n_particles=sum(sim.n_particles), error=ob["error"], n_fluid=ob["n_fluid"], tiling=tiling)
+
+
+def oracle_sample(workload, budget_s=12.0):
+    """Time the FP64 oracle on the host cores on the first box of the
+    workload: init, then steps until the budget is used (at least one)."""
+    from oracle import ref
+
+    boxes, seed = workload_params(workload, "fp64")
+    p = {k: v for k, v in boxes[0].items() if k not in ("precision", "contact_angle_deg")}
+    theta = boxes[0].get("contact_angle_deg", 90.0)
+    p["color"] = (theta - 90.0) / 442.0 if theta is not None and not math.isnan(theta) else 0.0
+    o = ref.Oracle(**p)
+    o.init_from_seed(seed)
+    N = p["nx"] * p["ny"] * p["nz"]
+    steps, spent = 0, 0.0
+    while steps == 0 or spent < budget_s:
+        t0 = time.perf_counter()
+        o.step(1)
+        spent += time.perf_counter() - t0
+        steps += 1
+        if spent > 3 * budget_s:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=N * steps / spent / 1e6, steps=steps, seconds=spent, cores=cores, N=N,
+                sample="%d step(s) of box 0 of %s (%d^3 nodes, %d particles) after seeded init" %
+                       (steps, workload, p["nx"], o.np))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c256", choices=["c256", "c128", "c512", "c32", "batch"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    metric = "MLUPS and % of HBM roofline: FP32 vs BF16/FP16-storage vs batched, same GPU"
+    names = {"c256": "256^3 60:40 alpha=0.20 R=5 theta=77deg", "c128": "128^3 50:50 alpha=0.15 R=5 theta=90deg",
+             "c512": "512^3 50:50 alpha=0.20 R=5 theta=90deg", "c32": "32^3 16 spheres R=4",
+             "batch": "64 boxes {48,64,96,128}^3 theta 60-120 alpha 0.05-0.25 ratio 50:50-70:30"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        r = oracle_sample(args.workload)
+        line = {"impl": "reference", "metric": metric, "value": r["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["seconds"] / r["steps"] * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": names[args.workload], "precision": "fp64 (oracle)"},
+                "cpu_baseline": {"value": r["value"], "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
+                                 "sample": r["sample"]},
+                "e2e": {"value": r["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    r = run_ours(args, rank, world, device)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        c = oracle_sample(args.workload)
+        cpu = {"value": c["value"], "unit": "MLUPS", "cores": c["cores"], "kind": "oracle", "sample": c["sample"]}
+    traffic = ncu_traffic(args.workload, args.precision)
+    line = {
+        "metric": metric, "value": r["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-dev/f32", "bf16": "bf16-dev/f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": names[args.workload], "precision": args.precision, "nodes": r["nodes"],
+                   "fluid_nodes": r["n_fluid"], "particles": r["n_particles"],
+                   "l2": "state larger than L2 (no flush needed)",
+                   "tiling": {"ty": r["tiling"][0], "cz": r["tiling"][1]}},
+        "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
+                     "frac": r["achieved"] / r["peak"], "traffic": traffic,
+                     "peak_kind": r["peak_kind"], "kernel": "k_step (fused stream-collide)",
+                     "bytes_per_launch": r["bytes"], "launch_ms": r["fused_ms"]},
+        "cpu_baseline": cpu,
+        "e2e": r["e2e"],
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "device_error": r["error"],
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -160,7 +160,9 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
 /* Densities rho[2][N] of one box (sum of populations, 0 on solid nodes). */
 int lb_export_rho(lb_handle* h, int32_t box, double* rho);
 
-/* Per-particle colour Delta rho of one box (host array of n_particles). */
+/* Per-particle colour Delta rho of one box (host array of n_particles).
+ * lb_init_from_seed, lb_init_fields and lb_import_state give every particle
+ * the box colour, so call this after them. */
 int lb_set_particle_colors(lb_handle* h, int32_t box, const double* colors);
 
 /* Fluid-coupling force and torque on each particle of one box in the last

@@ -248,9 +248,16 @@ class Simulation:
                     n_uncover=o.n_uncover, n_fluid=o.n_fluid, n_solid=o.n_solid, error=o.error,
                     n_particles=o.n_particles)
 
-    def export_state(self, box=0, f=True):
+    def export_state(self, box=0, f=True, f_out=None):
+        """Canonical state; f_out: optional C-contiguous float64 array
+        (2, 19, N) to fill (e.g. pinned host memory)."""
         N = self.n_nodes[box]
-        fa = np.zeros((2, 19, N)) if f else None
+        if f_out is not None:
+            if f_out.dtype != np.float64 or f_out.size != 2 * 19 * N or not f_out.flags.c_contiguous:
+                raise ValueError("f_out must be a C-contiguous float64 array of 2*19*N values")
+            fa = f_out
+        else:
+            fa = np.zeros((2, 19, N)) if f else None
         owner = np.zeros(N, np.int32)
         parts = np.zeros((max(self.n_particles[box], 1), 9))
         meta = np.zeros(4)

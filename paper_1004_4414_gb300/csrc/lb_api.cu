@@ -7,7 +7,7 @@
 #include <cstring>
 #include <vector>
 
-#include "../../include/lbpart.h"
+#include "lbpart.h"
 #include "lb_aux.cuh"
 #include "lb_ops.h"
 
@@ -196,6 +196,7 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     Shared sh{};
     const int NPa = NP > 0 ? NP : 1;
     sh.part = cv.take<PartState>(NPa);
+    sh.partf = cv.take<PartStateF>(NPa);
     sh.force = cv.take<double>((size_t)NPa * 6);
     sh.force_last = cv.take<double>((size_t)NPa * 6);
     sh.color = cv.take<double>(NPa);
@@ -485,6 +486,8 @@ int init_box(lb_handle* h, int b, const double* parts_host, const int32_t* walls
         CK(cudaMemcpyAsync(h->sh.color + B.pstart, col.data(), sizeof(double) * np, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(h->sh.force + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * np, st));
         CK(cudaMemsetAsync(h->sh.force_last + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * np, st));
+        k_part_to_float<<<(np + 255) / 256, 256, 0, st>>>(h->sh, B.pstart, np);
+        CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));
     }
     // walls (owner -2) or fluid
@@ -814,6 +817,8 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
         CK(cudaMemcpyAsync(h->sh.color + B.pstart, col.data(), sizeof(double) * B.np, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(h->sh.force + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * B.np, st));
         CK(cudaMemsetAsync(h->sh.force_last + (size_t)B.pstart * 6, 0, sizeof(double) * 6 * B.np, st));
+        k_part_to_float<<<(B.np + 255) / 256, 256, 0, st>>>(h->sh, B.pstart, B.np);
+        CK(cudaGetLastError());
     }
     std::vector<int32_t> own(N);
     h->has_walls[box] = 0;
@@ -899,6 +904,14 @@ int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz) {
     h->cz = cz;
     int rc = build_tiles(h);
     if (rc != LB_OK) return rc;
+    // The next step adds into its density buffer at the new tiling's edge
+    // nodes, which the previous step only zeroed for the old tiling.
+    if (h->initialised) {
+        for (int b = 0; b < h->nb; b++)
+            CK(cudaMemsetAsync(h->hbox[b].rho[(h->t + 1) % 3], 0, (size_t)2 * h->hbox[b].N * h->ops->real_size,
+                               h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
     destroy_graphs(h);
     if (h->initialised && h->stream) return build_graphs(h);
     return LB_OK;

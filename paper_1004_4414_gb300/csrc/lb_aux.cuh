@@ -112,7 +112,7 @@ static __global__ void k_init_pop(const BoxDev* __restrict__ boxes, int b, const
                 resid += fe - q;
                 sent += q;
             }
-            const R q0 = pop.store(c, 0, n, feq_rt<R>(0, r, ux, uy, uz) + resid);
+            const R q0 = pop.store(c, 0, n, feq_rest<R>(r, ux, uy, uz) + resid);
             sent += q0;
             rcur[(size_t)c * B.N + n] = sent;
             if (c == 0) m0 += (double)sent;

@@ -44,6 +44,18 @@ constexpr int ERR_UNSTABLE = 1, ERR_OVERFLOW = 2, ERR_FAST_PARTICLE = 4;
 struct PartState {        // per particle, FP64
     double X[3], U[3], W[3];
 };
+struct PartStateF {       // FP32 copy read by the FP32 fluid kernels (GB300's FP64 rate is low)
+    float X[3], U[3], W[3];
+};
+// particle record the fluid kernel of real type R reads
+template <class R>
+struct PartOf {
+    using type = PartStateF;
+};
+template <>
+struct PartOf<double> {
+    using type = PartState;
+};
 
 // ------------------------------------------------------------ descriptors
 // Everything a kernel needs to know about one box.  Lives in device memory.
@@ -85,6 +97,7 @@ struct TileDev {                // one CTA work item of the fused step kernel
 // Global per-step work lists and scratch (device memory).
 struct Shared {
     PartState* part;            // [NP]
+    PartStateF* partf;          // [NP] FP32 copy of part, refreshed after every MD update
     double* force;              // [NP][6] F, T accumulators
     double* force_last;         // [NP][6] coupling forces of the last step
     double* color;              // [NP]
@@ -133,6 +146,16 @@ __device__ __forceinline__ R feq_rt(int i, R rho, R ux, R uy, R uz) {
     R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
     R t = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu + R(4.5) * cu * cu * cu - R(4.5) * uu * cu;
     return wgt<R>(i) * rho * t;
+}
+
+// rest equilibrium as rho minus the 18 moving ones: equal to Eq. Equil in
+// exact arithmetic, and sum_i f^eq_i = rho holds in finite precision too
+template <class R>
+__device__ __forceinline__ R feq_rest(R rho, R ux, R uy, R uz) {
+    R s = R(0);
+#pragma unroll
+    for (int i = 1; i < 19; i++) s += feq_rt<R>(i, rho, ux, uy, uz);
+    return rho - s;
 }
 
 // ----------------------------------------------------- storage policies
@@ -212,6 +235,36 @@ struct Pop {
             base[((size_t)c * 19 + i) * N + n] = v;
             return v;
         }
+    }
+    // array of direction i (>= 1 for deviation storage) of component c
+    __device__ __forceinline__ S* dir(int c, int i) const {
+        if constexpr (P::dev) return base + ((size_t)c * 18 + (i - 1)) * N;
+        else return base + ((size_t)c * 19 + i) * N;
+    }
+    // load / store through a pointer into the array of direction i (or of
+    // opp(i): opposite directions share weight and reference density)
+    __device__ __forceinline__ R ld(const S* p, int c, int i) const {
+        if constexpr (P::dev) return wgt<float>(i) * (ref[c] + to_f(*p));
+        else return *p;
+    }
+    __device__ __forceinline__ R st(S* p, int c, int i, R v) const {
+        if constexpr (P::dev) {
+            const S q = from_f<S>(v * (1.0f / wgt<float>(i)) - ref[c]);
+            *p = q;
+            return wgt<float>(i) * (ref[c] + to_f(q));
+        } else {
+            *p = v;
+            return v;
+        }
+    }
+    __device__ __forceinline__ R ld_rest(int c, int n) const {
+        if constexpr (P::dev) return f0[(size_t)c * N + n];
+        else return base[(size_t)c * 19 * N + n];
+    }
+    __device__ __forceinline__ R st_rest(int c, int n, R v) const {
+        if constexpr (P::dev) f0[(size_t)c * N + n] = v;
+        else base[(size_t)c * 19 * N + n] = v;
+        return v;
     }
     // the value store(c, i, n, v) would leave, without storing
     __device__ __forceinline__ R quant(int c, int i, R v) const {

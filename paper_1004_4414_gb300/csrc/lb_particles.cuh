@@ -388,7 +388,7 @@ static __global__ void k_remap_apply(const BoxDev* __restrict__ boxes, Shared sh
                         const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
                         resid += fe - pop.store(c, i, w, fe);
                     }
-                    pop.store(c, 0, w, feq_rt<R>(0, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
+                    pop.store(c, 0, w, feq_rest<R>(rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
                 }
             }
         } else {
@@ -445,7 +445,7 @@ static __global__ void k_remap_apply(const BoxDev* __restrict__ boxes, Shared sh
                         const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
                         resid += fe - pop.quant(c, i, fe);
                     }
-                    pop.store(c, 0, w, feq_rt<R>(0, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
+                    pop.store(c, 0, w, feq_rest<R>(rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
                 }
             }
         }
@@ -592,6 +592,20 @@ __device__ __forceinline__ void pair_force(const BoxDev& B, const PartState& a, 
     }
 }
 
+// FP32 copy of particles [p0, p0 + n) for the FP32 fluid kernels
+static __global__ void k_part_to_float(Shared sh, int p0, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const PartState ps = sh.part[p0 + k];
+    PartStateF pf;
+    for (int a = 0; a < 3; a++) {
+        pf.X[a] = (float)ps.X[a];
+        pf.U[a] = (float)ps.U[a];
+        pf.W[a] = (float)ps.W[a];
+    }
+    sh.partf[p0 + k] = pf;
+}
+
 // coupling forces of the step are saved, then the pair forces are added
 static __global__ void k_md_forces(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -629,6 +643,13 @@ static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared s
         }
         if (!(ps.U[0] * ps.U[0] + ps.U[1] * ps.U[1] + ps.U[2] * ps.U[2] < 1.0)) set_err(sh.err, ERR_FAST_PARTICLE);
         sh.part[p] = ps;
+        PartStateF pf;
+        for (int a = 0; a < 3; a++) {
+            pf.X[a] = (float)ps.X[a];
+            pf.U[a] = (float)ps.U[a];
+            pf.W[a] = (float)ps.W[a];
+        }
+        sh.partf[p] = pf;
     }
     for (int a = 0; a < 6; a++) fp[a] = 0.0;
 }

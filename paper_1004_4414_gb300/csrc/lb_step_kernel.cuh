@@ -12,39 +12,102 @@
 // (Eq. eqn_shan_chen_particle).
 //
 // GB300 design:
-//   * Populations are kept in place with the AA pattern: on even steps a node
-//     reads its own 19 slots and writes the post-collision values to the
-//     opposite slots of itself; on odd steps it reads f_i from slot opp(i) of
-//     x - c_i and writes f*_j to slot j of x + c_j.  A population whose
-//     stream target is solid is reflected into slot opp(j) of the node on
-//     both parities, which is exactly where the next step reads it.  Memory
-//     per population is one slot; every slot is read once and written once
-//     per step.
-//   * A CTA owns a column tile of 32 x TY nodes (one warp per x row, so all
-//     global traffic is coalesced along x) and marches through a chunk of z
-//     planes.  Psi and the node flags of the tile plus a one-node ring are
-//     staged in a three-plane shared-memory ring buffer, so each density
-//     value is loaded from HBM/L2 once per tile.
-//   * The Shan-Chen force needs Psi of all neighbours at the same time
-//     level.  Instead of a second pass over the populations, the kernel
-//     produces rho(t+1) itself: each post-streaming value is added (shared
-//     memory atomics) to a three-plane accumulator at its destination node.
-//     Nodes whose whole stencil lies inside the tile are written with plain
-//     stores; tile-edge and ring nodes are added with global atomics into a
-//     density field that was zeroed at those nodes during the previous step
-//     (ring of three density buffers: current, next, to-zero).
+//   * Populations stay in place with the AA pattern.  Even steps: a node
+//     reads its own 19 slots and writes f*_j to slot opp(j) of itself.  Odd
+//     steps: it reads f_i from slot opp(i) of x - c_i and writes f*_j to slot
+//     j of x + c_j.  A population whose stream target is solid is reflected
+//     into slot opp(j) of the node itself on both parities, which is where
+//     the next step reads it.  Each slot is read once and written once per
+//     step.  Every load and store has its address selected first, so the
+//     common path has no branches; neighbour offsets are wrap-aware and
+//     computed once per thread.
+//   * Reflected links are rare (nodes next to particles).  The main path
+//     writes every post-collision value, a reflected one without the
+//     moving-wall term; then the warp takes its (node, direction) links as
+//     work items, 32 at a time, adds the wall term and the momentum exchange
+//     and sums the particle forces.
+//   * A CTA owns a column tile of 32 x TY nodes (one warp per x row: all
+//     population traffic is coalesced along x) and marches through a chunk
+//     of z planes.  Psi and the node flags of the tile plus a one-node ring
+//     sit in a three-plane shared-memory ring buffer.
+//   * The force needs Psi of every neighbour at the same time level, so the
+//     kernel produces rho(t+1) itself from the values it stores.  The values
+//     a node sends are summed by destination group (dy, dz); the x shift is
+//     a warp shuffle, the y shift a shared-memory exchange between rows and
+//     the z shift free (each thread marches along its own column and keeps
+//     the partial sums of three planes in registers).  Nodes whose whole
+//     stencil lies in the tile are written with plain stores; tile-edge and
+//     ring nodes are added with global reductions into a density buffer that
+//     was zeroed at exactly those nodes during the previous step (ring of
+//     three density buffers: current, next, to-zero).
 //   * Particle forces are summed per node (all reflected links of a node
-//     give forces parallel to c_j, so the torque of the node is
-//     (x - X_p) x F), reduced across the warp per particle with shuffles,
-//     and added to FP64 accumulators with one atomic per (warp, particle).
+//     carry forces parallel to c_j, so the node's torque is (x - X_p) x F),
+//     reduced across the warp per particle with shuffles, summed per CTA in
+//     a shared-memory table, and added to the FP64 accumulators once per
+//     (CTA, particle) -- conversions to FP64 are slow on GB300.
 #pragma once
+#include <type_traits>
+
 #include "lb_common.cuh"
 
 namespace lbp {
 
-// Sum (F, T) of the lanes that share a particle key, one FP64 atomic per
-// distinct key in the warp.  All 32 lanes of the warp must call it.
-__device__ __forceinline__ void warp_particle_add(int key, const double v[6], double* force) {
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Per-CTA table of particle forces and torques, summed in the kernel's
+// precision in shared memory and added to the FP64 accumulators once per
+// (CTA, particle) when the CTA finishes.  Open addressing on the particle
+// index; a full table falls back to direct FP64 atomics.
+constexpr int PT_SLOTS = 128;
+template <class R>
+struct PartTable {
+    int key[PT_SLOTS];
+    R val[PT_SLOTS][6];
+};
+
+template <class R>
+__device__ __forceinline__ void pt_init(PartTable<R>& t, int tid, int nthr) {
+    for (int i = tid; i < PT_SLOTS; i += nthr) {
+        t.key[i] = -1;
+#pragma unroll
+        for (int a = 0; a < 6; a++) t.val[i][a] = R(0);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void pt_add(PartTable<R>& t, int p, const R v[6], double* force) {
+    int h = p & (PT_SLOTS - 1);
+    for (int probe = 0; probe < PT_SLOTS; probe++) {
+        const int k = atomicCAS(&t.key[h], -1, p);
+        if (k == -1 || k == p) {
+#pragma unroll
+            for (int a = 0; a < 6; a++) atomicAdd(&t.val[h][a], v[a]);
+            return;
+        }
+        h = (h + 1) & (PT_SLOTS - 1);
+    }
+#pragma unroll
+    for (int a = 0; a < 6; a++) atomicAdd(&force[(size_t)p * 6 + a], (double)v[a]);
+}
+
+template <class R>
+__device__ __forceinline__ void pt_flush(const PartTable<R>& t, double* force, int tid, int nthr) {
+    for (int i = tid; i < PT_SLOTS * 6; i += nthr) {
+        const int s = i / 6, a = i - s * 6;
+        const int p = t.key[s];
+        if (p >= 0 && t.val[s][a] != R(0)) atomicAdd(&force[(size_t)p * 6 + a], (double)t.val[s][a]);
+    }
+}
+
+// Sum (F, T) of the lanes that share a particle key and add it to the CTA's
+// particle table, one entry per distinct key in the warp.  All 32 lanes of
+// the warp must call it.
+template <class R>
+__device__ __forceinline__ void warp_particle_add(int key, const R v[6], PartTable<R>& pt, double* force) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     unsigned pending = __ballot_sync(FULL, key >= 0);
@@ -53,343 +116,649 @@ __device__ __forceinline__ void warp_particle_add(int key, const double v[6], do
         const int k = __shfl_sync(FULL, key, leader);
         const bool mine = (key == k);
         const unsigned grp = __ballot_sync(FULL, mine);
-        double s[6];
+        R s[6];
 #pragma unroll
-        for (int a = 0; a < 6; a++) s[a] = mine ? v[a] : 0.0;
+        for (int a = 0; a < 6; a++) s[a] = mine ? v[a] : R(0);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
             for (int a = 0; a < 6; a++) s[a] += __shfl_xor_sync(FULL, s[a], off);
-        if (lane == leader)
-#pragma unroll
-            for (int a = 0; a < 6; a++) atomicAdd(&force[(size_t)k * 6 + a], s[a]);
+        if (lane == leader) pt_add<R>(pt, k, s, force);
         pending &= ~grp;
     }
 }
 
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
-    o[0] = a[1] * b[2] - a[2] * b[1];
-    o[1] = a[2] * b[0] - a[0] * b[2];
-    o[2] = a[0] * b[1] - a[1] * b[0];
+// Psi = rho0 (1 - exp(-rho / rho0)); irho0 = 1 / rho0
+template <class R>
+__device__ __forceinline__ R psi_of(R rho, R rho0, R irho0) {
+    if constexpr (sizeof(R) == 8) return rho0 * (1.0 - exp(-rho * irho0));
+    else return rho0 * (1.0f - expf(-rho * irho0));
 }
 
 template <class R>
-__device__ __forceinline__ R psi_of(R rho, R rho0) {
-    if constexpr (sizeof(R) == 8) return rho0 * (1.0 - exp(-rho / rho0));
-    else return rho0 * (1.0f - expf(-rho / rho0));
+__device__ __forceinline__ const typename PartOf<R>::type* part_ptr(const Shared& sh) {
+    if constexpr (sizeof(R) == 8) return sh.part;
+    else return sh.partf;
 }
 
-// shared memory of one CTA, in elements of R
+template <class R>
+__device__ __forceinline__ R mimg_r(R d, R L) {
+    return d > R(0.5) * L ? d - L : (d < -R(0.5) * L ? d + L : d);
+}
+
+template <class R>
+__device__ __forceinline__ void red_add(R* p, R v) {
+    atomicAdd(p, v);
+}
+
+// Destination groups of the density scatter: (dy, dz) of a direction.
+//   g: 0 (0,0) 1 (+1,0) 2 (-1,0) 3 (0,+1) 4 (0,-1) 5 (+1,+1) 6 (-1,-1)
+//      7 (+1,-1) 8 (-1,+1)
+__host__ __device__ constexpr int grp_of(int i) {
+    constexpr int g[19] = {0, 0, 0, 1, 2, 3, 4, 1, 2, 2, 1, 3, 4, 4, 3, 5, 6, 7, 8};
+    return g[i];
+}
+__host__ __device__ constexpr int grp_dy(int g) {
+    constexpr int v[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+    return v[g];
+}
+__host__ __device__ constexpr int grp_dz(int g) {
+    constexpr int v[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+    return v[g];
+}
+// groups with dy != 0 go through the shared-memory row exchange: index 0..5
+__host__ __device__ constexpr int yb_of(int g) {
+    constexpr int v[9] = {-1, 0, 1, -1, -1, 2, 3, 4, 5};
+    return v[g];
+}
+
+// lattice vectors for a direction known only at run time (rare paths)
+static __constant__ signed char kC[19][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
+                                             {0, 0, 1},   {0, 0, -1},  {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},
+                                             {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                             {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1}};
+
+// Per-warp scratch of the reflected-link pass (shared memory).
+template <class R>
+struct LinkScratch {
+    int lane[32];  // node (lane) of each link item of the current batch
+    int dir[32];   // direction of each link item
+    R dself[32][2];   // change of what each node sends to itself, per component
+    R dresid[32][2];  // change of the rounding residual (deviation storage)
+};
+
+// Reflected links of a warp's nodes.  Every population f*_j whose target
+// x + c_j is solid was stored in slot opp(j) of x without the wall term;
+// here each (node, j) link of the warp is one work item, 32 per batch: the
+// stored value gets the moving-wall term b = f*_j - 6 zeta_j rho^c
+// (u_s . c_j), u_s the particle's surface velocity at the link midpoint
+// x + c_j / 2, and the particle receives (2 f*_j - 6 zeta_j rho^c u_s . c_j)
+// c_j with torque r x F about its centre (r to the link midpoint).  Static
+// walls (owner -2) reflect without wall term or force.  All 32 lanes call it.
+template <class P>
+__device__ __forceinline__ void reflect_warp(const Pop<P>& pop, LinkScratch<typename P::real>& ls, unsigned smask,
+                                             int n, int x, int y, int z, int nx, int ny, int nz, int oxm, int oxp,
+                                             int oym, int oyp, int ozm, int ozp, typename P::real rho0_,
+                                             typename P::real rho1_, const int32_t* __restrict__ owner,
+                                             const typename PartOf<typename P::real>::type* __restrict__ parts,
+                                             PartTable<typename P::real>& pt, double* force) {
+    using R = typename P::real;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(smask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - cnt;
+    ls.dself[lane][0] = ls.dself[lane][1] = R(0);
+    ls.dresid[lane][0] = ls.dresid[lane][1] = R(0);
+    for (int base = 0; base < total; base += 32) {
+        // place this lane's items of the batch [base, base + 32)
+        if (excl < base + 32 && excl + cnt > base) {
+            unsigned m = smask;
+            for (int k = excl; m; k++) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                if (k >= base && k < base + 32) {
+                    ls.lane[k - base] = lane;
+                    ls.dir[k - base] = j;
+                }
+            }
+        }
+        __syncwarp();
+        const bool has = base + lane < total;
+        const int L = has ? ls.lane[lane] : lane;
+        const int j = has ? ls.dir[lane] : 0;
+        // node data of the owning lane
+        const int nL = __shfl_sync(FULL, n, L), xL = __shfl_sync(FULL, x, L), yL = __shfl_sync(FULL, y, L);
+        const int oxmL = __shfl_sync(FULL, oxm, L), oxpL = __shfl_sync(FULL, oxp, L);
+        const int oymL = __shfl_sync(FULL, oym, L), oypL = __shfl_sync(FULL, oyp, L);
+        const R r0L = __shfl_sync(FULL, rho0_, L), r1L = __shfl_sync(FULL, rho1_, L);
+        int key = -1;
+        R v[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+        if (has) {
+            const int jx = kC[j][0], jy = kC[j][1], jz = kC[j][2];
+            const int oj = (j & 1) ? j + 1 : j - 1;
+            const int noff = (jx < 0 ? oxmL : (jx > 0 ? oxpL : 0)) + (jy < 0 ? oymL : (jy > 0 ? oypL : 0)) +
+                             (jz < 0 ? ozm : (jz > 0 ? ozp : 0));
+            const int p = owner[nL + noff];
+            if (p >= 0) {
+                const auto& ps = parts[p];
+                const R d0 = mimg_r<R>((R)xL + R(0.5) * (R)jx - (R)ps.X[0], (R)nx);
+                const R d1 = mimg_r<R>((R)yL + R(0.5) * (R)jy - (R)ps.X[1], (R)ny);
+                const R d2 = mimg_r<R>((R)z + R(0.5) * (R)jz - (R)ps.X[2], (R)nz);
+                const R W0 = (R)ps.W[0], W1 = (R)ps.W[1], W2 = (R)ps.W[2];
+                const R usx = (R)ps.U[0] + W1 * d2 - W2 * d1;
+                const R usy = (R)ps.U[1] + W2 * d0 - W0 * d2;
+                const R usz = (R)ps.U[2] + W0 * d1 - W1 * d0;
+                const R cu6 = R(6) * ((jx * jx + jy * jy + jz * jz == 1) ? wgt<R>(1) : wgt<R>(7)) *
+                              (usx * (R)jx + usy * (R)jy + usz * (R)jz);
+                R mag = R(0);
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const R wall = cu6 * (c == 0 ? r0L : r1L);
+                    typename P::st* ptr = pop.dir(c, oj) + nL;
+                    const R fs = pop.ld(ptr, c, oj);
+                    if (wall != R(0)) {
+                        const R b = fs - wall;
+                        const R q = pop.st(ptr, c, oj, b);
+                        atomicAdd(&ls.dself[L][c], q - fs);
+                        if constexpr (P::dev) atomicAdd(&ls.dresid[L][c], b - q);
+                    }
+                    mag += R(2) * fs - wall;
+                }
+                const R F0 = mag * (R)jx, F1 = mag * (R)jy, F2 = mag * (R)jz;
+                key = p;
+                v[0] = F0;
+                v[1] = F1;
+                v[2] = F2;
+                v[3] = d1 * F2 - d2 * F1;
+                v[4] = d2 * F0 - d0 * F2;
+                v[5] = d0 * F1 - d1 * F0;
+            }
+        }
+        warp_particle_add<R>(key, v, pt, force);
+        __syncwarp();
+    }
+    __syncwarp();
+}
+
+// Shan-Chen force of a shell node onto its particle (Eq. eqn_shan_chen_particle)
+// is computed in the fused kernel; its torque arm (x - X_p) and the node
+// torque of the momentum exchange use this helper.
+template <class R, class PT>
+__device__ __forceinline__ void node_torque(const PT& ps, int x, int y, int z, int nx, int ny, int nz, const R F[3],
+                                            R out[6]) {
+    const R rr0 = mimg_r<R>((R)x - (R)ps.X[0], (R)nx);
+    const R rr1 = mimg_r<R>((R)y - (R)ps.X[1], (R)ny);
+    const R rr2 = mimg_r<R>((R)z - (R)ps.X[2], (R)nz);
+    out[0] = F[0];
+    out[1] = F[1];
+    out[2] = F[2];
+    out[3] = rr1 * F[2] - rr2 * F[1];
+    out[4] = rr2 * F[0] - rr0 * F[2];
+    out[5] = rr0 * F[1] - rr1 * F[0];
+}
+
 template <class R, int TY>
 struct StepSmem {
     static constexpr int W2 = 34, H2 = TY + 2, PLANE = W2 * H2;
-    static constexpr size_t bytes = (size_t)2 * 3 * 2 * PLANE * sizeof(R) + (size_t)3 * PLANE + 64;
+    static constexpr size_t psi_elems = (size_t)3 * 2 * PLANE;
+    static constexpr size_t yb_elems = (size_t)6 * 2 * TY * 32;
+    static constexpr size_t bytes = (psi_elems + yb_elems) * sizeof(R) + (size_t)3 * PLANE + 64;
 };
 
 template <class P, int PAR, int TY>
-static __global__ void __launch_bounds__(32 * TY)
+static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     k_step(const BoxDev* __restrict__ boxes, const TileDev* __restrict__ tiles, Shared sh, int rc, int rn, int rz,
            int mslot) {
     using R = typename P::real;
+    using S = typename P::st;
     using SM = StepSmem<R, TY>;
     constexpr int W2 = SM::W2, H2 = SM::H2, PLANE = SM::PLANE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* s_psi = reinterpret_cast<R*>(smem_raw);    // [3 slots][2 comps][H2][W2]
-    R* s_acc = s_psi + 3 * 2 * PLANE;             // [3 slots][2 comps][H2][W2]
-    uint8_t* s_flg = reinterpret_cast<uint8_t*>(s_acc + 3 * 2 * PLANE);  // [3 slots][H2][W2]
-    __shared__ double s_red[2][32];
+    R* s_psi = reinterpret_cast<R*>(smem_raw);                         // [3 slots][2][H2][W2]
+    R* s_yb = s_psi + SM::psi_elems;                                   // [6][2][TY][32]
+    uint8_t* s_flg = reinterpret_cast<uint8_t*>(s_yb + SM::yb_elems);  // [3 slots][H2][W2]
+    __shared__ double s_red[2][TY];
+    __shared__ LinkScratch<R> s_ls[TY];
+    __shared__ PartTable<R> s_pt;
 
     const TileDev T = tiles[blockIdx.x];
     const BoxDev& B = boxes[T.box];
     const int nx = B.nx, ny = B.ny, nz = B.nz, N = B.N;
+    const int nxy = nx * ny;
     const R* __restrict__ rcur = reinterpret_cast<const R*>(B.rho[rc]);
     R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);
     R* __restrict__ rzero = reinterpret_cast<R*>(B.rho[rz]);
     const uint8_t* __restrict__ gflags = B.flags;
     const int32_t* __restrict__ gowner = B.owner;
+    const auto* __restrict__ parts = part_ptr<R>(sh);
     const Pop<P> pop(B);
-    const R rho0 = (R)B.rho0, g = (R)B.g;
+    const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
     const R tau0 = (R)B.tau[0], tau1 = (R)B.tau[1], itau0 = (R)B.inv_tau[0], itau1 = (R)B.inv_tau[1];
     const R wax = (R)B.scw_axis, wdg = (R)B.scw_diag;
-    const R bx = (R)B.body[0], by = (R)B.body[1], bz = (R)B.body[2];
+    const R bfx = (R)B.body[0], bfy = (R)B.body[1], bfz = (R)B.body[2];
     const int velmode = B.vel_mode;
 
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
-    constexpr int NTHR = 32 * TY;
     const int w = T.w, h = T.h, d = T.d, x0 = T.x0, y0 = T.y0, z0 = T.z0;
     const bool active = lx < w && ly < h;
-    const int x = x0 + lx, y = y0 + ly;
-    // wrapped neighbour coordinates (index 1 + offset)
-    const int xw[3] = {x == 0 ? nx - 1 : x - 1, x, x + 1 >= nx ? x + 1 - nx : x + 1};
-    const int yw[3] = {y == 0 ? ny - 1 : y - 1, y, y + 1 >= ny ? y + 1 - ny : y + 1};
+    const int x = active ? x0 + lx : x0, y = active ? y0 + ly : y0;
+    // wrap-aware neighbour offsets along x and y
+    const int oxm = (x == 0) ? nx - 1 : -1, oxp = (x == nx - 1) ? -(nx - 1) : 1;
+    const int oym = (y == 0) ? (ny - 1) * nx : -nx, oyp = (y == ny - 1) ? -(ny - 1) * nx : nx;
+    const int nxyc = x + nx * y;  // in-plane index
 
-    auto slot = [&](int zz) { return (zz - z0 + 1) % 3; };
     auto PSI = [&](int s, int c, int r, int k) -> R& { return s_psi[((s * 2 + c) * H2 + r) * W2 + k]; };
-    auto ACC = [&](int s, int c, int r, int k) -> R& { return s_acc[((s * 2 + c) * H2 + r) * W2 + k]; };
-    auto FLG = [&](int s, int r, int k) -> uint8_t { return s_flg[(s * H2 + r) * W2 + k]; };
+    auto FLG = [&](int s, int r, int k) -> uint8_t& { return s_flg[(s * H2 + r) * W2 + k]; };
+    auto YB = [&](int q, int c, int r, int k) -> R& { return s_yb[((q * 2 + c) * TY + r) * 32 + k]; };
 
-    auto load_plane = [&](int zz) {
-        const int s = slot(zz), gz = wrapi(zz, nz);
-        const int cnt = (h + 2) * (w + 2);
-        for (int idx = tid; idx < cnt; idx += NTHR) {
-            const int r = idx / (w + 2), k = idx - r * (w + 2);
-            const int gx = wrapi(x0 + k - 1, nx), gy = wrapi(y0 + r - 1, ny);
-            const int n = gx + nx * (gy + ny * gz);
-            PSI(s, 0, r, k) = psi_of<R>(rcur[n], rho0);
-            PSI(s, 1, r, k) = psi_of<R>(rcur[N + n], rho0);
-            s_flg[(s * H2 + r) * W2 + k] = gflags[n];
+    // Psi and flags of plane zz (tile + ring) into slot s
+    auto load_window = [&](int zz, int s) {
+        const int gz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        const int pb = nxy * gz;
+        if (active) {
+            const int n = pb + nxyc;
+            PSI(s, 0, ly + 1, lx + 1) = psi_of<R>(rcur[n], rho0, irho0);
+            PSI(s, 1, ly + 1, lx + 1) = psi_of<R>(rcur[(size_t)N + n], rho0, irho0);
+            FLG(s, ly + 1, lx + 1) = gflags[n];
         }
-        for (int idx = tid; idx < 2 * PLANE; idx += NTHR) s_acc[s * 2 * PLANE + idx] = R(0);
+        const int nring = 2 * (w + 2) + 2 * h;
+        if (tid < nring) {
+            int r, k;
+            if (tid < w + 2) {
+                r = 0;
+                k = tid;
+            } else if (tid < 2 * (w + 2)) {
+                r = h + 1;
+                k = tid - (w + 2);
+            } else if (tid < 2 * (w + 2) + h) {
+                k = 0;
+                r = tid - 2 * (w + 2) + 1;
+            } else {
+                k = w + 1;
+                r = tid - 2 * (w + 2) - h + 1;
+            }
+            int gx = x0 + k - 1, gy = y0 + r - 1;
+            gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+            gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+            const int n = pb + gx + nx * gy;
+            PSI(s, 0, r, k) = psi_of<R>(rcur[n], rho0, irho0);
+            PSI(s, 1, r, k) = psi_of<R>(rcur[(size_t)N + n], rho0, irho0);
+            FLG(s, r, k) = gflags[n];
+        }
     };
 
-    auto flush_plane = [&](int pz) {
-        const int s = slot(pz), gz = wrapi(pz, nz);
-        const bool own_plane = pz >= z0 && pz < z0 + d;
-        const bool int_plane = pz >= z0 + 1 && pz <= z0 + d - 2;
-        const int cnt = (h + 2) * (w + 2);
-        for (int idx = tid; idx < cnt; idx += NTHR) {
-            const int r = idx / (w + 2), k = idx - r * (w + 2);
-            const int lxp = k - 1, lyp = r - 1;
-            const bool own = own_plane && lxp >= 0 && lxp < w && lyp >= 0 && lyp < h;
-            const bool interior = int_plane && lxp >= 1 && lxp <= w - 2 && lyp >= 1 && lyp <= h - 2;
-            const int n = wrapi(x0 + lxp, nx) + nx * (wrapi(y0 + lyp, ny) + ny * gz);
+    // rolling slots of planes z-1, z, z+1
+    int sm_ = 0, sc_ = 1, sp_ = 2;
+    load_window(z0 - 1, sm_);
+    load_window(z0, sc_);
+    load_window(z0 + 1, sp_);
+    R acc[3][2];  // own-column partial densities of planes z-1, z, z+1
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const R v = ACC(s, c, r, k);
-                if (interior) rnext[(size_t)c * N + n] = v;
-                else if (v != R(0)) atomicAdd(&rnext[(size_t)c * N + n], v);
-            }
-            if (own && !interior) {
-                rzero[n] = R(0);
-                rzero[(size_t)N + n] = R(0);
-            }
-        }
-    };
-
-    double msum0 = 0.0, msum1 = 0.0;
-    load_plane(z0 - 1);
-    load_plane(z0);
+    for (int k = 0; k < 3; k++) acc[k][0] = acc[k][1] = R(0);
+    R msum0 = R(0), msum1 = R(0);  // fluid mass sent (own precision: Eq. masscorr uses small differences)
+    pt_init<R>(s_pt, tid, 32 * TY);
+    __syncthreads();
 
     for (int z = z0; z < z0 + d; z++) {
-        load_plane(z + 1);
-        __syncthreads();
+        const int ozm = (z == 0) ? (nz - 1) * nxy : -nxy, ozp = (z == nz - 1) ? -(nz - 1) * nxy : nxy;
+        const int n = nxyc + nxy * z;
+        // offset of the neighbour x + c_i (i known at compile time)
+        auto off = [&](int i) -> int {
+            return (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) + (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) +
+                   (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
+        };
+        auto slot_dz = [&](int dz) { return dz < 0 ? sm_ : (dz > 0 ? sp_ : sc_); };
 
+        // per-group partial sums of the values this node sends; after the x
+        // shuffle mid[c][g] holds everything that arrives in this column
+        R mid[2][9];
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int q = 0; q < 9; q++) mid[c][q] = R(0);
+        R upx_[2][5], dnx_[2][5];  // values leaving the tile through x (edge lanes)
+        R rest_pre[2] = {R(0), R(0)}, resid_c[2] = {R(0), R(0)}, sent_c[2] = {R(0), R(0)}, self_c[2] = {R(0), R(0)};
+        R pv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
         int pkey = -1;
-        double pv[6] = {0, 0, 0, 0, 0, 0};
-        if (active) {
-            const int zc = wrapi(z, nz);
-            const int zw[3] = {zc == 0 ? nz - 1 : zc - 1, zc, zc + 1 >= nz ? zc + 1 - nz : zc + 1};
-            const int sl[3] = {slot(z - 1), slot(z), slot(z + 1)};
-            auto nidx = [&](int dx, int dy, int dz) { return xw[1 + dx] + nx * (yw[1 + dy] + ny * zw[1 + dz]); };
-            const int n = nidx(0, 0, 0);
-            const uint8_t fl = FLG(sl[1], ly + 1, lx + 1);
 
-            // Shan-Chen force sums S^c = sum_i W_i Psi^cbar(x + c_i) c_i
-            auto sc_sum = [&](int cb, R& sx, R& sy, R& sz) {
-                sx = sy = sz = R(0);
+        const uint8_t fl = active ? FLG(sc_, ly + 1, lx + 1) : FL_SOLID;
+        const bool fluid = active && !(fl & FL_SOLID);
+        unsigned smask = 0;  // bit i: x + c_i is solid
+        R f[2][19];
+        R rho[2] = {R(1), R(1)}, ux[2] = {R(0), R(0)}, uy[2] = {R(0), R(0)}, uz[2] = {R(0), R(0)};
+        if (fluid) {
+            // ------------------------------------------------- fluid node
+#pragma unroll
+            for (int i = 1; i < 19; i++)
+                smask |= (unsigned)(FLG(slot_dz(cz(i)), ly + 1 + cy(i), lx + 1 + cx(i)) & FL_SOLID) << i;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                f[c][0] = pop.ld_rest(c, n);
 #pragma unroll
                 for (int i = 1; i < 19; i++) {
-                    const R wl = is_axis(i) ? wax : wdg;
-                    const R p = PSI(sl[1 + cz(i)], cb, ly + 1 + cy(i), lx + 1 + cx(i));
-                    sx += wl * p * R(cx(i));
-                    sy += wl * p * R(cy(i));
-                    sz += wl * p * R(cz(i));
+                    // own slot i, or (odd steps, fluid source) slot opp(i) of x - c_i
+                    const S* p;
+                    if (PAR == 0) p = pop.dir(c, i) + n;
+                    else p = ((smask >> opp(i)) & 1u) ? pop.dir(c, i) + n : pop.dir(c, opp(i)) + (n + off(opp(i)));
+                    f[c][i] = pop.ld(p, c, i);
                 }
-            };
+            }
+            R jx[2], jy[2], jz[2];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                R r = 0, ax = 0, ay = 0, az = 0;
+#pragma unroll
+                for (int i = 0; i < 19; i++) {
+                    r += f[c][i];
+                    if (cx(i) > 0) ax += f[c][i];
+                    if (cx(i) < 0) ax -= f[c][i];
+                    if (cy(i) > 0) ay += f[c][i];
+                    if (cy(i) < 0) ay -= f[c][i];
+                    if (cz(i) > 0) az += f[c][i];
+                    if (cz(i) < 0) az -= f[c][i];
+                }
+                rho[c] = r;
+                jx[c] = ax;
+                jy[c] = ay;
+                jz[c] = az;
+            }
+            // Shan-Chen force F^c = -g Psi^c(x) sum_i W_i Psi^cbar(x + c_i) c_i
+            R Fx[2], Fy[2], Fz[2];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int cb = 1 - c;
+                R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+                for (int i = 1; i < 19; i++) {
+                    
+ const R p = (is_axis(i) ? wax : wdg) * PSI(slot_dz(cz(i)), cb, ly + 1 + cy(i), lx + 1 + cx(i));
 
-            if (!(fl & FL_SOLID)) {
-                // ---------------------------------------------- fluid node
-                R f[2][19];
-#pragma unroll
-                for (int c = 0; c < 2; c++)
-#pragma unroll
-                    for (int i = 0; i < 19; i++) {
-                        if (PAR == 0 || i == 0) {
-                            f[c][i] = pop.load(c, i, n);
-                        } else {
-                            const bool src_solid = FLG(sl[1 - cz(i)], ly + 1 - cy(i), lx + 1 - cx(i)) & FL_SOLID;
-                            f[c][i] = src_solid ? pop.load(c, i, n) : pop.load(c, opp(i), nidx(-cx(i), -cy(i), -cz(i)));
-                        }
-                    }
-                R rho[2], jx[2], jy[2], jz[2];
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    R r = 0, ax = 0, ay = 0, az = 0;
-#pragma unroll
-                    for (int i = 0; i < 19; i++) {
-                        r += f[c][i];
-                        ax += R(cx(i)) * f[c][i];
-                        ay += R(cy(i)) * f[c][i];
-                        az += R(cz(i)) * f[c][i];
-                    }
-                    rho[c] = r;
-                    jx[c] = ax;
-                    jy[c] = ay;
-                    jz[c] = az;
+                    if (cx(i) > 0) sx += p;
+                    if (cx(i) < 0) sx -= p;
+                    if (cy(i) > 0) sy += p;
+                    if (cy(i) < 0) sy -= p;
+                    if (cz(i) > 0) sz += p;
+                    if (cz(i) < 0) sz -= p;
                 }
-                R Fx[2], Fy[2], Fz[2];
+                const R pc = -g * PSI(sc_, c, ly + 1, lx + 1);
+                Fx[c] = pc * sx + rho[c] * bfx;
+                Fy[c] = pc * sy + rho[c] * bfy;
+                Fz[c] = pc * sz + rho[c] * bfz;
+            }
+            const R iden = R(1) / (rho[0] * itau0 + rho[1] * itau1);
+            const R upx = (jx[0] * itau0 + jx[1] * itau1) * iden;
+            const R upy = (jy[0] * itau0 + jy[1] * itau1) * iden;
+            const R upz = (jz[0] * itau0 + jz[1] * itau1) * iden;
 #pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    R sx, sy, sz;
-                    sc_sum(1 - c, sx, sy, sz);
-                    const R pc = PSI(sl[1], c, ly + 1, lx + 1);
-                    Fx[c] = -g * pc * sx + rho[c] * bx;
-                    Fy[c] = -g * pc * sy + rho[c] * by;
-                    Fz[c] = -g * pc * sz + rho[c] * bz;
-                }
-                R ux[2], uy[2], uz[2];
-                {
-                    const R den = rho[0] * itau0 + rho[1] * itau1;
-                    const R upx = (jx[0] * itau0 + jx[1] * itau1) / den;
-                    const R upy = (jy[0] * itau0 + jy[1] * itau1) / den;
-                    const R upz = (jz[0] * itau0 + jz[1] * itau1) / den;
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        const R tc = c == 0 ? tau0 : tau1;
-                        const R ir = R(1) / rho[c];
-                        const R basex = velmode ? jx[c] * ir : upx;
-                        const R basey = velmode ? jy[c] * ir : upy;
-                        const R basez = velmode ? jz[c] * ir : upz;
-                        ux[c] = basex + tc * Fx[c] * ir;
-                        uy[c] = basey + tc * Fy[c] * ir;
-                        uz[c] = basez + tc * Fz[c] * ir;
-                    }
-                    const R rt = rho[0] + rho[1];
-                    const R vx = (jx[0] + jx[1]) / rt, vy = (jy[0] + jy[1]) / rt, vz = (jz[0] + jz[1]) / rt;
-                    const R v2 = vx * vx + vy * vy + vz * vz;
-                    if (!(rho[0] > R(0)) || !(rho[1] > R(0)) || !(v2 < R(0.25))) set_err(sh.err, ERR_UNSTABLE);
-                }
+            for (int c = 0; c < 2; c++) {
+                const R tc = c == 0 ? tau0 : tau1;
+                const R ir = R(1) / rho[c];
+                const R bx_ = velmode ? jx[c] * ir : upx;
+                const R by_ = velmode ? jy[c] * ir : upy;
+                const R bz_ = velmode ? jz[c] * ir : upz;
+                ux[c] = bx_ + tc * Fx[c] * ir;
+                uy[c] = by_ + tc * Fy[c] * ir;
+                uz[c] = bz_ + tc * Fz[c] * ir;
+            }
+            const R rt = rho[0] + rho[1];
+            const R vx = jx[0] + jx[1], vy = jy[0] + jy[1], vz = jz[0] + jz[1];
+            if (!(rho[0] > R(0)) || !(rho[1] > R(0)) || !(vx * vx + vy * vy + vz * vz < R(0.25) * rt * rt))
+                set_err(sh.err, ERR_UNSTABLE);
+        }
 
-                // cached data of the last particle seen on a reflected link
-                int cp = -1;
-                double cX[3] = {0, 0, 0}, cU[3] = {0, 0, 0}, cW[3] = {0, 0, 0};
-                double nF[3] = {0, 0, 0};
+        const unsigned FULL = 0xffffffffu;
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            R up[5], dn[5];
+#pragma unroll
+            for (int q = 0; q < 5; q++) up[q] = dn[q] = R(0);
+            if (fluid) {
+                const R itc = c == 0 ? itau0 : itau1;
+                const R omt = R(1) - itc;
+                const R uu = ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c];
+                const R a0 = R(1) - R(1.5) * uu;
+                const R rw1 = rho[c] * wgt<R>(1), rw7 = rho[c] * wgt<R>(7);
+                R resid = R(0), sent = R(0), fe_sum = R(0), self = R(0);
+                // store f*_j: to its stream target, or reflected into slot
+                // opp(j) of this node when the target is solid
+                auto send = [&](auto JC, R fs) {
+                    constexpr int j = decltype(JC)::value;
+                    const bool solid = (smask >> j) & 1u;
+                    S* p;
+                    if (PAR == 0) p = pop.dir(c, opp(j)) + n;
+                    else p = solid ? pop.dir(c, opp(j)) + n : pop.dir(c, j) + (n + off(j));
+                    const R q = pop.st(p, c, j, fs);
+                    if constexpr (P::dev) resid += fs - q;
+                    sent += q;
+                    const R qf = solid ? R(0) : q;
+                    self += solid ? q : R(0);
+                    constexpr int gq = grp_of(j);
+                    if (cx(j) == 0) mid[c][gq] += qf;
+                    else if (cx(j) > 0) up[gq] += qf;
+                    else dn[gq] += qf;
+                };
+                // equilibria of opposite pairs share their even part:
+                // f^eq_(+/-) = zeta rho (E +/- O), E = 1 - 3/2 u^2 + 9/2 cu^2,
+                // O = cu (3 + 9/2 cu^2 - 9/2 u^2)
+                auto pair = [&](auto JC, R cu) {
+                    constexpr int j = decltype(JC)::value;
+                    const R rw = is_axis(j) ? rw1 : rw7;
+                    const R cu2 = cu * cu;
+                    const R E = a0 + R(4.5) * cu2;
+                    const R O = cu * (R(3) + R(4.5) * cu2 - R(4.5) * uu);
+                    
+ const R fep = rw * (E + O), fem = rw * (E - O);
+
+                    fe_sum += fep + fem;
+                    send(std::integral_constant<int, j>{}, omt * f[c][j] + itc * fep);
+                    send(std::integral_constant<int, opp(j)>{}, omt * f[c][opp(j)] + itc * fem);
+                };
+                const R Ux = ux[c], Uy = uy[c], Uz = uz[c];
+                pair(std::integral_constant<int, 1>{}, Ux);
+                pair(std::integral_constant<int, 3>{}, Uy);
+                pair(std::integral_constant<int, 5>{}, Uz);
+                pair(std::integral_constant<int, 7>{}, Ux + Uy);
+                pair(std::integral_constant<int, 9>{}, Ux - Uy);
+                pair(std::integral_constant<int, 11>{}, Ux + Uz);
+                pair(std::integral_constant<int, 13>{}, Ux - Uz);
+                pair(std::integral_constant<int, 15>{}, Uy + Uz);
+                pair(std::integral_constant<int, 17>{}, Uy - Uz);
+                // rest population, stored after the reflected-link pass: its
+                // equilibrium is rho minus the other 18 (equal to Eq. Equil in
+                // exact arithmetic; keeps mass exact in finite precision)
+                rest_pre[c] = omt * f[c][0] + itc * (rho[c] - fe_sum);
+                resid_c[c] = resid;
+                sent_c[c] = sent;
+                self_c[c] = self;
+            }
+            // x shift of the density scatter (all lanes take part)
+#pragma unroll
+            for (int q = 0; q < 5; q++) {
+
+                R fromL = __shfl_up_sync(FULL, up[q], 1);
+                R fromR = __shfl_down_sync(FULL, dn[q], 1);
+                if (lx == 0) fromL = R(0);
+                if (lx == 31) fromR = R(0);
+
+                mid[c][q] += fromL + fromR;
+                upx_[c][q] = up[q];
+                dnx_[c][q] = dn[q];
+            }
+        }
+        // reflected links of the whole warp, then the rest populations; in
+        // deviation storage the rest population absorbs the rounding of the
+        // 18 stored values, so node mass is exact
+        {
+            LinkScratch<R>& ls = s_ls[ly];
+
+            reflect_warp<P>(pop, ls, fluid ? smask : 0u, n, x, y, z, nx, ny, nz, oxm, oxp, oym, oyp, ozm, ozp, rho[0],
+                            rho[1], gowner, parts, s_pt, sh.force);
+            if (fluid) {
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const R itc = c == 0 ? itau0 : itau1;
-                    const R uu = ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c];
-                    R resid = R(0);
-                    R sent = R(0);
-#pragma unroll
-                    for (int j = 1; j < 19; j++) {
-                        const R cuj = R(cx(j)) * ux[c] + R(cy(j)) * uy[c] + R(cz(j)) * uz[c];
-                        const R fe = wgt<R>(j) * rho[c] *
-                                     (R(1) + R(3) * cuj + R(4.5) * cuj * cuj - R(1.5) * uu +
-                                      R(4.5) * cuj * cuj * cuj - R(4.5) * uu * cuj);
-                        const R fs = f[c][j] - (f[c][j] - fe) * itc;
-                        const uint8_t dfl = FLG(sl[1 + cz(j)], ly + 1 + cy(j), lx + 1 + cx(j));
-                        if (!(dfl & FL_SOLID)) {
-                            const R q = (PAR == 0) ? pop.store(c, opp(j), n, fs)
-                                                   : pop.store(c, j, nidx(cx(j), cy(j), cz(j)), fs);
-                            atomicAdd(&ACC(sl[1 + cz(j)], c, ly + 1 + cy(j), lx + 1 + cx(j)), q);
-                            resid += fs - q;
-                            sent += q;
-                        } else {
-                            const int p = gowner[nidx(cx(j), cy(j), cz(j))];
-                            R cu = R(0);
-                            double r[3];
-                            if (p >= 0) {
-                                if (p != cp) {
-                                    const PartState ps = sh.part[p];
-#pragma unroll
-                                    for (int a = 0; a < 3; a++) {
-                                        cX[a] = ps.X[a];
-                                        cU[a] = ps.U[a];
-                                        cW[a] = ps.W[a];
-                                    }
-                                    cp = p;
-                                }
-                                // surface velocity at the link midpoint x + c_j / 2
-                                r[0] = mimg((double)x + 0.5 * cx(j) - cX[0], (double)nx);
-                                r[1] = mimg((double)y + 0.5 * cy(j) - cX[1], (double)ny);
-                                r[2] = mimg((double)zc + 0.5 * cz(j) - cX[2], (double)nz);
-                                const double usx = cU[0] + cW[1] * r[2] - cW[2] * r[1];
-                                const double usy = cU[1] + cW[2] * r[0] - cW[0] * r[2];
-                                const double usz = cU[2] + cW[0] * r[1] - cW[1] * r[0];
-                                cu = (R)(usx * cx(j) + usy * cy(j) + usz * cz(j));
-                            }
-                            const R wall = R(6) * wgt<R>(j) * rho[c] * cu;
-                            const R b = fs - wall;
-                            const R q = pop.store(c, opp(j), n, b);
-                            atomicAdd(&ACC(sl[1], c, ly + 1, lx + 1), q);
-                            resid += b - q;
-                            sent += q;
-                            if (p >= 0) {
-                                const double mag = 2.0 * (double)fs - (double)wall;
-                                const double lf[3] = {mag * cx(j), mag * cy(j), mag * cz(j)};
-                                if (pkey < 0 || pkey == p) {
-                                    pkey = p;
-#pragma unroll
-                                    for (int a = 0; a < 3; a++) nF[a] += lf[a];
-                                } else {
-                                    // a second particle on this node's links: add directly
-                                    double tq[3];
-                                    cross3(r, lf, tq);
-                                    for (int a = 0; a < 3; a++) {
-                                        atomicAdd(&sh.force[(size_t)p * 6 + a], lf[a]);
-                                        atomicAdd(&sh.force[(size_t)p * 6 + 3 + a], tq[a]);
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    // rest population; in deviation storage it absorbs the
-                    // rounding of the 18 stored values so node mass is exact
-                    const R fe0 = wgt<R>(0) * rho[c] * (R(1) - R(1.5) * uu);
-                    const R fs0 = f[c][0] - (f[c][0] - fe0) * itc + resid;
-                    const R q0 = pop.store(c, 0, n, fs0);
-                    atomicAdd(&ACC(sl[1], c, ly + 1, lx + 1), q0);
-                    sent += q0;
-                    if (c == 0) msum0 += (double)sent;
-                    else msum1 += (double)sent;
-                }
-                if (pkey >= 0) {
-                    const PartState ps = sh.part[pkey];
-                    const double rr[3] = {mimg((double)x - ps.X[0], (double)nx), mimg((double)y - ps.X[1], (double)ny),
-                                          mimg((double)zc - ps.X[2], (double)nz)};
-                    double tq[3];
-                    cross3(rr, nF, tq);
-#pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        pv[a] = nF[a];
-                        pv[3 + a] = tq[a];
-                    }
-                }
-            } else if (fl & FL_SHELL) {
-                // ---------------------------------- shell node: virtual fluid
-                const int p = gowner[n];
-                if (p >= 0) {
-                    double Ft[3] = {0, 0, 0};
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        R sx, sy, sz;
-                        sc_sum(1 - c, sx, sy, sz);
-                        const R pc = PSI(sl[1], c, ly + 1, lx + 1);
-                        Ft[0] += (double)(-g * pc * sx);
-                        Ft[1] += (double)(-g * pc * sy);
-                        Ft[2] += (double)(-g * pc * sz);
-                    }
-                    const PartState ps = sh.part[p];
-                    const double rr[3] = {mimg((double)x - ps.X[0], (double)nx), mimg((double)y - ps.X[1], (double)ny),
-                                          mimg((double)zc - ps.X[2], (double)nz)};
-                    double tq[3];
-                    cross3(rr, Ft, tq);
-                    pkey = p;
-#pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        pv[a] = Ft[a];
-                        pv[3 + a] = tq[a];
-                    }
+                    const R dself = ls.dself[lx][c];
+                    const R q0 = pop.st_rest(c, n, rest_pre[c] + resid_c[c] + (P::dev ? ls.dresid[lx][c] : R(0)));
+                    mid[c][0] += q0 + self_c[c] + dself;
+                    const R sent = sent_c[c] + dself + q0;
+                    if (c == 0) msum0 += sent;
+                    else msum1 += sent;
                 }
             }
         }
-        warp_particle_add(pkey, pv, sh.force);
+        if (active && (fl & FL_SOLID) && (fl & FL_SHELL)) {
+            // ---------------------------------- shell node: virtual fluid
+            const int p = gowner[n];
+            if (p >= 0) {
+                R Ft[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int cb = 1 - c;
+                    R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+                    for (int i = 1; i < 19; i++) {
+                        const R pp = (is_axis(i) ? wax : wdg) * PSI(slot_dz(cz(i)), cb, ly + 1 + cy(i), lx + 1 + cx(i));
+                        if (cx(i) > 0) sx += pp;
+                        if (cx(i) < 0) sx -= pp;
+                        if (cy(i) > 0) sy += pp;
+                        if (cy(i) < 0) sy -= pp;
+                        if (cz(i) > 0) sz += pp;
+                        if (cz(i) < 0) sz -= pp;
+                    }
+                    const R pc = -g * PSI(sc_, c, ly + 1, lx + 1);
+                    Ft[0] += pc * sx;
+                    Ft[1] += pc * sy;
+                    Ft[2] += pc * sz;
+                }
+                node_torque<R>(parts[p], x, y, z, nx, ny, nz, Ft, pv);
+                pkey = p;
+            }
+        }
+
+        // values leaving the tile through x: the first lane sends left, the
+        // last active lane sends right
+        if (active && (lx == 0 || lx == w - 1)) {
+            const int gxs = lx == 0 ? (x0 == 0 ? nx - 1 : x0 - 1) : (x0 + w >= nx ? x0 + w - nx : x0 + w);
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int q = 0; q < 5; q++) {
+                    const R v = lx == 0 ? dnx_[c][q] : upx_[c][q];
+                    const R v2 = (lx == 0 && lx == w - 1) ? upx_[c][q] : R(0);  // a one-node-wide tile sends both ways
+                    const int dy = grp_dy(q), dz = grp_dz(q);
+                    int gy = y + dy;
+                    gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+                    int gz = z + dz;
+                    gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
+                    const int base = nx * (gy + ny * gz);
+                    if (v != R(0)) red_add(&rnext[(size_t)c * N + base + gxs], v);
+                    if (v2 != R(0)) {
+                        const int gxr = x0 + w >= nx ? x0 + w - nx : x0 + w;
+                        red_add(&rnext[(size_t)c * N + base + gxr], v2);
+                    }
+                }
+        }
+        // y shift: rows exchange through shared memory; values leaving the
+        // tile through y are reduced into the ring rows directly
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            acc[1][c] += mid[c][0];
+            acc[2][c] += mid[c][3];
+            acc[0][c] += mid[c][4];
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                if (yb_of(q) < 0) continue;
+                YB(yb_of(q), c, ly, lx) = mid[c][q];
+            }
+        }
+        if (active && (ly == 0 || ly == h - 1)) {
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int q = 1; q < 9; q++) {
+                    if (yb_of(q) < 0) continue;
+                    const int dy = grp_dy(q), dz = grp_dz(q);
+                    if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
+                    if (mid[c][q] == R(0)) continue;
+                    int gy = y + dy;
+                    gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+                    int gz = z + dz;
+                    gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
+                    red_add(&rnext[(size_t)c * N + x + nx * (gy + ny * gz)], mid[c][q]);
+                }
+        }
+        warp_particle_add<R>(pkey, pv, s_pt, sh.force);
         __syncthreads();
-        flush_plane(z - 1);
+
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int q = 1; q < 9; q++) {
+                    if (yb_of(q) < 0) continue;
+                    const int dy = grp_dy(q), dz = grp_dz(q);
+                    const int src = ly - dy;
+                    if (src < 0 || src >= h) continue;
+                    acc[1 + dz][c] += YB(yb_of(q), c, src, lx);
+                }
+            // plane z - 1 is complete: interior nodes are stored, edge and
+            // ring nodes reduced
+            const int pz = z - 1;
+            const bool own_plane = pz >= z0;
+            const bool interior = own_plane && pz <= z0 + d - 2 && pz >= z0 + 1 && lx >= 1 && lx <= w - 2 && ly >= 1 &&
+                                  ly <= h - 2;
+            const int gz = pz < 0 ? pz + nz : pz;
+            const int m = nxyc + nxy * gz;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                if (interior) rnext[(size_t)c * N + m] = acc[0][c];
+                else if (acc[0][c] != R(0)) red_add(&rnext[(size_t)c * N + m], acc[0][c]);
+            }
+            if (own_plane && !interior) {
+                rzero[m] = R(0);
+                rzero[(size_t)N + m] = R(0);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            acc[0][c] = acc[1][c];
+            acc[1][c] = acc[2][c];
+            acc[2][c] = R(0);
+        }
+        // plane z + 2 replaces plane z - 1 in the window
+        {
+            const int t = sm_;
+            sm_ = sc_;
+            sc_ = sp_;
+            sp_ = t;
+        }
+
+        if (z + 1 < z0 + d) load_window(z + 2, sp_);
+
         __syncthreads();
     }
-    flush_plane(z0 + d - 1);
-    flush_plane(z0 + d);
+    // last own plane and the ring plane above the chunk
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const int pz = z0 + d - 1 + k;
+            const int gz = pz >= nz ? pz - nz : pz;
+            const int m = nxyc + nxy * gz;
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+                if (acc[k][c] != R(0)) red_add(&rnext[(size_t)c * N + m], acc[k][c]);
+            if (k == 0) {
+                rzero[m] = R(0);
+                rzero[(size_t)N + m] = R(0);
+            }
+        }
+    }
 
     // fluid mass produced for the next step (used by Eq. masscorr)
     {
@@ -400,8 +769,8 @@ static __global__ void __launch_bounds__(32 * TY)
             msum1 += __shfl_xor_sync(FULL, msum1, off);
         }
         if (lx == 0) {
-            s_red[0][ly] = msum0;
-            s_red[1][ly] = msum1;
+            s_red[0][ly] = (double)msum0;
+            s_red[1][ly] = (double)msum1;
         }
         __syncthreads();
         if (tid == 0) {
@@ -414,6 +783,9 @@ static __global__ void __launch_bounds__(32 * TY)
             atomicAdd(&B.mass_acc[mslot * 2 + 1], a1);
         }
     }
+    // particle forces of this CTA into the FP64 accumulators (the barrier
+    // above orders every table update before the flush)
+    pt_flush<R>(s_pt, sh.force, tid, 32 * TY);
 }
 
 }  // namespace lbp

@@ -129,11 +129,13 @@ def test_colors_per_particle_fp64():
     P = lbinputs.spheres(shape, 3.0, 4, seed=21, min_gap=1.0, vmax=0.03)
     o, s = pair(nx=24, ny=24, nz=16, n_particles=4, radius=3.0, g_br=0.15, particle_density=2.0)
     col = np.array([0.05, -0.04, 0.0, 0.02])
-    o.set_colors(col)
-    s.set_colors(0, col)
     rho = lbinputs.lamellae(shape, axis=2, rho_major=0.7, rho_minor=0.05)
     o.init_fields(rho, particles=P)
     s.init_fields(0, rho, particles=P)
+    # initialisation gives every particle the box colour; per-particle
+    # colours are set afterwards
+    o.set_colors(col)
+    s.set_colors(0, col)
     o.step(13)
     s.step(13)
     compare(o, s, ftol=1e-11, ptol=1e-11)
@@ -215,6 +217,24 @@ def test_tilings_agree(ty, cz):
     o.step(12)
     s.step(12)
     compare(o, s, ftol=1e-11, ptol=1e-11)
+
+
+def test_retiling_mid_run():
+    """Changing the block shape between steps (as the autotuner does) keeps
+    the state exact."""
+    shape = (40, 24, 20)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 3.5, 3, seed=43, min_gap=0.5, vmax=0.04, wmax=0.02)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=3, radius=3.5, g_br=0.12, color=0.03, particle_density=2.0)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=44)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    for ty, cz in ((8, 4), (4, 7), (16, 20), (8, 1), (4, 3)):
+        s.set_tiling(ty, cz)
+        s.step(3)
+        o.step(3)
+    compare(o, s, ftol=1e-11, ptol=1e-11)
+    assert s.observables()["error"] == 0
 
 
 def test_batched_boxes_fp64():
