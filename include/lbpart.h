@@ -188,6 +188,39 @@ int lb_kernel_time(lb_handle* h, double* ms_fused, int64_t* launches_fused, int6
 /* Destroy the handle (does not free the caller's workspace). */
 void lb_destroy(lb_handle* h);
 
+/* Field sums of a population field held on the device, computed without
+ * allocating any memory.  The paper has no counterpart to this call; it is
+ * for callers that cannot allocate device memory at the point of the call,
+ * such as a monitor run between the steps of a long job: cudaMalloc and
+ * cudaFree can synchronise the whole device and can fail once the job has
+ * committed nearly all device memory.  It calls no allocating routine.
+ *
+ * d_f      device, f[2][19][n_nodes] FP64 in the layout of lb_export_state
+ *          (populations of solid nodes are ignored); caller-owned.
+ * d_owner  device, owner[n_nodes] int32 as in lb_export_state (-1 fluid,
+ *          anything else solid); caller-owned.
+ * n_nodes  0 <= n_nodes <= LB_FIELD_MOMENTS_MAX_NODES (2^27 = 512^3);
+ *          larger sizes return LB_EINVAL without touching the device.
+ * stream   cudaStream_t to run on (NULL: the legacy default stream).
+ * d_out    device, 8 doubles, caller-owned: {mass_r, mass_b, j_x, j_y, j_z,
+ *          max |j|/rho, n_fluid, n_solid} -- the same sums lb_observables
+ *          reports as mass, mom_fluid, max_u, n_fluid and n_solid.
+ *
+ * Asynchronous on the stream: read d_out after synchronising it.  Pointers
+ * that are not device memory of the current device, or misaligned, return
+ * LB_EINVAL; launch failures return LB_ECUDA.
+ *
+ * Scratch: the library holds one fixed array of LB_FIELD_MOMENTS_MAX_BLOCKS
+ * partial sums (256 KB) on every device that loads it, until the process
+ * exits.  Every call shares that array and overwrites what the previous call
+ * left there, so calls that overlap on the GPU (on different streams, or
+ * from different host threads) race and give wrong sums: serialise them.
+ * The first call on each device looks up the array's device address with
+ * the device current; make that first call before any stream capture. */
+#define LB_FIELD_MOMENTS_MAX_BLOCKS 1024
+#define LB_FIELD_MOMENTS_MAX_NODES 134217728LL
+int lb_field_moments(const double* d_f, const int32_t* d_owner, int64_t n_nodes, void* stream, double* d_out);
+
 const char* lb_strerror(int code);
 
 #ifdef __cplusplus

@@ -77,7 +77,7 @@ ABI_FUNCTIONS = (
     "lb_workspace_bytes", "lb_create", "lb_init_from_seed", "lb_init_fields", "lb_step", "lb_sync",
     "lb_observables", "lb_export_state", "lb_import_state", "lb_export_rho", "lb_set_particle_colors",
     "lb_particle_forces", "lb_box_info", "lb_set_tiling", "lb_set_profiling", "lb_kernel_time",
-    "lb_destroy", "lb_strerror",
+    "lb_destroy", "lb_strerror", "lb_field_moments",
 )
 
 _lib = None
@@ -119,6 +119,7 @@ def load_library(path=LIB_PATH):
     L.lb_destroy.restype = None
     L.lb_strerror.argtypes = [C.c_int]
     L.lb_strerror.restype = C.c_char_p
+    L.lb_field_moments.argtypes = [vp, vp, C.c_int64, vp, vp]
     _lib = L
     return L
 
@@ -132,6 +133,29 @@ def strerror(code):
 def _ck(rc, where):
     if rc != LB_OK:
         raise LbError(rc, where)
+
+
+FIELD_MOMENTS_MAX_NODES = 1 << 27
+
+
+def field_moments(f, owner, out, stream=None):
+    """lb_field_moments on torch CUDA tensors, without allocating: f float64
+    (2, 19, N) and owner int32 (N,) in the lb_export_state layout, out a
+    float64 tensor of 8 values on the same device ({mass_r, mass_b, j_x, j_y,
+    j_z, max |u|, n_fluid, n_solid}).  Asynchronous on `stream` (default: the
+    current torch stream)."""
+    import torch
+
+    n = owner.numel()
+    if f.dtype != torch.float64 or owner.dtype != torch.int32 or out.dtype != torch.float64:
+        raise TypeError("f and out must be float64, owner int32")
+    if f.numel() != 2 * 19 * n or out.numel() < 8 or not (f.is_contiguous() and owner.is_contiguous()):
+        raise ValueError("f must be contiguous (2, 19, N) for owner of N nodes; out needs 8 values")
+    s = stream if stream is not None else torch.cuda.current_stream(out.device)
+    _ck(load_library().lb_field_moments(C.c_void_p(f.data_ptr()), C.c_void_p(owner.data_ptr()), n,
+                                        C.c_void_p(s.cuda_stream), C.c_void_p(out.data_ptr())),
+        "lb_field_moments")
+    return out
 
 
 def make_params(**kw):

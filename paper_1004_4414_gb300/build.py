@@ -1,7 +1,8 @@
 """Build the sm_103a shared library paper_1004_4414_gb300/_build/liblbpart.so.
 
-Five translation units are compiled in parallel with nvcc for
-compute_103a / sm_103a: the host C ABI (lb_api.cu) and one instantiation of
+Six translation units are compiled in parallel with nvcc for
+compute_103a / sm_103a: the host C ABI (lb_api.cu), the allocation-free
+field sums (lb_noalloc.cu) and one instantiation of
 the precision-dependent kernels per population storage type
 (lb_kern_inst.cu with LB_PREC = 0..3).  Host code is compiled without
 floating-point contraction so the seeded sphere placement takes the same
@@ -24,7 +25,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompil
 def _sources():
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     hdrs.append(os.path.join(HERE, "..", "include", "lbpart.h"))
-    units = [("lb_api", os.path.join(CSRC, "lb_api.cu"), [])]
+    units = [("lb_api", os.path.join(CSRC, "lb_api.cu"), []),
+             ("lb_noalloc", os.path.join(CSRC, "lb_noalloc.cu"), [])]
     for k, name in enumerate(("fp64", "fp32", "fp16", "bf16")):
         units.append(("lb_kern_" + name, os.path.join(CSRC, "lb_kern_inst.cu"), ["-DLB_PREC=%d" % k]))
     return units, hdrs
