@@ -188,6 +188,19 @@ def fused_bytes(sim, precision):
     return total
 
 
+def job_throughput(node_updates, seconds, world, device):
+    """Whole-job MLUPS over all ranks: the node updates of every rank divided
+    by the slowest rank's time.  Returns (MLUPS, max-over-ranks ms)."""
+    import torch
+
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(node_updates)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
+    return float(n.item()) / float(t.item()) / 1e6, float(t.item()) * 1e3
+
+
 def run_ours(args, rank, world, device):
     import numpy as np
     import torch
@@ -230,11 +243,7 @@ def run_ours(args, rank, world, device):
     sim.set_profiling(False)
     sim.sync()
     clocks = clk.summary()
-    t_ms = torch.tensor([ms], dtype=torch.float64, device=device)
-    if world > 1:
-        torch.distributed.all_reduce(t_ms, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_ms.item())
-    value = nodes * world * args.steps / (ms_max * 1e-3) / 1e6
+    value, ms_max = job_throughput(nodes * args.steps, ms * 1e-3, world, device)
 
     # ---- roofline of the fused kernel
     bytes_launch = fused_bytes(sim, args.precision)
@@ -244,29 +253,30 @@ def run_ours(args, rank, world, device):
 
     # ---- end to end through the C ABI with host buffers: import the state
     # from pinned host memory, K steps, export it back
-    st = sim.export_state(0) if sim.nb == 1 else None
-    e2e = None
-    if st is not None:
+    states_in, outs, h2d = [], [], 0
+    for b in range(sim.nb):
+        st = sim.export_state(b)
         pin_f = torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy()
         pin_f[...] = st["f"]
-        st_in = dict(st, f=pin_f)
-        out_f = torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy()
-        barrier()
-        torch.cuda.synchronize(device)
-        t0 = time.perf_counter()
-        sim.import_state(0, st_in)
-        sim.step(args.steps)
-        sim.sync()
-        sim.export_state(0, f_out=out_f)
-        t1 = time.perf_counter()
-        barrier()
-        dt = torch.tensor([t1 - t0], dtype=torch.float64, device=device)
-        if world > 1:
-            torch.distributed.all_reduce(dt, op=torch.distributed.ReduceOp.MAX)
-        h2d = st["f"].nbytes + st["owner"].nbytes + st["particles"].nbytes
-        e2e = {"value": nodes * world * args.steps / float(dt.item()) / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": h2d / args.steps,
-               "what": "lb_import_state (pinned host state) + lb_step(K) + lb_export_state (pinned host)"}
+        states_in.append(dict(st, f=pin_f))
+        outs.append(torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy())
+        h2d += st["f"].nbytes + st["owner"].nbytes + st["particles"].nbytes
+    barrier()
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for b in range(sim.nb):
+        sim.import_state(b, states_in[b])
+    sim.step(args.steps)
+    sim.sync()
+    for b in range(sim.nb):
+        sim.export_state(b, f_out=outs[b])
+    t1 = time.perf_counter()
+    barrier()
+    e2e_value, _ = job_throughput(nodes * args.steps, t1 - t0, world, device)
+    e2e = {"value": e2e_value, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": h2d / args.steps,
+           "what": "lb_import_state of every box from pinned host memory + lb_step(K) + "
+                   "lb_export_state of every box into pinned host memory"}
     ob = sim.observables(0)
     return dict(value=value, ms=ms_max, fused_ms=avg_ms, fused_n=fused_n, bytes=bytes_launch, achieved=achieved,
                 peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=total_launches, nodes=nodes,

@@ -9,7 +9,9 @@ dh the distance along z from the particle centre to the interface, located
 by linear interpolation of the phi = 0 crossing.
 
 coverage: fraction of particles whose fluid neighbour nodes carry both signs
-of phi (the paper names interface coverage but does not define it).
+of phi (the paper names interface coverage but does not define it).  Parity
+unpinned: the definition is a reading; a brute-force test pins only the code
+against that reading, not the reading against the paper.
 """
 import numpy as np
 

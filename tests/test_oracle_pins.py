@@ -514,3 +514,46 @@ def test_interface_height_and_angle():
     assert abs(oan.interface_height(col) - 2.5) < 1e-15
     assert abs(oan.contact_angle(-2.93, 10.0) - 107.04) < 0.01
     assert oan.contact_angle(0.0, 5.0) == 90.0
+
+
+def test_coverage_brute_force():
+    """Interface coverage (a reading: the paper does not define it), checked
+    against a per-node loop on a hand-built 7^3 box: particle 0 touches both
+    phases, particle 1 only phi > 0, particle 2 only fluid at phi = 0 (counts
+    as neither side)."""
+    n = 7
+    owner = -np.ones((n, n, n), np.int32)
+    phi = np.ones((n, n, n))
+    owner[1, 1, 1] = 0
+    phi[1, 1, 2] = -0.5          # a diagonal-free axis neighbour of particle 0
+    owner[5, 5, 5] = 1           # surrounded by phi = 1 only
+    owner[3, 5, 1] = 2
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if 0 < abs(dx) + abs(dy) + abs(dz) <= 2:
+                    phi[(3 + dz) % n, (5 + dy) % n, (1 + dx) % n] = 0.0
+    # brute force over the D3Q19 neighbours of every solid node
+    signs = {0: set(), 1: set(), 2: set()}
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                p = owner[z, y, x]
+                if p < 0:
+                    continue
+                for dz in (-1, 0, 1):
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            if not 0 < abs(dx) + abs(dy) + abs(dz) <= 2:
+                                continue
+                            q = ((z + dz) % n, (y + dy) % n, (x + dx) % n)
+                            if owner[q] == -1 and phi[q] != 0:
+                                signs[p].add(np.sign(phi[q]))
+    expect = np.mean([len(signs[p]) == 2 for p in range(3)])
+    assert expect == 1.0 / 3.0
+    assert oan.coverage(phi, owner, 3) == expect
+    # a node two links away (x + 2) is not a neighbour
+    phi2 = phi.copy()
+    phi2[1, 1, 2] = 1.0
+    phi2[1, 1, 3] = -1.0
+    assert oan.coverage(phi2, owner, 3) == 0.0
