@@ -45,8 +45,12 @@ KERNEL_SOURCES = ("lb_step_kernel.cuh", "lb_common.cuh")
 
 
 def workload_params(name, precision="fp32"):
+    # particle density 3: with the explicit particle update, spheres of
+    # density 1 in fluid of total density 0.7 that touch in clusters drive a
+    # growing fluid mode after ~200 steps at 256^3 (the FP64 oracle does the
+    # same); at 3 the workloads stay stable for thousands of steps
     base = dict(tau=(1.0, 1.0), g_br=0.08, rho0=1.0, sc_weight=(2.0, 1.0), noise_amp=0.01, radius=5.0,
-                particle_density=1.0, k_hertz=100.0, precision=precision)
+                particle_density=3.0, k_hertz=100.0, precision=precision)
     if name == "c256":
         return [dict(base, nx=256, ny=256, nz=256, n_particles=-1, volume_fraction=0.20,
                      rho_init=(0.42, 0.28), contact_angle_deg=77.0)], 3
@@ -218,8 +222,19 @@ def run_ours(args, rank, world, device):
     from paper_1004_4414_gb300.autotune import autotune
 
     tiling, _ = autotune(sim)
+    # the timed steps start from the seeded state again
+    sim.init_from_seed(seed + 1000 * rank)
     sim.step(args.warmup)
     sim.sync()
+    # host copy of the state after the warm-up, the input of the end-to-end leg
+    states_in, outs, h2d = [], [], 0
+    for b in range(sim.nb):
+        st = sim.export_state(b)
+        pin_f = torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy()
+        pin_f[...] = st["f"]
+        states_in.append(dict(st, f=pin_f))
+        outs.append(torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy())
+        h2d += st["f"].nbytes + st["owner"].nbytes + st["particles"].nbytes
 
     def barrier():
         if world > 1:
@@ -251,16 +266,14 @@ def run_ours(args, rank, world, device):
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
 
-    # ---- end to end through the C ABI with host buffers: import the state
-    # from pinned host memory, K steps, export it back
-    states_in, outs, h2d = [], [], 0
-    for b in range(sim.nb):
-        st = sim.export_state(b)
-        pin_f = torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy()
-        pin_f[...] = st["f"]
-        states_in.append(dict(st, f=pin_f))
-        outs.append(torch.empty(st["f"].shape, dtype=torch.float64, pin_memory=True).numpy())
-        h2d += st["f"].nbytes + st["owner"].nbytes + st["particles"].nbytes
+    # ---- end to end through the C ABI with host buffers: import the
+    # post-warm-up state from pinned host memory, K steps, export it back.
+    # The boxes of one handle share the step counter, so the states are
+    # imported as of the current step (the exported state is canonical).
+    cur = sim.observables(0)["step"]
+    for st in states_in:
+        st["meta"] = st["meta"].copy()
+        st["meta"][0] = cur
     barrier()
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()

@@ -78,8 +78,8 @@ typedef struct {
     double color;                /* particle colour Delta rho; used when contact_angle_deg is NaN */
     double contact_angle_deg;    /* if finite: Delta rho = (theta - 90) / 442 (fit of Fig. 4b) */
     double k_hertz;              /* K_Hertz of Eq. eq:hertz */
-    double lub_cut;              /* lubrication below this gap */
-    double lub_min;              /* gap where lubrication is clamped */
+    double lub_cut;              /* lubrication below this gap (> lub_min) */
+    double lub_min;              /* gap where lubrication is clamped (> 0) */
     double mass_corr_c0;         /* C0 of Eq. masscorr (0 = off) */
     double body_force[3];        /* uniform acceleration of the fluid (tests; 0 in the paper's runs) */
     int32_t vel_mode;            /* 0: Shan-Chen common velocity in f^eq, 1: each component's own velocity */

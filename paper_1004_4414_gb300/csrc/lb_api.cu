@@ -68,7 +68,7 @@ int validate(const lb_params* bx, int nb) {
         if (p.vel_mode != 0 && p.vel_mode != 1) return LB_EINVAL;
         if (p.reserved != 0) return LB_EINVAL;
         if (derive_np(p) < 0) return LB_EINVAL;
-        if (!(p.lub_min >= 0.0)) return LB_EINVAL;
+        if (!(p.lub_min > 0.0) || !(p.lub_cut > p.lub_min)) return LB_EINVAL;
     }
     return LB_OK;
 }
@@ -310,7 +310,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         k_cell_count<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
         k_cell_scan<<<h->nb, 1024, 0, st>>>(h->d_boxes, h->sh);
         k_cell_fill<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
-        k_nlist<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_nlist<<<(NP + NLIST_WARPS - 1) / NLIST_WARPS, 32 * NLIST_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         k_remap_detect<<<(NP + DETECT_WARPS - 1) / DETECT_WARPS, 32 * DETECT_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         k_remap_mark<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->sh);
         CK(cudaGetLastError());
@@ -345,7 +345,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     }
     if (NP > 0) {
         const int pg = (NP + 255) / 256;
-        k_md_forces<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_md_forces<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
         launches += 2;
     }

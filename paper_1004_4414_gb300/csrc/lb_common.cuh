@@ -294,6 +294,9 @@ __device__ __forceinline__ double mimg(double d, double L) {
     else if (d < -0.5 * L) d += L;
     return d;
 }
+__device__ __forceinline__ float mimgf(float d, float L) {
+    return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
+}
 // squared distance without contraction, so that the inside/outside test of
 // a node is decided exactly as in a plain sequential evaluation
 __device__ __forceinline__ double dist2_nc(double dx, double dy, double dz) {

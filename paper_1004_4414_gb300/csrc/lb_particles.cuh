@@ -22,32 +22,6 @@ __device__ __forceinline__ int cell_of(const BoxDev& B, const double X[3]) {
     return B.cell_off + c[0] + B.nc[0] * (c[1] + B.nc[1] * c[2]);
 }
 
-// visit every particle in the cells around X (each cell once)
-template <class F>
-__device__ __forceinline__ void for_near(const BoxDev& B, const Shared& sh, const double X[3], F fn) {
-    int c[3], lo[3], nr[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        int v = (int)(X[a] / B.cell_len[a]);
-        c[a] = v < 0 ? 0 : (v >= B.nc[a] ? B.nc[a] - 1 : v);
-        if (B.nc[a] >= 3) {
-            lo[a] = c[a] - 1;
-            nr[a] = 3;
-        } else {
-            lo[a] = 0;
-            nr[a] = B.nc[a];
-        }
-    }
-    for (int k2 = 0; k2 < nr[2]; k2++)
-        for (int k1 = 0; k1 < nr[1]; k1++)
-            for (int k0 = 0; k0 < nr[0]; k0++) {
-                const int cc = B.cell_off + wrapi(lo[0] + k0, B.nc[0]) +
-                               B.nc[0] * (wrapi(lo[1] + k1, B.nc[1]) + B.nc[1] * wrapi(lo[2] + k2, B.nc[2]));
-                const int s0 = sh.cell_start[cc], s1 = s0 + sh.cell_count[cc];
-                for (int s = s0; s < s1; s++) fn(sh.cell_list[s]);
-            }
-}
-
 static __global__ void k_step_begin(const BoxDev* __restrict__ boxes, int nb, Shared sh, int total_cells, int mslot_next) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     for (int i = tid; i < total_cells; i += gridDim.x * blockDim.x) sh.cell_count[i] = 0;
@@ -105,28 +79,84 @@ static __global__ void k_cell_fill(const BoxDev* __restrict__ boxes, Shared sh, 
     sh.cell_list[pos] = p;
 }
 
-// neighbours whose spheres could share or take over a node of p:
-// centre distance <= 2R + 2 (a node owned before the move lies within
-// R + |U| <= R + 1 of the new centre)
-static __global__ void k_nlist(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
+// Neighbour list of p: every particle whose centre lies within
+// 2R + max(2, lub_cut) (a node owned before the move lies within R + |U| <=
+// R + 1 of the new centre, and lubrication acts below a gap of lub_cut).
+// One warp per particle; lane k scans cell k of the 3x3x3 block around p.
+// FP32 distances against a slightly larger radius give a superset of the
+// exact list, which is harmless for both users (claims and pair forces).
+// The list is sorted by particle index, so the pair-force sums do not
+// depend on the order in which the cells were filled.
+constexpr int NLIST_WARPS = 4;
+static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    __shared__ int s_ids[NLIST_WARPS][NL_MAX];
+    const unsigned FULL = 0xffffffffu;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * NLIST_WARPS + wib;
+    if (p >= NP) return;  // the whole warp leaves together
     const BoxDev& B = boxes[sh.pbox[p]];
-    const PartState ps = sh.part[p];
-    const double lim = 2.0 * B.radius + 2.0, lim2 = lim * lim;
+    const PartStateF pf = sh.partf[p];
+    const float reach = 2.0f * (float)B.radius + fmaxf(2.0f, (float)B.lub_cut);
+    const float lim2 = reach * reach * 1.0001f + 1e-3f;
+    const float Lf[3] = {(float)B.nx, (float)B.ny, (float)B.nz};
+    // the block of cells around the cell of p (from its FP64 position)
+    int c[3], lo[3], nr[3];
+    const double* X = sh.part[p].X;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int v = (int)(X[a] / B.cell_len[a]);
+        c[a] = v < 0 ? 0 : (v >= B.nc[a] ? B.nc[a] - 1 : v);
+        lo[a] = B.nc[a] >= 3 ? c[a] - 1 : 0;
+        nr[a] = B.nc[a] >= 3 ? 3 : B.nc[a];
+    }
+    const int ncell = nr[0] * nr[1] * nr[2];
+    int s0 = 0, s1 = 0;
+    if (lane < ncell) {
+        const int k0 = lane % nr[0], k1 = (lane / nr[0]) % nr[1], k2 = lane / (nr[0] * nr[1]);
+        const int cc = B.cell_off + wrapi(lo[0] + k0, B.nc[0]) +
+                       B.nc[0] * (wrapi(lo[1] + k1, B.nc[1]) + B.nc[1] * wrapi(lo[2] + k2, B.nc[2]));
+        s0 = sh.cell_start[cc];
+        s1 = s0 + sh.cell_count[cc];
+    }
+    auto near = [&](int q) {
+        if (q == p) return false;
+        const PartStateF qf = sh.partf[q];
+        const float dx = mimgf(qf.X[0] - pf.X[0], Lf[0]), dy = mimgf(qf.X[1] - pf.X[1], Lf[1]),
+                    dz = mimgf(qf.X[2] - pf.X[2], Lf[2]);
+        return dx * dx + dy * dy + dz * dz <= lim2;
+    };
     int cnt = 0;
-    for_near(B, sh, ps.X, [&](int q) {
-        if (q == p) return;
-        const PartState& pq = sh.part[q];
-        const double dx = mimg(pq.X[0] - ps.X[0], B.nx), dy = mimg(pq.X[1] - ps.X[1], B.ny),
-                     dz = mimg(pq.X[2] - ps.X[2], B.nz);
-        if (dx * dx + dy * dy + dz * dz <= lim2) {
-            if (cnt < NL_MAX) sh.nlist[(size_t)p * NL_MAX + cnt] = q;
-            cnt++;
+    for (int s = s0; s < s1; s++) cnt += near(sh.cell_list[s]) ? 1 : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    int pos = incl - cnt;
+    for (int s = s0; s < s1 && pos < NL_MAX; s++) {
+        const int q = sh.cell_list[s];
+        if (near(q)) s_ids[wib][pos++] = q;
+    }
+    __syncwarp();
+    const int n = total < NL_MAX ? total : NL_MAX;
+    int v = lane < n ? s_ids[wib][lane] : 0x7fffffff;
+    // bitonic sort of the 32 lanes, ascending
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int u = __shfl_xor_sync(FULL, v, j);
+            const bool up = (lane & k) == 0 || k == 32;
+            const bool low = (lane & j) == 0;
+            v = (low == up) ? min(v, u) : max(v, u);
         }
-    });
-    if (cnt > NL_MAX) set_err(sh.err, ERR_OVERFLOW);
-    sh.nlist_n[p] = cnt < NL_MAX ? cnt : NL_MAX;
+    if (lane < n) sh.nlist[(size_t)p * NL_MAX + lane] = v;
+    if (lane == 0) {
+        sh.nlist_n[p] = n;
+        if (total > NL_MAX) set_err(sh.err, ERR_OVERFLOW);
+    }
 }
 
 // ------------------------------------------------------------- remap
@@ -134,58 +164,62 @@ static __global__ void k_nlist(const BoxDev* __restrict__ boxes, Shared sh, int 
 // solid/fluid status or owner changes.  A node belongs to the particle whose
 // centre is nearest among those within R (|x - X|^2 <= R^2, minimum image);
 // ties go to the lower index.  Events: covered (fluid -> p), uncovered
-// (p -> fluid), transfer (q -> p, no fluid involved).
+// (p -> fluid), transfer (q -> p, no fluid involved).  Distances are FP32
+// (relative to p, from the FP32 particle copy) unless they fall within
+// `band` of R^2, where the FP64 value, evaluated without contraction as in a
+// plain sequential evaluation, decides.  FP64 is slow on this GPU, so it is
+// kept off the common path.
 constexpr int DETECT_WARPS = 4;
 static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
-    __shared__ double s_nx[DETECT_WARPS][NL_MAX][3];
+    __shared__ float s_rq[DETECT_WARPS][NL_MAX][3];  // X_q - X_p, minimum image
     __shared__ int s_nid[DETECT_WARPS][NL_MAX];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * DETECT_WARPS + wib;
     if (p >= NP) return;  // the whole warp leaves together
     const int b = sh.pbox[p];
     const BoxDev& B = boxes[b];
-    const PartState ps = sh.part[p];
+    const PartStateF pf = sh.partf[p];
     const double R = B.radius, R2 = R * R;
     const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
+    const float Lf[3] = {(float)B.nx, (float)B.ny, (float)B.nz};
     const int nn = sh.nlist_n[p];
     for (int k = lane; k < nn; k += 32) {
         const int q = sh.nlist[(size_t)p * NL_MAX + k];
         s_nid[wib][k] = q;
-        for (int a = 0; a < 3; a++) s_nx[wib][k][a] = sh.part[q].X[a];
+        const PartStateF qf = sh.partf[q];
+        for (int a = 0; a < 3; a++) s_rq[wib][k][a] = mimgf(qf.X[a] - pf.X[a], Lf[a]);
     }
     __syncwarp();
     const int half = (int)ceil(R) + 2;
     int lo[3], span[3];
+    float off[3];  // X_p - lo: node (lo + k) sits at k - off from the centre
     const int dims[3] = {B.nx, B.ny, B.nz};
     for (int a = 0; a < 3; a++) {
-        lo[a] = (int)floor(ps.X[a]) - half;
+        lo[a] = (int)floorf(pf.X[a]) - half;
+        off[a] = pf.X[a] - (float)lo[a];
         span[a] = 2 * half + 1;
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
     const float Rf2o = (float)((R + 1.5) * (R + 1.5));
     const float R2f = (float)R2;
-    // FP32 distances decide unless they fall within `band` of R^2, where the
-    // FP64 value (evaluated without contraction) decides
     const float band = (float)(0.02 + 2e-3 * R2);
-    const float Xf[3] = {(float)ps.X[0], (float)ps.X[1], (float)ps.X[2]};
-    const float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
-    auto mimgf = [](float d, float Lx) { return d > 0.5f * Lx ? d - Lx : (d < -0.5f * Lx ? d + Lx : d); };
     for (int base = 0; base < total; base += 32) {
         const int idx = base + lane;
         int ev_old = 0, ev_new = 0, node = 0;
         bool have = false;
         if (idx < total) {
             const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-            const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
-            const float fx = mimgf((float)gx - Xf[0], Lf[0]), fy = mimgf((float)gy - Xf[1], Lf[1]),
-                        fz = mimgf((float)gz - Xf[2], Lf[2]);
+            const float fx = mimgf((float)kx - off[0], Lf[0]), fy = mimgf((float)ky - off[1], Lf[1]),
+                        fz = mimgf((float)kz - off[2], Lf[2]);
             const float d2f = fx * fx + fy * fy + fz * fz;
-            auto exact_d2 = [&](const double* C) {
-                return dist2_nc(mimg((double)gx - C[0], L[0]), mimg((double)gy - C[1], L[1]),
-                                mimg((double)gz - C[2], L[2]));
-            };
             if (d2f <= Rf2o) {
+                const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
+                auto exact_d2 = [&](int q) {
+                    const double* C = sh.part[q].X;
+                    return dist2_nc(mimg((double)gx - C[0], L[0]), mimg((double)gy - C[1], L[1]),
+                                    mimg((double)gz - C[2], L[2]));
+                };
                 const int n = gx + B.nx * (gy + B.ny * gz);
                 const int own = B.owner[n];
                 if (own != OWN_WALL) {
@@ -194,22 +228,22 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
                     if (fabsf(d2f - R2f) > band) {
                         inside = d2f < R2f;
                     } else {
-                        d2p = exact_d2(ps.X);
+                        d2p = exact_d2(p);
                         inside = d2p <= R2;
                     }
                     if (inside || own == p) {
                         bool other = false, anyone = false;
                         for (int k = 0; k < nn; k++) {
-                            const float ex = mimgf((float)gx - (float)s_nx[wib][k][0], Lf[0]);
-                            const float ey = mimgf((float)gy - (float)s_nx[wib][k][1], Lf[1]);
-                            const float ez = mimgf((float)gz - (float)s_nx[wib][k][2], Lf[2]);
+                            const float ex = mimgf(fx - s_rq[wib][k][0], Lf[0]);
+                            const float ey = mimgf(fy - s_rq[wib][k][1], Lf[1]);
+                            const float ez = mimgf(fz - s_rq[wib][k][2], Lf[2]);
                             if (ex * ex + ey * ey + ez * ez > R2f + band) continue;
-                            const double d2q = exact_d2(s_nx[wib][k]);
+                            const int q = s_nid[wib][k];
+                            const double d2q = exact_d2(q);
                             if (d2q <= R2) {
                                 anyone = true;
                                 if (inside) {
-                                    if (d2p < 0.0) d2p = exact_d2(ps.X);
-                                    const int q = s_nid[wib][k];
+                                    if (d2p < 0.0) d2p = exact_d2(p);
                                     if (d2q < d2p || (d2q == d2p && q < p)) other = true;
                                 }
                             }
@@ -504,26 +538,30 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     const int p = blockIdx.x * 4 + wib;
     if (p >= NP) return;
     const BoxDev& B = boxes[sh.pbox[p]];
-    const PartState ps = sh.part[p];
+    const PartStateF pf = sh.partf[p];
     R* rcur = reinterpret_cast<R*>(B.rho[rc]);
-    const double R_ = B.radius;
+    const float R_ = (float)B.radius;
     const double col = sh.color[p];
-    const int half = (int)ceil(R_) + 1;
+    const int half = (int)ceilf(R_) + 1;
     int lo[3], span[3];
+    float off[3];  // X - lo: node (lo + k) sits at k - off from the centre
     const int dims[3] = {B.nx, B.ny, B.nz};
     for (int a = 0; a < 3; a++) {
-        lo[a] = (int)floor(ps.X[a]) - half;
+        lo[a] = (int)floorf(pf.X[a]) - half;
+        off[a] = pf.X[a] - (float)lo[a];
         span[a] = 2 * half + 1;
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
-    const float lim = (float)((R_ + 0.5) * (R_ + 0.5));
+    // FP32 prefilter only (every shell node of p lies within R); the shell
+    // flag and the owner decide.  No FP64 here: it is slow on this GPU.
+    const float lim = (R_ + 0.5f) * (R_ + 0.5f);
     for (int idx = lane; idx < total; idx += 32) {
         const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-        const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
-        const float dx = (float)mimg((double)gx - ps.X[0], B.nx), dy = (float)mimg((double)gy - ps.X[1], B.ny),
-                    dz = (float)mimg((double)gz - ps.X[2], B.nz);
+        const float dx = mimgf((float)kx - off[0], (float)B.nx), dy = mimgf((float)ky - off[1], (float)B.ny),
+                    dz = mimgf((float)kz - off[2], (float)B.nz);
         if (dx * dx + dy * dy + dz * dz > lim) continue;
+        const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
         const int n = gx + B.nx * (gy + B.ny * gz);
         if (!(B.flags[n] & FL_SHELL) || B.owner[n] != p) continue;
         R s0 = R(0), s1 = R(0);
@@ -607,21 +645,28 @@ static __global__ void k_part_to_float(Shared sh, int p0, int n) {
 }
 
 // coupling forces of the step are saved, then the pair forces are added
-static __global__ void k_md_forces(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
+// Pair forces (Hertz contact and lubrication) on p, added to the fluid
+// force; the fluid part is kept in force_last first.  One warp per particle,
+// lane k takes the k-th entry of the (sorted) neighbour list; a fixed
+// butterfly sums the lanes, so the result does not depend on timing.
+constexpr int MD_WARPS = 4;
+static __global__ void __launch_bounds__(32 * MD_WARPS) k_md_forces(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const unsigned FULL = 0xffffffffu;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * MD_WARPS + wib;
+    if (p >= NP) return;  // the whole warp leaves together
     const BoxDev& B = boxes[sh.pbox[p]];
     double* fp = &sh.force[(size_t)p * 6];
-    double F[3] = {fp[0], fp[1], fp[2]};
-    for (int a = 0; a < 6; a++) sh.force_last[(size_t)p * 6 + a] = fp[a];
-    const PartState ps = sh.part[p];
-    for_near(B, sh, ps.X, [&](int q) {
-        if (q == p) return;
-        pair_force(B, ps, sh.part[q], F);
-    });
-    fp[0] = F[0];
-    fp[1] = F[1];
-    fp[2] = F[2];
+    const double mine = lane < 6 ? fp[lane] : 0.0;
+    if (lane < 6) sh.force_last[(size_t)p * 6 + lane] = mine;
+    double F[3] = {0.0, 0.0, 0.0};
+    const int nn = sh.nlist_n[p];
+    if (lane < nn) pair_force(B, sh.part[p], sh.part[sh.nlist[(size_t)p * NL_MAX + lane]], F);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(FULL, F[a], off);
+    if (lane < 3) fp[lane] = mine + F[lane];
 }
 
 // leap-frog: U += F/m, omega += T/J, X += U (periodic); accumulators zeroed

@@ -60,7 +60,7 @@ def test_invalid_parameters_rejected(lib):
 
     n = C.c_size_t(0)
     for bad in (dict(nx=0), dict(tau=(0.5, 1.0)), dict(precision=7), dict(reserved=1), dict(radius=0.0),
-                dict(rho_init=(0.0, 0.7))):
+                dict(rho_init=(0.0, 0.7)), dict(lub_min=0.0), dict(lub_cut=0.1, lub_min=0.1)):
         p = binding.make_params(**bad)
         arr = (binding.LbParams * 1)(p)
         assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_EINVAL
