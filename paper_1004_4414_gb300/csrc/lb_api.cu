@@ -211,6 +211,14 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     sh.ev_rho = cv.take<double>((size_t)evcap * 2);
     sh.ev_count = cv.take<int>(1);
     sh.ev_cap = evcap;
+    {
+        // shell nodes of one sphere: a one-node layer around its surface
+        double rmax = 0.0;
+        for (int b = 0; b < nb; b++) rmax = bx[b].radius > rmax ? bx[b].radius : rmax;
+        sh.shell_cap = (int)(12.0 * (rmax + 1.0) * (rmax + 1.0)) + 64;
+    }
+    sh.shell_list = cv.take<int>((size_t)NPa * sh.shell_cap);
+    sh.shell_n = cv.take<int>(NPa);
     sh.err = cv.take<int>(1);
     sh.counters = cv.take<unsigned long long>((size_t)nb * 2);
     BoxDev* d_boxes = cv.take<BoxDev>(nb);
@@ -345,9 +353,10 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     }
     if (NP > 0) {
         const int pg = (NP + 255) / 256;
+        CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, NP));
         k_md_forces<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
-        launches += 2;
+        launches += 3;
     }
     h->launches_since = launches;
     if (prof) h->prof_total += launches;

@@ -112,6 +112,9 @@ struct Shared {
     double* ev_rho;             // [cap][2] refill density
     int* ev_count;              // [1]
     int ev_cap;
+    int* shell_list;            // [NP][shell_cap] shell nodes of each particle (this step)
+    int* shell_n;               // [NP]
+    int shell_cap;
     int* err;                   // [1] sticky error bits
     unsigned long long* counters; // [n_boxes][2] n_cover, n_uncover
 };
@@ -288,6 +291,8 @@ __device__ __forceinline__ int wrapi(int a, int n) {
     a %= n;
     return a < 0 ? a + n : a;
 }
+// a + d for |d| <= 1 on a periodic axis of length n (no division)
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 // minimum image of a displacement along an axis of length L
 __device__ __forceinline__ double mimg(double d, double L) {
     if (d > 0.5 * L) d -= L;

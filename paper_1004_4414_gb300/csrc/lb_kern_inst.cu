@@ -85,6 +85,12 @@ cudaError_t shell_density(cudaStream_t st, const BoxDev* boxes, Shared sh, int r
     return cudaGetLastError();
 }
 
+cudaError_t couple(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int NP) {
+    if (NP <= 0) return cudaSuccess;
+    k_couple<PP><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot);
+    return cudaGetLastError();
+}
+
 cudaError_t wall_shell(cudaStream_t st, const BoxDev* boxes, int b, int rc) {
     k_wall_shell<RR><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, rc);
     return cudaGetLastError();
@@ -118,6 +124,7 @@ cudaError_t obs_partial(cudaStream_t st, const BoxDev* boxes, int b, int par, do
 }  // namespace
 
 const LbOps OPS_NAME = {PP::id,       sizeof(RR),   setup,         step_smem,  step,       remap_apply, remap_finish,
-                        shell_density, wall_shell, init_pop,       export_dir, import_dir, rho_from_pop, obs_partial};
+                        shell_density, couple,     wall_shell,     init_pop,   export_dir, import_dir,   rho_from_pop,
+                        obs_partial};
 
 }  // namespace lbp

@@ -534,18 +534,24 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
 // particle colour on red (Delta rho > 0) or blue (Delta rho < 0) (Sec. IV).
 template <class R>
 static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh, int rc, int NP) {
+    __shared__ int s_q[4][64];
+    const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * 4 + wib;
-    if (p >= NP) return;
+    if (p >= NP) return;  // the whole warp leaves together
     const BoxDev& B = boxes[sh.pbox[p]];
     const PartStateF pf = sh.partf[p];
-    R* rcur = reinterpret_cast<R*>(B.rho[rc]);
+    R* __restrict__ rcur = reinterpret_cast<R*>(B.rho[rc]);
+    const uint8_t* __restrict__ flags = B.flags;
+    const int32_t* __restrict__ owner = B.owner;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const size_t N = (size_t)B.N;
     const float R_ = (float)B.radius;
-    const double col = sh.color[p];
+    const R col = (R)sh.color[p];
     const int half = (int)ceilf(R_) + 1;
     int lo[3], span[3];
     float off[3];  // X - lo: node (lo + k) sits at k - off from the centre
-    const int dims[3] = {B.nx, B.ny, B.nz};
+    const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; a++) {
         lo[a] = (int)floorf(pf.X[a]) - half;
         off[a] = pf.X[a] - (float)lo[a];
@@ -553,33 +559,225 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
-    // FP32 prefilter only (every shell node of p lies within R); the shell
-    // flag and the owner decide.  No FP64 here: it is slow on this GPU.
-    const float lim = (R_ + 0.5f) * (R_ + 0.5f);
-    for (int idx = lane; idx < total; idx += 32) {
-        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-        const float dx = mimgf((float)kx - off[0], (float)B.nx), dy = mimgf((float)ky - off[1], (float)B.ny),
-                    dz = mimgf((float)kz - off[2], (float)B.nz);
-        if (dx * dx + dy * dy + dz * dz > lim) continue;
-        const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
-        const int n = gx + B.nx * (gy + B.ny * gz);
-        if (!(B.flags[n] & FL_SHELL) || B.owner[n] != p) continue;
+    // virtual density of one shell node n of p
+    auto process = [&](int n) {
+        const int gx = n % nx, gy = (n / nx) % ny, gz = n / (nx * ny);
         R s0 = R(0), s1 = R(0);
         int cnt = 0;
 #pragma unroll
         for (int i = 1; i < 19; i++) {
-            const int m = wrapi(gx + cx(i), B.nx) + B.nx * (wrapi(gy + cy(i), B.ny) + B.ny * wrapi(gz + cz(i), B.nz));
-            if (!(B.flags[m] & FL_SOLID)) {
+            const int m = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
+            if (!(flags[m] & FL_SOLID)) {
                 s0 += rcur[m];
-                s1 += rcur[(size_t)B.N + m];
+                s1 += rcur[N + m];
                 cnt++;
             }
         }
         R r0 = s0 / (R)cnt, r1 = s1 / (R)cnt;
-        if (col > 0.0) r0 += (R)col;
-        else if (col < 0.0) r1 += (R)(-col);
+        if (col > R(0)) r0 += col;
+        else if (col < R(0)) r1 -= col;
         rcur[n] = r0;
-        rcur[(size_t)B.N + n] = r1;
+        rcur[N + n] = r1;
+    };
+    // FP32 prefilter only (every shell node of p lies within R); the shell
+    // flag and the owner decide.  No FP64 here: it is slow on this GPU.
+    // Shell nodes are queued as they are found and handled 32 at a time;
+    // they are also listed for k_couple.
+    const float lim = (R_ + 0.5f) * (R_ + 0.5f);
+    const int cap = sh.shell_cap;
+    int* __restrict__ list = sh.shell_list + (size_t)p * cap;
+    int nq = 0, done = 0;  // warp-uniform: queue length (< 64), nodes handled
+    for (int base = 0;; base += 32) {
+        const int idx = base + lane;
+        bool take = false;
+        int n = 0;
+        if (idx < total) {
+            const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+            const float dx = mimgf((float)kx - off[0], (float)nx), dy = mimgf((float)ky - off[1], (float)ny),
+                        dz = mimgf((float)kz - off[2], (float)nz);
+            if (dx * dx + dy * dy + dz * dz <= lim) {
+                n = wrapi(lo[0] + kx, nx) + nx * (wrapi(lo[1] + ky, ny) + ny * wrapi(lo[2] + kz, nz));
+                take = (flags[n] & FL_SHELL) && owner[n] == p;
+            }
+        }
+        const unsigned m = __ballot_sync(FULL, take);
+        if (take) s_q[wib][nq + __popc(m & ((1u << lane) - 1u))] = n;
+        nq += __popc(m);
+        __syncwarp();
+        const bool last = base + 32 >= total;  // the final round drains the queue
+        if (nq >= 32 || (last && nq > 0)) {
+            const int k = nq < 32 ? nq : 32;
+            const int item = lane < k ? s_q[wib][nq - k + lane] : -1;
+            __syncwarp();
+            nq -= k;
+            if (item >= 0) {
+                if (done + lane < cap) list[done + lane] = item;
+                process(item);
+            }
+            done += k;
+        }
+        if (last && nq == 0) break;
+    }
+    if (lane == 0) {
+        sh.shell_n[p] = done < cap ? done : cap;
+        if (done > cap) set_err(sh.err, ERR_OVERFLOW);
+    }
+}
+
+// ----------------------------------------------------- fluid -> particle
+// Coupling terms of each particle that live on its surface, after the fused
+// step; one block per particle over its shell nodes s (solid nodes of p with
+// a fluid D3Q19 neighbour, listed by k_shell_density in this step):
+//   * the Shan-Chen force of the virtual fluid at s on the particle
+//     (Eq. eqn_shan_chen_particle): F = sum_c -g Psi^c(s) sum_i W_i
+//     Psi^cbar(s + c_i) c_i, torque (s - X) x F;
+//   * every link from a fluid neighbour x = s + c_i to s, direction
+//     j = opp(i).  The fused step stored the post-collision f*_j of x,
+//     reflected, in slot i of x (both parities).  Here it gets the
+//     moving-wall term, b = f*_j - 6 zeta_j rho^c(x) (u_s . c_j) with u_s =
+//     U + omega x r at the link midpoint r = x + c_j / 2 - X
+//     (Eq. eqn_ladd_bewegtewand), and the particle receives
+//     (2 f*_j - 6 zeta_j rho^c(x) u_s . c_j) c_j with torque r x F
+//     (Eq. eqn_bounce-back-force).  The change of the stored value also
+//     changes rho(t+1) at x and the fluid mass the step produced; in
+//     deviation storage the rest slot of x absorbs the rounding.
+// A link belongs to the owner of its solid end, so each slot is written
+// once; the density and rest-slot updates are atomic because several links
+// can share a fluid node.  Static walls (owner -2) reflect without a wall
+// term and need nothing here.  rho^c(x) is the density field of the current
+// step (the fused step's moments up to rounding order).
+constexpr int COUPLE_THREADS = 128;
+template <class P>
+static __global__ void __launch_bounds__(COUPLE_THREADS, 4)
+    k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot) {
+    using R = typename P::real;
+    using S = typename P::st;
+    const unsigned FULL = 0xffffffffu;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ R s_red[COUPLE_THREADS / 32][8];
+    const int p = blockIdx.x;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    const Pop<P> pop(B);
+    const auto& ps = part_ptr<R>(sh)[p];
+    const size_t N = (size_t)B.N;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const R* __restrict__ rcur = reinterpret_cast<const R*>(B.rho[rc]);
+    R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);
+    const uint8_t* __restrict__ flags = B.flags;
+    double* __restrict__ mass_acc = B.mass_acc;
+    const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
+    const R wax = (R)B.scw_axis, wdg = (R)B.scw_diag;
+    const R Lx = (R)nx, Ly = (R)ny, Lz = (R)nz;
+    const R X0 = (R)ps.X[0], X1 = (R)ps.X[1], X2 = (R)ps.X[2];
+    const R U0 = (R)ps.U[0], U1 = (R)ps.U[1], U2 = (R)ps.U[2];
+    const R W0 = (R)ps.W[0], W1 = (R)ps.W[1], W2 = (R)ps.W[2];
+    R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    R dm0 = R(0), dm1 = R(0);
+    // work of one shell node s of p (any subset of lanes may call it).  The
+    // neighbour densities and flags are read-only in this kernel and come
+    // through the non-coherent path; all link values are loaded before any
+    // is stored, so the loads of a node are in flight together.
+    auto process = [&](int s) {
+        const int gx = s % nx, gy = (s / nx) % ny, gz = s / (nx * ny);
+        const R rs0 = mimg_r<R>((R)gx - X0, Lx), rs1 = mimg_r<R>((R)gy - X1, Ly), rs2 = mimg_r<R>((R)gz - X2, Lz);
+        int mi[19];
+        unsigned fmask = 0;  // bit i: s + c_i is fluid (a link)
+        R sr0 = R(0), sr1 = R(0), sr2 = R(0), sb0 = R(0), sb1 = R(0), sb2 = R(0);
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            mi[i] = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
+            fmask |= (__ldg(flags + mi[i]) & FL_SOLID) ? 0u : (1u << i);
+            const R w = is_axis(i) ? wax : wdg;
+            const R pr = w * psi_of<R>(__ldg(rcur + mi[i]), rho0, irho0);
+            const R pb = w * psi_of<R>(__ldg(rcur + N + mi[i]), rho0, irho0);
+            sr0 += pr * (R)cx(i);
+            sr1 += pr * (R)cy(i);
+            sr2 += pr * (R)cz(i);
+            sb0 += pb * (R)cx(i);
+            sb1 += pb * (R)cy(i);
+            sb2 += pb * (R)cz(i);
+        }
+        R fs0[19], fs1[19];
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            fs0[i] = R(0);
+            fs1[i] = R(0);
+            if (fmask & (1u << i)) {
+                fs0[i] = pop.ld(pop.dir(0, i) + mi[i], 0, i);
+                fs1[i] = pop.ld(pop.dir(1, i) + mi[i], 1, i);
+            }
+        }
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            if (!(fmask & (1u << i))) continue;
+            const int m = mi[i];
+            // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
+            const R r0 = rs0 + R(0.5) * (R)cx(i), r1 = rs1 + R(0.5) * (R)cy(i), r2 = rs2 + R(0.5) * (R)cz(i);
+            const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
+            const R cu6 = -R(6) * wgt<R>(i) * (us0 * (R)cx(i) + us1 * (R)cy(i) + us2 * (R)cz(i));
+            R mag = R(0);
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const R fs = c == 0 ? fs0[i] : fs1[i];
+                const R wall = cu6 * __ldg(rcur + (size_t)c * N + m);
+                if (wall != R(0)) {
+                    const R b = fs - wall;
+                    const R q = pop.st(pop.dir(c, i) + m, c, i, b);
+                    R dr = q - fs;
+                    if constexpr (P::dev) {
+                        const R res = b - q;
+                        atomicAdd(&pop.f0[(size_t)c * N + m], res);
+                        dr += res;
+                    }
+                    atomicAdd(&rnext[(size_t)c * N + m], dr);
+                    if (c == 0) dm0 += dr;
+                    else dm1 += dr;
+                }
+                mag += R(2) * fs - wall;
+            }
+            const R F0 = -mag * (R)cx(i), F1 = -mag * (R)cy(i), F2 = -mag * (R)cz(i);
+            acc[0] += F0;
+            acc[1] += F1;
+            acc[2] += F2;
+            acc[3] += r1 * F2 - r2 * F1;
+            acc[4] += r2 * F0 - r0 * F2;
+            acc[5] += r0 * F1 - r1 * F0;
+        }
+        const R psr = psi_of<R>(__ldg(rcur + s), rho0, irho0), psb = psi_of<R>(__ldg(rcur + N + s), rho0, irho0);
+        const R F0 = -g * (psr * sb0 + psb * sr0), F1 = -g * (psr * sb1 + psb * sr1), F2 = -g * (psr * sb2 + psb * sr2);
+        acc[0] += F0;
+        acc[1] += F1;
+        acc[2] += F2;
+        acc[3] += rs1 * F2 - rs2 * F1;
+        acc[4] += rs2 * F0 - rs0 * F2;
+        acc[5] += rs0 * F1 - rs1 * F0;
+    };
+    // the shell nodes found by k_shell_density in this step
+    const int ns = sh.shell_n[p];
+    const int* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
+    for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) process(list[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 6; a++) acc[a] += __shfl_xor_sync(FULL, acc[a], o);
+        dm0 += __shfl_xor_sync(FULL, dm0, o);
+        dm1 += __shfl_xor_sync(FULL, dm1, o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int a = 0; a < 6; a++) s_red[wib][a] = acc[a];
+        s_red[wib][6] = dm0;
+        s_red[wib][7] = dm1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int a = threadIdx.x;
+        R v = s_red[0][a];
+#pragma unroll
+        for (int w = 1; w < COUPLE_THREADS / 32; w++) v += s_red[w][a];
+        // the only writer of this particle's accumulator in this kernel
+        if (a < 6) sh.force[(size_t)p * 6 + a] += (double)v;
+        else if (v != R(0)) atomicAdd(&mass_acc[mslot * 2 + (a - 6)], (double)v);
     }
 }
 

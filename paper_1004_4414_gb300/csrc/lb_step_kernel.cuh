@@ -1,15 +1,14 @@
-// lb_step_kernel.cuh -- the fused per-step kernel of the fluid: streaming,
-// moving-wall bounce-back with momentum exchange, Shan-Chen force,
-// cubic-equilibrium BGK collision, the shell Shan-Chen force on the
-// particles, and the density field of the next step.
+// lb_step_kernel.cuh -- the fused per-step kernel of the fluid: streaming
+// with bounce-back, Shan-Chen force, cubic-equilibrium BGK collision, and the
+// density field of the next step.
 //
 // Method (paper): Eq. eq:boltz with the BGK operator and the equilibrium of
 // Eq. Equil at the velocity shifted by tau F / rho (Sec. II); the force of
 // Eq. eqn_shan-chen-F with Psi of Eq. eqn_ref_dens over the 18 D3Q19 links;
-// bounce-back with the moving-wall term and the momentum-exchange force
-// (Eqs. eqn_bounce-back, eqn_ladd_bewegtewand; coefficient 6 zeta_j =
-// 2 zeta_j / c_s^2); the force of the virtual fluid on its particle
-// (Eq. eqn_shan_chen_particle).
+// bounce-back at solid nodes (Eq. eqn_bounce-back).  The moving-wall term,
+// the momentum exchange and the shell force on the particles are added
+// afterwards by k_couple (lb_particles.cuh), which only touches the links
+// at particle surfaces.
 //
 // GB300 design:
 //   * Populations stay in place with the AA pattern.  Even steps: a node
@@ -19,13 +18,8 @@
 //     into slot opp(j) of the node itself on both parities, which is where
 //     the next step reads it.  Each slot is read once and written once per
 //     step.  Every load and store has its address selected first, so the
-//     common path has no branches; neighbour offsets are wrap-aware and
-//     computed once per thread.
-//   * Reflected links are rare (nodes next to particles).  The main path
-//     writes every post-collision value, a reflected one without the
-//     moving-wall term; then the warp takes its (node, direction) links as
-//     work items, 32 at a time, adds the wall term and the momentum exchange
-//     and sums the particle forces.
+//     path has no branches; neighbour offsets are wrap-aware and computed
+//     once per thread.
 //   * A CTA owns a column tile of 32 x TY nodes (one warp per x row: all
 //     population traffic is coalesced along x) and marches through a chunk
 //     of z planes.  Psi and the node flags of the tile plus a one-node ring
@@ -40,11 +34,6 @@
 //     ring nodes are added with global reductions into a density buffer that
 //     was zeroed at exactly those nodes during the previous step (ring of
 //     three density buffers: current, next, to-zero).
-//   * Particle forces are summed per node (all reflected links of a node
-//     carry forces parallel to c_j, so the node's torque is (x - X_p) x F),
-//     reduced across the warp per particle with shuffles, summed per CTA in
-//     a shared-memory table, and added to the FP64 accumulators once per
-//     (CTA, particle) -- conversions to FP64 are slow on GB300.
 #pragma once
 #include <type_traits>
 
@@ -56,76 +45,6 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// Per-CTA table of particle forces and torques, summed in the kernel's
-// precision in shared memory and added to the FP64 accumulators once per
-// (CTA, particle) when the CTA finishes.  Open addressing on the particle
-// index; a full table falls back to direct FP64 atomics.
-constexpr int PT_SLOTS = 128;
-template <class R>
-struct PartTable {
-    int key[PT_SLOTS];
-    R val[PT_SLOTS][6];
-};
-
-template <class R>
-__device__ __forceinline__ void pt_init(PartTable<R>& t, int tid, int nthr) {
-    for (int i = tid; i < PT_SLOTS; i += nthr) {
-        t.key[i] = -1;
-#pragma unroll
-        for (int a = 0; a < 6; a++) t.val[i][a] = R(0);
-    }
-}
-
-template <class R>
-__device__ __forceinline__ void pt_add(PartTable<R>& t, int p, const R v[6], double* force) {
-    int h = p & (PT_SLOTS - 1);
-    for (int probe = 0; probe < PT_SLOTS; probe++) {
-        const int k = atomicCAS(&t.key[h], -1, p);
-        if (k == -1 || k == p) {
-#pragma unroll
-            for (int a = 0; a < 6; a++) atomicAdd(&t.val[h][a], v[a]);
-            return;
-        }
-        h = (h + 1) & (PT_SLOTS - 1);
-    }
-#pragma unroll
-    for (int a = 0; a < 6; a++) atomicAdd(&force[(size_t)p * 6 + a], (double)v[a]);
-}
-
-template <class R>
-__device__ __forceinline__ void pt_flush(const PartTable<R>& t, double* force, int tid, int nthr) {
-    for (int i = tid; i < PT_SLOTS * 6; i += nthr) {
-        const int s = i / 6, a = i - s * 6;
-        const int p = t.key[s];
-        if (p >= 0 && t.val[s][a] != R(0)) atomicAdd(&force[(size_t)p * 6 + a], (double)t.val[s][a]);
-    }
-}
-
-// Sum (F, T) of the lanes that share a particle key and add it to the CTA's
-// particle table, one entry per distinct key in the warp.  All 32 lanes of
-// the warp must call it.
-template <class R>
-__device__ __forceinline__ void warp_particle_add(int key, const R v[6], PartTable<R>& pt, double* force) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    unsigned pending = __ballot_sync(FULL, key >= 0);
-    while (pending) {
-        const int leader = __ffs(pending) - 1;
-        const int k = __shfl_sync(FULL, key, leader);
-        const bool mine = (key == k);
-        const unsigned grp = __ballot_sync(FULL, mine);
-        R s[6];
-#pragma unroll
-        for (int a = 0; a < 6; a++) s[a] = mine ? v[a] : R(0);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int a = 0; a < 6; a++) s[a] += __shfl_xor_sync(FULL, s[a], off);
-        if (lane == leader) pt_add<R>(pt, k, s, force);
-        pending &= ~grp;
-    }
 }
 
 // Psi = rho0 (1 - exp(-rho / rho0)); irho0 = 1 / rho0
@@ -178,132 +97,6 @@ static __constant__ signed char kC[19][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0
                                              {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
                                              {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1}};
 
-// Per-warp scratch of the reflected-link pass (shared memory).
-template <class R>
-struct LinkScratch {
-    int lane[32];  // node (lane) of each link item of the current batch
-    int dir[32];   // direction of each link item
-    R dself[32][2];   // change of what each node sends to itself, per component
-    R dresid[32][2];  // change of the rounding residual (deviation storage)
-};
-
-// Reflected links of a warp's nodes.  Every population f*_j whose target
-// x + c_j is solid was stored in slot opp(j) of x without the wall term;
-// here each (node, j) link of the warp is one work item, 32 per batch: the
-// stored value gets the moving-wall term b = f*_j - 6 zeta_j rho^c
-// (u_s . c_j), u_s the particle's surface velocity at the link midpoint
-// x + c_j / 2, and the particle receives (2 f*_j - 6 zeta_j rho^c u_s . c_j)
-// c_j with torque r x F about its centre (r to the link midpoint).  Static
-// walls (owner -2) reflect without wall term or force.  All 32 lanes call it.
-template <class P>
-__device__ __forceinline__ void reflect_warp(const Pop<P>& pop, LinkScratch<typename P::real>& ls, unsigned smask,
-                                             int n, int x, int y, int z, int nx, int ny, int nz, int oxm, int oxp,
-                                             int oym, int oyp, int ozm, int ozp, typename P::real rho0_,
-                                             typename P::real rho1_, const int32_t* __restrict__ owner,
-                                             const typename PartOf<typename P::real>::type* __restrict__ parts,
-                                             PartTable<typename P::real>& pt, double* force) {
-    using R = typename P::real;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int cnt = __popc(smask);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    const int excl = incl - cnt;
-    ls.dself[lane][0] = ls.dself[lane][1] = R(0);
-    ls.dresid[lane][0] = ls.dresid[lane][1] = R(0);
-    for (int base = 0; base < total; base += 32) {
-        // place this lane's items of the batch [base, base + 32)
-        if (excl < base + 32 && excl + cnt > base) {
-            unsigned m = smask;
-            for (int k = excl; m; k++) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                if (k >= base && k < base + 32) {
-                    ls.lane[k - base] = lane;
-                    ls.dir[k - base] = j;
-                }
-            }
-        }
-        __syncwarp();
-        const bool has = base + lane < total;
-        const int L = has ? ls.lane[lane] : lane;
-        const int j = has ? ls.dir[lane] : 0;
-        // node data of the owning lane
-        const int nL = __shfl_sync(FULL, n, L), xL = __shfl_sync(FULL, x, L), yL = __shfl_sync(FULL, y, L);
-        const int oxmL = __shfl_sync(FULL, oxm, L), oxpL = __shfl_sync(FULL, oxp, L);
-        const int oymL = __shfl_sync(FULL, oym, L), oypL = __shfl_sync(FULL, oyp, L);
-        const R r0L = __shfl_sync(FULL, rho0_, L), r1L = __shfl_sync(FULL, rho1_, L);
-        int key = -1;
-        R v[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-        if (has) {
-            const int jx = kC[j][0], jy = kC[j][1], jz = kC[j][2];
-            const int oj = (j & 1) ? j + 1 : j - 1;
-            const int noff = (jx < 0 ? oxmL : (jx > 0 ? oxpL : 0)) + (jy < 0 ? oymL : (jy > 0 ? oypL : 0)) +
-                             (jz < 0 ? ozm : (jz > 0 ? ozp : 0));
-            const int p = owner[nL + noff];
-            if (p >= 0) {
-                const auto& ps = parts[p];
-                const R d0 = mimg_r<R>((R)xL + R(0.5) * (R)jx - (R)ps.X[0], (R)nx);
-                const R d1 = mimg_r<R>((R)yL + R(0.5) * (R)jy - (R)ps.X[1], (R)ny);
-                const R d2 = mimg_r<R>((R)z + R(0.5) * (R)jz - (R)ps.X[2], (R)nz);
-                const R W0 = (R)ps.W[0], W1 = (R)ps.W[1], W2 = (R)ps.W[2];
-                const R usx = (R)ps.U[0] + W1 * d2 - W2 * d1;
-                const R usy = (R)ps.U[1] + W2 * d0 - W0 * d2;
-                const R usz = (R)ps.U[2] + W0 * d1 - W1 * d0;
-                const R cu6 = R(6) * ((jx * jx + jy * jy + jz * jz == 1) ? wgt<R>(1) : wgt<R>(7)) *
-                              (usx * (R)jx + usy * (R)jy + usz * (R)jz);
-                R mag = R(0);
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const R wall = cu6 * (c == 0 ? r0L : r1L);
-                    typename P::st* ptr = pop.dir(c, oj) + nL;
-                    const R fs = pop.ld(ptr, c, oj);
-                    if (wall != R(0)) {
-                        const R b = fs - wall;
-                        const R q = pop.st(ptr, c, oj, b);
-                        atomicAdd(&ls.dself[L][c], q - fs);
-                        if constexpr (P::dev) atomicAdd(&ls.dresid[L][c], b - q);
-                    }
-                    mag += R(2) * fs - wall;
-                }
-                const R F0 = mag * (R)jx, F1 = mag * (R)jy, F2 = mag * (R)jz;
-                key = p;
-                v[0] = F0;
-                v[1] = F1;
-                v[2] = F2;
-                v[3] = d1 * F2 - d2 * F1;
-                v[4] = d2 * F0 - d0 * F2;
-                v[5] = d0 * F1 - d1 * F0;
-            }
-        }
-        warp_particle_add<R>(key, v, pt, force);
-        __syncwarp();
-    }
-    __syncwarp();
-}
-
-// Shan-Chen force of a shell node onto its particle (Eq. eqn_shan_chen_particle)
-// is computed in the fused kernel; its torque arm (x - X_p) and the node
-// torque of the momentum exchange use this helper.
-template <class R, class PT>
-__device__ __forceinline__ void node_torque(const PT& ps, int x, int y, int z, int nx, int ny, int nz, const R F[3],
-                                            R out[6]) {
-    const R rr0 = mimg_r<R>((R)x - (R)ps.X[0], (R)nx);
-    const R rr1 = mimg_r<R>((R)y - (R)ps.X[1], (R)ny);
-    const R rr2 = mimg_r<R>((R)z - (R)ps.X[2], (R)nz);
-    out[0] = F[0];
-    out[1] = F[1];
-    out[2] = F[2];
-    out[3] = rr1 * F[2] - rr2 * F[1];
-    out[4] = rr2 * F[0] - rr0 * F[2];
-    out[5] = rr0 * F[1] - rr1 * F[0];
-}
-
 template <class R, int TY>
 struct StepSmem {
     static constexpr int W2 = 34, H2 = TY + 2, PLANE = W2 * H2;
@@ -319,14 +112,12 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     using R = typename P::real;
     using S = typename P::st;
     using SM = StepSmem<R, TY>;
-    constexpr int W2 = SM::W2, H2 = SM::H2, PLANE = SM::PLANE;
+    constexpr int W2 = SM::W2, H2 = SM::H2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s_psi = reinterpret_cast<R*>(smem_raw);                         // [3 slots][2][H2][W2]
     R* s_yb = s_psi + SM::psi_elems;                                   // [6][2][TY][32]
     uint8_t* s_flg = reinterpret_cast<uint8_t*>(s_yb + SM::yb_elems);  // [3 slots][H2][W2]
     __shared__ double s_red[2][TY];
-    __shared__ LinkScratch<R> s_ls[TY];
-    __shared__ PartTable<R> s_pt;
 
     const TileDev T = tiles[blockIdx.x];
     const BoxDev& B = boxes[T.box];
@@ -336,8 +127,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);
     R* __restrict__ rzero = reinterpret_cast<R*>(B.rho[rz]);
     const uint8_t* __restrict__ gflags = B.flags;
-    const int32_t* __restrict__ gowner = B.owner;
-    const auto* __restrict__ parts = part_ptr<R>(sh);
     const Pop<P> pop(B);
     const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
     const R tau0 = (R)B.tau[0], tau1 = (R)B.tau[1], itau0 = (R)B.inv_tau[0], itau1 = (R)B.inv_tau[1];
@@ -403,7 +192,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
 #pragma unroll
     for (int k = 0; k < 3; k++) acc[k][0] = acc[k][1] = R(0);
     R msum0 = R(0), msum1 = R(0);  // fluid mass sent (own precision: Eq. masscorr uses small differences)
-    pt_init<R>(s_pt, tid, 32 * TY);
     __syncthreads();
 
     for (int z = z0; z < z0 + d; z++) {
@@ -425,8 +213,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             for (int q = 0; q < 9; q++) mid[c][q] = R(0);
         R upx_[2][5], dnx_[2][5];  // values leaving the tile through x (edge lanes)
         R rest_pre[2] = {R(0), R(0)}, resid_c[2] = {R(0), R(0)}, sent_c[2] = {R(0), R(0)}, self_c[2] = {R(0), R(0)};
-        R pv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-        int pkey = -1;
 
         const uint8_t fl = active ? FLG(sc_, ly + 1, lx + 1) : FL_SOLID;
         const bool fluid = active && !(fl & FL_SOLID);
@@ -570,9 +356,9 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 pair(std::integral_constant<int, 13>{}, Ux - Uz);
                 pair(std::integral_constant<int, 15>{}, Uy + Uz);
                 pair(std::integral_constant<int, 17>{}, Uy - Uz);
-                // rest population, stored after the reflected-link pass: its
-                // equilibrium is rho minus the other 18 (equal to Eq. Equil in
-                // exact arithmetic; keeps mass exact in finite precision)
+                // rest population: its equilibrium is rho minus the other 18
+                // (equal to Eq. Equil in exact arithmetic; keeps mass exact in
+                // finite precision)
                 rest_pre[c] = omt * f[c][0] + itc * (rho[c] - fe_sum);
                 resid_c[c] = resid;
                 sent_c[c] = sent;
@@ -592,52 +378,16 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 dnx_[c][q] = dn[q];
             }
         }
-        // reflected links of the whole warp, then the rest populations; in
-        // deviation storage the rest population absorbs the rounding of the
-        // 18 stored values, so node mass is exact
-        {
-            LinkScratch<R>& ls = s_ls[ly];
-
-            reflect_warp<P>(pop, ls, fluid ? smask : 0u, n, x, y, z, nx, ny, nz, oxm, oxp, oym, oyp, ozm, ozp, rho[0],
-                            rho[1], gowner, parts, s_pt, sh.force);
-            if (fluid) {
+        // rest populations; in deviation storage the rest population absorbs
+        // the rounding of the 18 stored values, so node mass is exact
+        if (fluid) {
 #pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const R dself = ls.dself[lx][c];
-                    const R q0 = pop.st_rest(c, n, rest_pre[c] + resid_c[c] + (P::dev ? ls.dresid[lx][c] : R(0)));
-                    mid[c][0] += q0 + self_c[c] + dself;
-                    const R sent = sent_c[c] + dself + q0;
-                    if (c == 0) msum0 += sent;
-                    else msum1 += sent;
-                }
-            }
-        }
-        if (active && (fl & FL_SOLID) && (fl & FL_SHELL)) {
-            // ---------------------------------- shell node: virtual fluid
-            const int p = gowner[n];
-            if (p >= 0) {
-                R Ft[3] = {R(0), R(0), R(0)};
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const int cb = 1 - c;
-                    R sx = 0, sy = 0, sz = 0;
-#pragma unroll
-                    for (int i = 1; i < 19; i++) {
-                        const R pp = (is_axis(i) ? wax : wdg) * PSI(slot_dz(cz(i)), cb, ly + 1 + cy(i), lx + 1 + cx(i));
-                        if (cx(i) > 0) sx += pp;
-                        if (cx(i) < 0) sx -= pp;
-                        if (cy(i) > 0) sy += pp;
-                        if (cy(i) < 0) sy -= pp;
-                        if (cz(i) > 0) sz += pp;
-                        if (cz(i) < 0) sz -= pp;
-                    }
-                    const R pc = -g * PSI(sc_, c, ly + 1, lx + 1);
-                    Ft[0] += pc * sx;
-                    Ft[1] += pc * sy;
-                    Ft[2] += pc * sz;
-                }
-                node_torque<R>(parts[p], x, y, z, nx, ny, nz, Ft, pv);
-                pkey = p;
+            for (int c = 0; c < 2; c++) {
+                const R q0 = pop.st_rest(c, n, rest_pre[c] + resid_c[c]);
+                mid[c][0] += q0 + self_c[c];
+                const R sent = sent_c[c] + q0;
+                if (c == 0) msum0 += sent;
+                else msum1 += sent;
             }
         }
 
@@ -693,7 +443,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     red_add(&rnext[(size_t)c * N + x + nx * (gy + ny * gz)], mid[c][q]);
                 }
         }
-        warp_particle_add<R>(pkey, pv, s_pt, sh.force);
         __syncthreads();
 
         if (active) {
@@ -783,9 +532,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             atomicAdd(&B.mass_acc[mslot * 2 + 1], a1);
         }
     }
-    // particle forces of this CTA into the FP64 accumulators (the barrier
-    // above orders every table update before the flush)
-    pt_flush<R>(s_pt, sh.force, tid, 32 * TY);
 }
 
 }  // namespace lbp
