@@ -147,41 +147,66 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     auto FLG = [&](int s, int r, int k) -> uint8_t& { return s_flg[(s * H2 + r) * W2 + k]; };
     auto YB = [&](int q, int c, int r, int k) -> R& { return s_yb[((q * 2 + c) * TY + r) * 32 + k]; };
 
-    // Psi and flags of plane zz (tile + ring) into slot s
-    auto load_window = [&](int zz, int s) {
+    // The window of a plane: Psi and flags of the tile (one node per
+    // thread) and of its one-node ring (thread tid < nring takes ring node
+    // (ring_r, ring_k)); ring positions do not depend on the plane.
+    const int nring = 2 * (w + 2) + 2 * h;
+    int ring_r = 0, ring_k = 0, ring_xy = 0;
+    if (tid < nring) {
+        if (tid < w + 2) {
+            ring_r = 0;
+            ring_k = tid;
+        } else if (tid < 2 * (w + 2)) {
+            ring_r = h + 1;
+            ring_k = tid - (w + 2);
+        } else if (tid < 2 * (w + 2) + h) {
+            ring_k = 0;
+            ring_r = tid - 2 * (w + 2) + 1;
+        } else {
+            ring_k = w + 1;
+            ring_r = tid - 2 * (w + 2) - h + 1;
+        }
+        int gx = x0 + ring_k - 1, gy = y0 + ring_r - 1;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+        ring_xy = gx + nx * gy;
+    }
+    // raw window values of one plane, fetched ahead of their use
+    struct WinRaw {
+        R a0, a1, b0, b1;
+        uint8_t af, bf;
+    };
+    auto fetch_window = [&](int zz) {
+        WinRaw v{R(0), R(0), R(0), R(0), 0, 0};
         const int gz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
         const int pb = nxy * gz;
         if (active) {
             const int n = pb + nxyc;
-            PSI(s, 0, ly + 1, lx + 1) = psi_of<R>(rcur[n], rho0, irho0);
-            PSI(s, 1, ly + 1, lx + 1) = psi_of<R>(rcur[(size_t)N + n], rho0, irho0);
-            FLG(s, ly + 1, lx + 1) = gflags[n];
+            v.a0 = rcur[n];
+            v.a1 = rcur[(size_t)N + n];
+            v.af = gflags[n];
         }
-        const int nring = 2 * (w + 2) + 2 * h;
         if (tid < nring) {
-            int r, k;
-            if (tid < w + 2) {
-                r = 0;
-                k = tid;
-            } else if (tid < 2 * (w + 2)) {
-                r = h + 1;
-                k = tid - (w + 2);
-            } else if (tid < 2 * (w + 2) + h) {
-                k = 0;
-                r = tid - 2 * (w + 2) + 1;
-            } else {
-                k = w + 1;
-                r = tid - 2 * (w + 2) - h + 1;
-            }
-            int gx = x0 + k - 1, gy = y0 + r - 1;
-            gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-            gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-            const int n = pb + gx + nx * gy;
-            PSI(s, 0, r, k) = psi_of<R>(rcur[n], rho0, irho0);
-            PSI(s, 1, r, k) = psi_of<R>(rcur[(size_t)N + n], rho0, irho0);
-            FLG(s, r, k) = gflags[n];
+            const int n = pb + ring_xy;
+            v.b0 = rcur[n];
+            v.b1 = rcur[(size_t)N + n];
+            v.bf = gflags[n];
+        }
+        return v;
+    };
+    auto store_window = [&](const WinRaw& v, int s) {
+        if (active) {
+            PSI(s, 0, ly + 1, lx + 1) = psi_of<R>(v.a0, rho0, irho0);
+            PSI(s, 1, ly + 1, lx + 1) = psi_of<R>(v.a1, rho0, irho0);
+            FLG(s, ly + 1, lx + 1) = v.af;
+        }
+        if (tid < nring) {
+            PSI(s, 0, ring_r, ring_k) = psi_of<R>(v.b0, rho0, irho0);
+            PSI(s, 1, ring_r, ring_k) = psi_of<R>(v.b1, rho0, irho0);
+            FLG(s, ring_r, ring_k) = v.bf;
         }
     };
+    auto load_window = [&](int zz, int s) { store_window(fetch_window(zz), s); };
 
     // rolling slots of planes z-1, z, z+1
     int sm_ = 0, sc_ = 1, sp_ = 2;
@@ -195,6 +220,11 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     __syncthreads();
 
     for (int z = z0; z < z0 + d; z++) {
+        // window of plane z + 2, fetched now and stored at the end of this
+        // plane, so that its load latency hides behind the plane's work
+        const bool more = z + 1 < z0 + d;
+        WinRaw ahead{R(0), R(0), R(0), R(0), 0, 0};
+        if (more) ahead = fetch_window(z + 2);
         const int ozm = (z == 0) ? (nz - 1) * nxy : -nxy, ozp = (z == nz - 1) ? -(nz - 1) * nxy : nxy;
         const int n = nxyc + nxy * z;
         // offset of the neighbour x + c_i (i known at compile time)
@@ -488,7 +518,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             sp_ = t;
         }
 
-        if (z + 1 < z0 + d) load_window(z + 2, sp_);
+        if (more) store_window(ahead, sp_);
 
         __syncthreads();
     }
