@@ -646,9 +646,9 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
 // can share a fluid node.  Static walls (owner -2) reflect without a wall
 // term and need nothing here.  rho^c(x) is the density field of the current
 // step (the fused step's moments up to rounding order).
-constexpr int COUPLE_THREADS = 128;
+constexpr int COUPLE_THREADS = 256;
 template <class P>
-static __global__ void __launch_bounds__(COUPLE_THREADS, 4)
+static __global__ void __launch_bounds__(COUPLE_THREADS)
     k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot) {
     using R = typename P::real;
     using S = typename P::st;
@@ -673,23 +673,67 @@ static __global__ void __launch_bounds__(COUPLE_THREADS, 4)
     const R W0 = (R)ps.W[0], W1 = (R)ps.W[1], W2 = (R)ps.W[2];
     R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     R dm0 = R(0), dm1 = R(0);
-    // work of one shell node s of p (any subset of lanes may call it).  The
-    // neighbour densities and flags are read-only in this kernel and come
-    // through the non-coherent path; all link values are loaded before any
-    // is stored, so the loads of a node are in flight together.
-    auto process = [&](int s) {
+    // the shell nodes found by k_shell_density in this step
+    const int ns = sh.shell_n[p];
+    const int* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
+    // (1) links: one item per (direction i, shell node s), direction-major,
+    // so that neighbouring threads touch neighbouring nodes of one array
+    for (int k = threadIdx.x; k < 18 * ns; k += COUPLE_THREADS) {
+        const int i = 1 + k / ns;
+        const int s = list[k - (i - 1) * ns];
+        const int ix = kC[i][0], iy = kC[i][1], iz = kC[i][2];
         const int gx = s % nx, gy = (s / nx) % ny, gz = s / (nx * ny);
-        const R rs0 = mimg_r<R>((R)gx - X0, Lx), rs1 = mimg_r<R>((R)gy - X1, Ly), rs2 = mimg_r<R>((R)gz - X2, Lz);
-        int mi[19];
-        unsigned fmask = 0;  // bit i: s + c_i is fluid (a link)
+        const int m = wrap1(gx + ix, nx) + nx * (wrap1(gy + iy, ny) + ny * wrap1(gz + iz, nz));
+        if (__ldg(flags + m) & FL_SOLID) continue;
+        // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
+        const R r0 = mimg_r<R>((R)gx - X0, Lx) + R(0.5) * (R)ix;
+        const R r1 = mimg_r<R>((R)gy - X1, Ly) + R(0.5) * (R)iy;
+        const R r2 = mimg_r<R>((R)gz - X2, Lz) + R(0.5) * (R)iz;
+        const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
+        const R cu6 = -R(6) * (i <= 6 ? wgt<R>(1) : wgt<R>(7)) * (us0 * (R)ix + us1 * (R)iy + us2 * (R)iz);
+        S* const p0 = pop.dir(0, i) + m;
+        S* const p1 = pop.dir(1, i) + m;
+        const R fs0 = pop.ld(p0, 0, i), fs1 = pop.ld(p1, 1, i);
+        const R rr = __ldg(rcur + m), rb = __ldg(rcur + N + m);
+        R mag = R(0);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const R fs = c == 0 ? fs0 : fs1;
+            const R wall = cu6 * (c == 0 ? rr : rb);
+            if (wall != R(0)) {
+                const R b = fs - wall;
+                const R q = pop.st(c == 0 ? p0 : p1, c, i, b);
+                R dr = q - fs;
+                if constexpr (P::dev) {
+                    const R res = b - q;
+                    atomicAdd(&pop.f0[(size_t)c * N + m], res);
+                    dr += res;
+                }
+                atomicAdd(&rnext[(size_t)c * N + m], dr);
+                if (c == 0) dm0 += dr;
+                else dm1 += dr;
+            }
+            mag += R(2) * fs - wall;
+        }
+        const R F0 = -mag * (R)ix, F1 = -mag * (R)iy, F2 = -mag * (R)iz;
+        acc[0] += F0;
+        acc[1] += F1;
+        acc[2] += F2;
+        acc[3] += r1 * F2 - r2 * F1;
+        acc[4] += r2 * F0 - r0 * F2;
+        acc[5] += r0 * F1 - r1 * F0;
+    }
+    // (2) the Shan-Chen force of the virtual fluid at each shell node
+    for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) {
+        const int s = list[k];
+        const int gx = s % nx, gy = (s / nx) % ny, gz = s / (nx * ny);
         R sr0 = R(0), sr1 = R(0), sr2 = R(0), sb0 = R(0), sb1 = R(0), sb2 = R(0);
 #pragma unroll
         for (int i = 1; i < 19; i++) {
-            mi[i] = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
-            fmask |= (__ldg(flags + mi[i]) & FL_SOLID) ? 0u : (1u << i);
+            const int m = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
             const R w = is_axis(i) ? wax : wdg;
-            const R pr = w * psi_of<R>(__ldg(rcur + mi[i]), rho0, irho0);
-            const R pb = w * psi_of<R>(__ldg(rcur + N + mi[i]), rho0, irho0);
+            const R pr = w * psi_of<R>(__ldg(rcur + m), rho0, irho0);
+            const R pb = w * psi_of<R>(__ldg(rcur + N + m), rho0, irho0);
             sr0 += pr * (R)cx(i);
             sr1 += pr * (R)cy(i);
             sr2 += pr * (R)cz(i);
@@ -697,52 +741,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS, 4)
             sb1 += pb * (R)cy(i);
             sb2 += pb * (R)cz(i);
         }
-        R fs0[19], fs1[19];
-#pragma unroll
-        for (int i = 1; i < 19; i++) {
-            fs0[i] = R(0);
-            fs1[i] = R(0);
-            if (fmask & (1u << i)) {
-                fs0[i] = pop.ld(pop.dir(0, i) + mi[i], 0, i);
-                fs1[i] = pop.ld(pop.dir(1, i) + mi[i], 1, i);
-            }
-        }
-#pragma unroll
-        for (int i = 1; i < 19; i++) {
-            if (!(fmask & (1u << i))) continue;
-            const int m = mi[i];
-            // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
-            const R r0 = rs0 + R(0.5) * (R)cx(i), r1 = rs1 + R(0.5) * (R)cy(i), r2 = rs2 + R(0.5) * (R)cz(i);
-            const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
-            const R cu6 = -R(6) * wgt<R>(i) * (us0 * (R)cx(i) + us1 * (R)cy(i) + us2 * (R)cz(i));
-            R mag = R(0);
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const R fs = c == 0 ? fs0[i] : fs1[i];
-                const R wall = cu6 * __ldg(rcur + (size_t)c * N + m);
-                if (wall != R(0)) {
-                    const R b = fs - wall;
-                    const R q = pop.st(pop.dir(c, i) + m, c, i, b);
-                    R dr = q - fs;
-                    if constexpr (P::dev) {
-                        const R res = b - q;
-                        atomicAdd(&pop.f0[(size_t)c * N + m], res);
-                        dr += res;
-                    }
-                    atomicAdd(&rnext[(size_t)c * N + m], dr);
-                    if (c == 0) dm0 += dr;
-                    else dm1 += dr;
-                }
-                mag += R(2) * fs - wall;
-            }
-            const R F0 = -mag * (R)cx(i), F1 = -mag * (R)cy(i), F2 = -mag * (R)cz(i);
-            acc[0] += F0;
-            acc[1] += F1;
-            acc[2] += F2;
-            acc[3] += r1 * F2 - r2 * F1;
-            acc[4] += r2 * F0 - r0 * F2;
-            acc[5] += r0 * F1 - r1 * F0;
-        }
+        const R rs0 = mimg_r<R>((R)gx - X0, Lx), rs1 = mimg_r<R>((R)gy - X1, Ly), rs2 = mimg_r<R>((R)gz - X2, Lz);
         const R psr = psi_of<R>(__ldg(rcur + s), rho0, irho0), psb = psi_of<R>(__ldg(rcur + N + s), rho0, irho0);
         const R F0 = -g * (psr * sb0 + psb * sr0), F1 = -g * (psr * sb1 + psb * sr1), F2 = -g * (psr * sb2 + psb * sr2);
         acc[0] += F0;
@@ -751,11 +750,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS, 4)
         acc[3] += rs1 * F2 - rs2 * F1;
         acc[4] += rs2 * F0 - rs0 * F2;
         acc[5] += rs0 * F1 - rs1 * F0;
-    };
-    // the shell nodes found by k_shell_density in this step
-    const int ns = sh.shell_n[p];
-    const int* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
-    for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) process(list[k]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
