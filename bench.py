@@ -14,6 +14,7 @@ measured HBM roofline reached by the fused stream-collide kernel.
 Workloads (seeded, synthetic; the paper's runs are synthetic as well):
   c256  256^3, fluid ratio 60:40 of total density 0.7, alpha = 0.20, R = 5,
         contact angle 77 deg (colour -0.0294), g = 0.08 (default)
+  c256p the c256 parameters on a 128^3 box (small case for profiler captures)
   c128  128^3, 50:50, alpha = 0.15, R = 5, 90 deg
   c512  512^3, 50:50, alpha = 0.20, R = 5, 90 deg
   c32   32^3, 0.7 / 0.7, 16 spheres R = 4 (parity configuration)
@@ -53,6 +54,10 @@ def workload_params(name, precision="fp32"):
                 particle_density=3.0, k_hertz=100.0, precision=precision)
     if name == "c256":
         return [dict(base, nx=256, ny=256, nz=256, n_particles=-1, volume_fraction=0.20,
+                     rho_init=(0.42, 0.28), contact_angle_deg=77.0)], 3
+    if name == "c256p":
+        # profiling case: the c256 parameters on a 128^3 box (state > L2, ~1 GB)
+        return [dict(base, nx=128, ny=128, nz=128, n_particles=-1, volume_fraction=0.20,
                      rho_init=(0.42, 0.28), contact_angle_deg=77.0)], 3
     if name == "c128":
         return [dict(base, nx=128, ny=128, nz=128, n_particles=-1, volume_fraction=0.15,
@@ -328,7 +333,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c256", choices=["c256", "c128", "c512", "c32", "batch"])
+    ap.add_argument("--workload", default="c256", choices=["c256", "c256p", "c128", "c512", "c32", "batch"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -339,6 +344,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     metric = "MLUPS and % of HBM roofline: FP32 vs BF16/FP16-storage vs batched, same GPU"
     names = {"c256": "256^3 60:40 alpha=0.20 R=5 theta=77deg", "c128": "128^3 50:50 alpha=0.15 R=5 theta=90deg",
+             "c256p": "128^3 with the 256^3 parameters (profiling case)",
              "c512": "512^3 50:50 alpha=0.20 R=5 theta=90deg", "c32": "32^3 16 spheres R=4",
              "batch": "64 boxes {48,64,96,128}^3 theta 60-120 alpha 0.05-0.25 ratio 50:50-70:30"}
 
