@@ -353,7 +353,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     }
     if (NP > 0) {
         const int pg = (NP + 255) / 256;
-        CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, NP));
+        CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, par, NP));
         k_md_forces<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
         launches += 3;

@@ -129,14 +129,14 @@ static __global__ void k_init_pop(const BoxDev* __restrict__ boxes, int b, const
     }
 }
 
-// populations of node n at the coming step of parity par
+// populations of node n at the coming step of parity par: before an even
+// step f_i sits in slot i of n, before an odd step in slot opp(i) of n - c_i
+// (whatever the status of n - c_i)
 template <class P>
 __device__ __forceinline__ typename P::real load_node_pop(const BoxDev& B, const Pop<P>& pop, int par, int c, int i,
                                                           int n) {
     if (par == 0 || i == 0) return pop.load(c, i, n);
-    const int s = nbr_index(B, n, -cx(i), -cy(i), -cz(i));
-    if (B.flags[s] & FL_SOLID) return pop.load(c, i, n);
-    return pop.load(c, opp(i), s);
+    return pop.load(c, opp(i), nbr_index(B, n, -cx(i), -cy(i), -cz(i)));
 }
 
 template <class P>
@@ -155,13 +155,8 @@ static __global__ void k_import_dir(const BoxDev* __restrict__ boxes, int b, int
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
         if (B.flags[n] & FL_SOLID) continue;
         const R v = (R)in[n];
-        if (par == 0 || i == 0) {
-            pop.store(c, i, n, v);
-        } else {
-            const int s = nbr_index(B, n, -cx(i), -cy(i), -cz(i));
-            if (B.flags[s] & FL_SOLID) pop.store(c, i, n, v);
-            else pop.store(c, opp(i), s, v);
-        }
+        if (par == 0 || i == 0) pop.store(c, i, n, v);
+        else pop.store(c, opp(i), nbr_index(B, n, -cx(i), -cy(i), -cz(i)), v);
     }
 }
 

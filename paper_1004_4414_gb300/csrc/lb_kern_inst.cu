@@ -85,9 +85,9 @@ cudaError_t shell_density(cudaStream_t st, const BoxDev* boxes, Shared sh, int r
     return cudaGetLastError();
 }
 
-cudaError_t couple(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int NP) {
+cudaError_t couple(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par, int NP) {
     if (NP <= 0) return cudaSuccess;
-    k_couple<PP><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot);
+    k_couple<PP><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot, par);
     return cudaGetLastError();
 }
 

@@ -298,23 +298,11 @@ __device__ __forceinline__ int nbr_index(const BoxDev& B, int n, int dx, int dy,
     const int x = n % B.nx, y = (n / B.nx) % B.ny, z = n / (B.nx * B.ny);
     return wrapi(x + dx, B.nx) + B.nx * (wrapi(y + dy, B.ny) + B.ny * wrapi(z + dz, B.nz));
 }
-__device__ __forceinline__ int ev_old_owner(const BoxDev& B, int n) {
-    const int m = B.evmark[n];
-    return m ? m - 3 : B.owner[n];
-}
 __device__ __forceinline__ bool old_solid(const BoxDev& B, int n) {
     const int m = B.evmark[n];
     if (m) return (m - 3) != OWN_FLUID;
     return B.flags[n] & FL_SOLID;
 }
-__device__ __forceinline__ bool new_solid(const BoxDev& B, int n) { return B.flags[n] & FL_SOLID; }
-// a marked node whose solid/fluid status changed (not a transfer)
-__device__ __forceinline__ bool status_event(const BoxDev& B, int n) {
-    const int m = B.evmark[n];
-    if (!m) return false;
-    return ((m - 3) != OWN_FLUID) != (bool)(B.flags[n] & FL_SOLID);
-}
-
 // refill of an uncovered node (Eqs. eqn_rho_neu and masscorr): mean density
 // of the neighbours that were fluid, times the mass-correction factor; the
 // surface velocity of the particle that left it.
@@ -376,13 +364,13 @@ __device__ __forceinline__ void node_rel(const BoxDev& B, const Shared& sh, int 
 }
 
 // Cover / uncover.  PAR is the parity of the coming fused step.  Before an
-// even step each node holds its populations in its own slots.  Before an
-// odd step the population of a node that streams in from neighbour z sits
-// in z's slot when both were fluid and in the node's own slot otherwise;
-// when the status of a link end changes, the link's two slots are
-// rearranged so the odd step finds every population where the new status
-// says it is.  The link is handled once: by its lower-index end when both
-// ends changed.
+// even step f_i of a node sits in its own slot i; before an odd step it sits
+// in slot opp(i) of the neighbour x - c_i, whatever that neighbour's status
+// (the even step stores a population reflected at a solid node in that
+// node's slot).  So a status change moves nothing: a covered node gives the
+// momentum of its populations to the particle, an uncovered node gets
+// f^eq(rho_new, u_s) in the same places, and the particle loses the
+// momentum of the created fluid.
 template <class P, int PAR>
 static __global__ void k_remap_apply(const BoxDev* __restrict__ boxes, Shared sh, int rc, int mslot_cur) {
     using R = typename P::real;
@@ -395,99 +383,38 @@ static __global__ void k_remap_apply(const BoxDev* __restrict__ boxes, Shared sh
         const Pop<P> pop(B);
         const R* rcur = reinterpret_cast<const R*>(B.rho[rc]);
         const bool covered = (old == OWN_FLUID);
-        double mom_w[3] = {0, 0, 0};
-        Refill<R> rf;
-        if (!covered) {
-            rf = refill_of<R>(B, sh, w, old, rcur, mslot_cur);
-            sh.ev_rho[(size_t)e * 2 + 0] = (double)rf.rho[0];
-            sh.ev_rho[(size_t)e * 2 + 1] = (double)rf.rho[1];
-            atomicAdd(&sh.counters[ev.y * 2 + 1], 1ull);
-        } else {
-            atomicAdd(&sh.counters[ev.y * 2 + 0], 1ull);
-        }
-        if (PAR == 0) {
-            for (int c = 0; c < 2; c++) {
-                if (covered) {
-#pragma unroll
-                    for (int i = 1; i < 19; i++) {
-                        const R v = pop.load(c, i, w);
-                        mom_w[0] += (double)v * cx(i);
-                        mom_w[1] += (double)v * cy(i);
-                        mom_w[2] += (double)v * cz(i);
-                    }
-                } else {
-                    R resid = R(0);
-#pragma unroll
-                    for (int i = 1; i < 19; i++) {
-                        const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
-                        resid += fe - pop.store(c, i, w, fe);
-                    }
-                    pop.store(c, 0, w, feq_rest<R>(rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
-                }
-            }
-        } else {
-            const int wx = w % B.nx, wy = (w / B.nx) % B.ny, wz = w / (B.nx * B.ny);
-            for (int i = 1; i < 19; i++) {
-                const int z = wrapi(wx + cx(i), B.nx) + B.nx * (wrapi(wy + cy(i), B.ny) + B.ny * wrapi(wz + cz(i), B.nz));
-                const bool zev = status_event(B, z);
-                if (zev && z < w) continue;
-                const bool wo = covered, wn = !covered;
-                const bool zo = !old_solid(B, z), zn = !new_solid(B, z);
-                Refill<R> rz;
-                const bool z_unc = zev && !zo && zn;
-                if (z_unc) rz = refill_of<R>(B, sh, z, ev_old_owner(B, z), rcur, mslot_cur);
-                double mom_z[3] = {0, 0, 0};
-                for (int c = 0; c < 2; c++) {
-                    // a = w, population f_opp(i)(w); b = z, population f_i(z);
-                    // slots sa = A[opp(i)][w], sb = A[i][z]
-                    R va = R(0), vb = R(0);
-                    if (wo) va = zo ? pop.load(c, i, z) : pop.load(c, opp(i), w);
-                    else va = feq_rt<R>(opp(i), rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
-                    if (zo) vb = wo ? pop.load(c, opp(i), w) : pop.load(c, i, z);
-                    else if (zn) vb = feq_rt<R>(i, rz.rho[c], rz.us[0], rz.us[1], rz.us[2]);
-                    if (wo && !wn) {
-                        mom_w[0] += (double)va * cx(opp(i));
-                        mom_w[1] += (double)va * cy(opp(i));
-                        mom_w[2] += (double)va * cz(opp(i));
-                    }
-                    if (zo && !zn) {
-                        mom_z[0] += (double)vb * cx(i);
-                        mom_z[1] += (double)vb * cy(i);
-                        mom_z[2] += (double)vb * cz(i);
-                    }
-                    if (wn && zn) {
-                        pop.store(c, i, z, va);
-                        pop.store(c, opp(i), w, vb);
-                    } else if (wn) {
-                        pop.store(c, opp(i), w, va);
-                    } else if (zn) {
-                        pop.store(c, i, z, vb);
-                    }
-                }
-                if (zo && !zn && zev) {
-                    const int pz = B.owner[z];
-                    double r[3];
-                    node_rel(B, sh, z, pz, r);
-                    add_force_torque(sh, pz, r, mom_z);
-                }
-            }
-            if (!covered) {
-                for (int c = 0; c < 2; c++) {
-                    R resid = R(0);
-#pragma unroll
-                    for (int i = 1; i < 19; i++) {
-                        const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
-                        resid += fe - pop.quant(c, i, fe);
-                    }
-                    pop.store(c, 0, w, feq_rest<R>(rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
-                }
-            }
-        }
+        // node holding f_i of w before the coming step
+        auto src = [&](int i) { return PAR == 0 ? w : nbr_index(B, w, -cx(i), -cy(i), -cz(i)); };
+        auto slot = [&](int i) { return PAR == 0 ? i : opp(i); };
         if (covered) {
+            atomicAdd(&sh.counters[ev.y * 2 + 0], 1ull);
+            double mom_w[3] = {0, 0, 0};
+            for (int c = 0; c < 2; c++) {
+#pragma unroll
+                for (int i = 1; i < 19; i++) {
+                    const R v = pop.load(c, slot(i), src(i));
+                    mom_w[0] += (double)v * cx(i);
+                    mom_w[1] += (double)v * cy(i);
+                    mom_w[2] += (double)v * cz(i);
+                }
+            }
             double r[3];
             node_rel(B, sh, w, nw, r);
             add_force_torque(sh, nw, r, mom_w);
         } else {
+            const Refill<R> rf = refill_of<R>(B, sh, w, old, rcur, mslot_cur);
+            sh.ev_rho[(size_t)e * 2 + 0] = (double)rf.rho[0];
+            sh.ev_rho[(size_t)e * 2 + 1] = (double)rf.rho[1];
+            atomicAdd(&sh.counters[ev.y * 2 + 1], 1ull);
+            for (int c = 0; c < 2; c++) {
+                R resid = R(0);
+#pragma unroll
+                for (int i = 1; i < 19; i++) {
+                    const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
+                    resid += fe - pop.store(c, slot(i), src(i), fe);
+                }
+                pop.store(c, 0, w, feq_rest<R>(rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
+            }
             // the particle loses the momentum of the created fluid
             // (Eq. eqn_ladd_vernichtenunderzeugen, sign from conservation)
             const double rs = (double)rf.rho[0] + (double)rf.rho[1];
@@ -633,8 +560,9 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
 //     Psi^cbar(s + c_i) c_i, torque (s - X) x F;
 //   * every link from a fluid neighbour x = s + c_i to s, direction
 //     j = opp(i).  The fused step stored the post-collision f*_j of x,
-//     reflected, in slot i of x (both parities).  Here it gets the
-//     moving-wall term, b = f*_j - 6 zeta_j rho^c(x) (u_s . c_j) with u_s =
+//     reflected, in slot j of s (even step) or slot i of x (odd step).
+//     Here it gets the moving-wall term, b = f*_j - 6 zeta_j rho^c(x)
+//     (u_s . c_j) with u_s =
 //     U + omega x r at the link midpoint r = x + c_j / 2 - X
 //     (Eq. eqn_ladd_bewegtewand), and the particle receives
 //     (2 f*_j - 6 zeta_j rho^c(x) u_s . c_j) c_j with torque r x F
@@ -649,7 +577,7 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
 constexpr int COUPLE_THREADS = 256;
 template <class P>
 static __global__ void __launch_bounds__(COUPLE_THREADS)
-    k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot) {
+    k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot, int par) {
     using R = typename P::real;
     using S = typename P::st;
     const unsigned FULL = 0xffffffffu;
@@ -691,8 +619,10 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
         const R r2 = mimg_r<R>((R)gz - X2, Lz) + R(0.5) * (R)iz;
         const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
         const R cu6 = -R(6) * (i <= 6 ? wgt<R>(1) : wgt<R>(7)) * (us0 * (R)ix + us1 * (R)iy + us2 * (R)iz);
-        S* const p0 = pop.dir(0, i) + m;
-        S* const p1 = pop.dir(1, i) + m;
+        // the reflected f*_j: after an even step in slot j = opp(i) of s,
+        // after an odd step in slot opp(j) = i of m
+        S* const p0 = par == 0 ? pop.dir(0, opp(i)) + s : pop.dir(0, i) + m;
+        S* const p1 = par == 0 ? pop.dir(1, opp(i)) + s : pop.dir(1, i) + m;
         const R fs0 = pop.ld(p0, 0, i), fs1 = pop.ld(p1, 1, i);
         const R rr = __ldg(rcur + m), rb = __ldg(rcur + N + m);
         R mag = R(0);

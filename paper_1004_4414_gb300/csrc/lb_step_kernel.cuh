@@ -14,12 +14,13 @@
 //   * Populations stay in place with the AA pattern.  Even steps: a node
 //     reads its own 19 slots and writes f*_j to slot opp(j) of itself.  Odd
 //     steps: it reads f_i from slot opp(i) of x - c_i and writes f*_j to slot
-//     j of x + c_j.  A population whose stream target is solid is reflected
-//     into slot opp(j) of the node itself on both parities, which is where
-//     the next step reads it.  Each slot is read once and written once per
-//     step.  Every load and store has its address selected first, so the
-//     path has no branches; neighbour offsets are wrap-aware and computed
-//     once per thread.
+//     j of x + c_j.  A population whose stream target y = x + c_j is solid
+//     is reflected into the slot the next step reads it from: slot j of y
+//     after an even step (the odd step at x reads its f_opp(j) there), slot
+//     opp(j) of x after an odd step.  So the loads of both parities never
+//     depend on the status of a neighbour; only the stores select.  Each
+//     slot is read once and written once per step; neighbour offsets are
+//     wrap-aware and computed once per thread.
 //   * A CTA owns a column tile of 32 x TY nodes (one warp per x row: all
 //     population traffic is coalesced along x) and marches through a chunk
 //     of z planes.  Psi and the node flags of the tile plus a one-node ring
@@ -259,10 +260,8 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 f[c][0] = pop.ld_rest(c, n);
 #pragma unroll
                 for (int i = 1; i < 19; i++) {
-                    // own slot i, or (odd steps, fluid source) slot opp(i) of x - c_i
-                    const S* p;
-                    if (PAR == 0) p = pop.dir(c, i) + n;
-                    else p = ((smask >> opp(i)) & 1u) ? pop.dir(c, i) + n : pop.dir(c, opp(i)) + (n + off(opp(i)));
+                    // even steps: own slot i; odd steps: slot opp(i) of x - c_i
+                    const S* p = PAR == 0 ? pop.dir(c, i) + n : pop.dir(c, opp(i)) + (n + off(opp(i)));
                     f[c][i] = pop.ld(p, c, i);
                 }
             }
@@ -342,13 +341,16 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 const R a0 = R(1) - R(1.5) * uu;
                 const R rw1 = rho[c] * wgt<R>(1), rw7 = rho[c] * wgt<R>(7);
                 R resid = R(0), sent = R(0), fe_sum = R(0), self = R(0);
-                // store f*_j: to its stream target, or reflected into slot
-                // opp(j) of this node when the target is solid
+                // store f*_j where the next step reads it.  Stream target
+                // y = x + c_j fluid: even steps slot opp(j) of x, odd steps
+                // slot j of y.  Target solid (bounce-back, f_opp(j) of x at
+                // t+1): even steps slot j of y, which the odd step at x reads
+                // for direction opp(j); odd steps slot opp(j) of x.
                 auto send = [&](auto JC, R fs) {
                     constexpr int j = decltype(JC)::value;
                     const bool solid = (smask >> j) & 1u;
                     S* p;
-                    if (PAR == 0) p = pop.dir(c, opp(j)) + n;
+                    if (PAR == 0) p = solid ? pop.dir(c, j) + (n + off(j)) : pop.dir(c, opp(j)) + n;
                     else p = solid ? pop.dir(c, opp(j)) + n : pop.dir(c, j) + (n + off(j));
                     const R q = pop.st(p, c, j, fs);
                     if constexpr (P::dev) resid += fs - q;
