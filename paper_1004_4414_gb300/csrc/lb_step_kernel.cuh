@@ -243,7 +243,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
 #pragma unroll
             for (int q = 0; q < 9; q++) mid[c][q] = R(0);
         R upx_[2][5], dnx_[2][5];  // values leaving the tile through x (edge lanes)
-        R rest_pre[2] = {R(0), R(0)}, resid_c[2] = {R(0), R(0)}, sent_c[2] = {R(0), R(0)}, self_c[2] = {R(0), R(0)};
+        R rest_pre[2] = {R(0), R(0)}, resid_c[2] = {R(0), R(0)}, self_c[2] = {R(0), R(0)};
 
         const uint8_t fl = active ? FLG(sc_, ly + 1, lx + 1) : FL_SOLID;
         const bool fluid = active && !(fl & FL_SOLID);
@@ -292,9 +292,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 R sx = 0, sy = 0, sz = 0;
 #pragma unroll
                 for (int i = 1; i < 19; i++) {
-                    
- const R p = (is_axis(i) ? wax : wdg) * PSI(slot_dz(cz(i)), cb, ly + 1 + cy(i), lx + 1 + cx(i));
-
+                    const R p = (is_axis(i) ? wax : wdg) * PSI(slot_dz(cz(i)), cb, ly + 1 + cy(i), lx + 1 + cx(i));
                     if (cx(i) > 0) sx += p;
                     if (cx(i) < 0) sx -= p;
                     if (cy(i) > 0) sy += p;
@@ -340,7 +338,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 const R uu = ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c];
                 const R a0 = R(1) - R(1.5) * uu;
                 const R rw1 = rho[c] * wgt<R>(1), rw7 = rho[c] * wgt<R>(7);
-                R resid = R(0), sent = R(0), fe_sum = R(0), self = R(0);
+                R resid = R(0), fe_sum = R(0), self = R(0);
                 // store f*_j where the next step reads it.  Stream target
                 // y = x + c_j fluid: even steps slot opp(j) of x, odd steps
                 // slot j of y.  Target solid (bounce-back, f_opp(j) of x at
@@ -354,7 +352,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     else p = solid ? pop.dir(c, opp(j)) + n : pop.dir(c, j) + (n + off(j));
                     const R q = pop.st(p, c, j, fs);
                     if constexpr (P::dev) resid += fs - q;
-                    sent += q;
                     const R qf = solid ? R(0) : q;
                     self += solid ? q : R(0);
                     constexpr int gq = grp_of(j);
@@ -371,9 +368,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     const R cu2 = cu * cu;
                     const R E = a0 + R(4.5) * cu2;
                     const R O = cu * (R(3) + R(4.5) * cu2 - R(4.5) * uu);
-                    
- const R fep = rw * (E + O), fem = rw * (E - O);
-
+                    const R fep = rw * (E + O), fem = rw * (E - O);
                     fe_sum += fep + fem;
                     send(std::integral_constant<int, j>{}, omt * f[c][j] + itc * fep);
                     send(std::integral_constant<int, opp(j)>{}, omt * f[c][opp(j)] + itc * fem);
@@ -393,18 +388,15 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 // finite precision)
                 rest_pre[c] = omt * f[c][0] + itc * (rho[c] - fe_sum);
                 resid_c[c] = resid;
-                sent_c[c] = sent;
                 self_c[c] = self;
             }
             // x shift of the density scatter (all lanes take part)
 #pragma unroll
             for (int q = 0; q < 5; q++) {
-
                 R fromL = __shfl_up_sync(FULL, up[q], 1);
                 R fromR = __shfl_down_sync(FULL, dn[q], 1);
                 if (lx == 0) fromL = R(0);
                 if (lx == 31) fromR = R(0);
-
                 mid[c][q] += fromL + fromR;
                 upx_[c][q] = up[q];
                 dnx_[c][q] = dn[q];
@@ -417,9 +409,10 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             for (int c = 0; c < 2; c++) {
                 const R q0 = pop.st_rest(c, n, rest_pre[c] + resid_c[c]);
                 mid[c][0] += q0 + self_c[c];
-                const R sent = sent_c[c] + q0;
-                if (c == 0) msum0 += sent;
-                else msum1 += sent;
+                // the 19 stored values sum to rho^c: the collision conserves
+                // mass and the rest slot absorbs the rounding of the others
+                if (c == 0) msum0 += rho[0];
+                else msum1 += rho[1];
             }
         }
 
