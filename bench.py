@@ -296,9 +296,43 @@ def run_ours(args, rank, world, device):
            "what": "lb_import_state of every box from pinned host memory + lb_step(K) + "
                    "lb_export_state of every box into pinned host memory"}
     ob = sim.observables(0)
+    n_fluid = sum(sim.observables(b)["n_fluid"] for b in range(sim.nb))
+    seq = None
+    if sim.nb > 1 and not args.no_sequential:
+        seq_value, seq_ms = sequential_boxes(args, boxes, seed + 1000 * rank, device)
+        seq = {"sequential_mlups": seq_value, "batched_mlups": value, "ratio": value / seq_value,
+               "sequential_ms": seq_ms, "what": "the same boxes and states, one handle per box, run one after another"}
     return dict(value=value, ms=ms_max, fused_ms=avg_ms, fused_n=fused_n, bytes=bytes_launch, achieved=achieved,
                 peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=total_launches, nodes=nodes,
-                n_particles=sum(sim.n_particles), error=ob["error"], n_fluid=ob["n_fluid"], tiling=tiling)
+                n_particles=sum(sim.n_particles), error=ob["error"], n_fluid=n_fluid, tiling=tiling, seq=seq)
+
+
+def sequential_boxes(args, boxes, seed, device):
+    """The boxes of a batch run one after another, each on its own handle
+    (its own autotuned tiling), from the same seeded states (box b of a
+    batch uses seed + b): MLUPS over the summed CUDA-event time of K steps."""
+    import torch
+
+    from paper_1004_4414_gb300 import Simulation
+    from paper_1004_4414_gb300.autotune import autotune
+
+    updates, ms = 0, 0.0
+    for b, box in enumerate(boxes):
+        sim = Simulation([box], device=device)
+        autotune(sim)
+        sim.init_from_seed(seed + b)
+        sim.step(args.warmup)
+        sim.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(args.steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize(device)
+        ms += e0.elapsed_time(e1)
+        updates += sim.n_nodes[0] * args.steps
+        sim.close()
+    return updates / (ms * 1e-3) / 1e6, ms
 
 
 def oracle_sample(workload, budget_s=12.0):
@@ -336,6 +370,7 @@ def main():
     ap.add_argument("--workload", default="c256", choices=["c256", "c256p", "c128", "c512", "c32", "batch"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sequential", action="store_true", help="batch: skip the one-box-at-a-time comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -395,6 +430,7 @@ def main():
         "e2e": r["e2e"],
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],
+        "batch_vs_sequential": r["seq"],
         "device_error": r["error"],
     }
     print(json.dumps(line))
