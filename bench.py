@@ -319,6 +319,7 @@ def sequential_boxes(args, boxes, seed, device):
     updates, ms = 0, 0.0
     for b, box in enumerate(boxes):
         sim = Simulation([box], device=device)
+        sim.init_from_seed(seed + b)
         autotune(sim)
         sim.init_from_seed(seed + b)
         sim.step(args.warmup)
