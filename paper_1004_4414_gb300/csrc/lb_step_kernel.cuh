@@ -235,16 +235,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
         };
         auto slot_dz = [&](int dz) { return dz < 0 ? sm_ : (dz > 0 ? sp_ : sc_); };
 
-        // per-group partial sums of the values this node sends; after the x
-        // shuffle mid[c][g] holds everything that arrives in this column
-        R mid[2][9];
-#pragma unroll
-        for (int c = 0; c < 2; c++)
-#pragma unroll
-            for (int q = 0; q < 9; q++) mid[c][q] = R(0);
-        R upx_[2][5], dnx_[2][5];  // values leaving the tile through x (edge lanes)
-        R rest_pre[2] = {R(0), R(0)}, resid_c[2] = {R(0), R(0)}, self_c[2] = {R(0), R(0)};
-
         const uint8_t fl = active ? FLG(sc_, ly + 1, lx + 1) : FL_SOLID;
         const bool fluid = active && !(fl & FL_SOLID);
         unsigned smask = 0;  // bit i: x + c_i is solid
@@ -327,9 +317,16 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
         }
 
         const unsigned FULL = 0xffffffffu;
+        // Each component's density scatter is finished inside its own
+        // iteration, so its partial sums do not stay live across both.
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            R up[5], dn[5];
+            // per-group partial sums of the values this node sends (mid: no x
+            // move; up / dn: to x + 1 / x - 1); after the x shuffle mid[g]
+            // holds everything that arrives in this column
+            R mid[9], up[5], dn[5];
+#pragma unroll
+            for (int q = 0; q < 9; q++) mid[q] = R(0);
 #pragma unroll
             for (int q = 0; q < 5; q++) up[q] = dn[q] = R(0);
             if (fluid) {
@@ -355,7 +352,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     const R qf = solid ? R(0) : q;
                     self += solid ? q : R(0);
                     constexpr int gq = grp_of(j);
-                    if (cx(j) == 0) mid[c][gq] += qf;
+                    if (cx(j) == 0) mid[gq] += qf;
                     else if (cx(j) > 0) up[gq] += qf;
                     else dn[gq] += qf;
                 };
@@ -386,46 +383,33 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 // rest population: its equilibrium is rho minus the other 18
                 // (equal to Eq. Equil in exact arithmetic; keeps mass exact in
                 // finite precision)
-                rest_pre[c] = omt * f[c][0] + itc * (rho[c] - fe_sum);
-                resid_c[c] = resid;
-                self_c[c] = self;
+                // rest populations; in deviation storage the rest population
+                // absorbs the rounding of the 18 stored values, so node mass
+                // is exact
+                const R q0 = pop.st_rest(c, n, omt * f[c][0] + itc * (rho[c] - fe_sum) + resid);
+                mid[0] += q0 + self;
+                // the 19 stored values sum to rho^c: the collision conserves
+                // mass and the rest slot absorbs the rounding of the others
+                if (c == 0) msum0 += rho[0];
+                else msum1 += rho[1];
             }
-            // x shift of the density scatter (all lanes take part)
+            // x shift (all lanes take part)
 #pragma unroll
             for (int q = 0; q < 5; q++) {
                 R fromL = __shfl_up_sync(FULL, up[q], 1);
                 R fromR = __shfl_down_sync(FULL, dn[q], 1);
                 if (lx == 0) fromL = R(0);
                 if (lx == 31) fromR = R(0);
-                mid[c][q] += fromL + fromR;
-                upx_[c][q] = up[q];
-                dnx_[c][q] = dn[q];
+                mid[q] += fromL + fromR;
             }
-        }
-        // rest populations; in deviation storage the rest population absorbs
-        // the rounding of the 18 stored values, so node mass is exact
-        if (fluid) {
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const R q0 = pop.st_rest(c, n, rest_pre[c] + resid_c[c]);
-                mid[c][0] += q0 + self_c[c];
-                // the 19 stored values sum to rho^c: the collision conserves
-                // mass and the rest slot absorbs the rounding of the others
-                if (c == 0) msum0 += rho[0];
-                else msum1 += rho[1];
-            }
-        }
-
-        // values leaving the tile through x: the first lane sends left, the
-        // last active lane sends right
-        if (active && (lx == 0 || lx == w - 1)) {
-            const int gxs = lx == 0 ? (x0 == 0 ? nx - 1 : x0 - 1) : (x0 + w >= nx ? x0 + w - nx : x0 + w);
-#pragma unroll
-            for (int c = 0; c < 2; c++)
+            // values leaving the tile through x: the first lane sends left,
+            // the last active lane sends right
+            if (active && (lx == 0 || lx == w - 1)) {
+                const int gxs = lx == 0 ? (x0 == 0 ? nx - 1 : x0 - 1) : (x0 + w >= nx ? x0 + w - nx : x0 + w);
 #pragma unroll
                 for (int q = 0; q < 5; q++) {
-                    const R v = lx == 0 ? dnx_[c][q] : upx_[c][q];
-                    const R v2 = (lx == 0 && lx == w - 1) ? upx_[c][q] : R(0);  // a one-node-wide tile sends both ways
+                    const R v = lx == 0 ? dn[q] : up[q];
+                    const R v2 = (lx == 0 && lx == w - 1) ? up[q] : R(0);  // a one-node-wide tile sends both ways
                     const int dy = grp_dy(q), dz = grp_dz(q);
                     int gy = y + dy;
                     gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
@@ -438,35 +422,31 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                         red_add(&rnext[(size_t)c * N + base + gxr], v2);
                     }
                 }
-        }
-        // y shift: rows exchange through shared memory; values leaving the
-        // tile through y are reduced into the ring rows directly
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            acc[1][c] += mid[c][0];
-            acc[2][c] += mid[c][3];
-            acc[0][c] += mid[c][4];
+            }
+            // y shift: rows exchange through shared memory; values leaving
+            // the tile through y are reduced into the ring rows directly
+            acc[1][c] += mid[0];
+            acc[2][c] += mid[3];
+            acc[0][c] += mid[4];
 #pragma unroll
             for (int q = 1; q < 9; q++) {
                 if (yb_of(q) < 0) continue;
-                YB(yb_of(q), c, ly, lx) = mid[c][q];
+                YB(yb_of(q), c, ly, lx) = mid[q];
             }
-        }
-        if (active && (ly == 0 || ly == h - 1)) {
-#pragma unroll
-            for (int c = 0; c < 2; c++)
+            if (active && (ly == 0 || ly == h - 1)) {
 #pragma unroll
                 for (int q = 1; q < 9; q++) {
                     if (yb_of(q) < 0) continue;
                     const int dy = grp_dy(q), dz = grp_dz(q);
                     if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
-                    if (mid[c][q] == R(0)) continue;
+                    if (mid[q] == R(0)) continue;
                     int gy = y + dy;
                     gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
                     int gz = z + dz;
                     gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
-                    red_add(&rnext[(size_t)c * N + x + nx * (gy + ny * gz)], mid[c][q]);
+                    red_add(&rnext[(size_t)c * N + x + nx * (gy + ny * gz)], mid[q]);
                 }
+            }
         }
         __syncthreads();
 
