@@ -60,6 +60,7 @@ int validate(const lb_params* bx, int nb) {
     for (int b = 0; b < nb; b++) {
         const lb_params& p = bx[b];
         if (p.nx < 1 || p.ny < 1 || p.nz < 1) return LB_EINVAL;
+        if (p.nx > 65535 || p.ny > 65535 || p.nz > 65535) return LB_EINVAL;
         if ((double)p.nx * p.ny * p.nz >= 2147483647.0) return LB_EINVAL;
         if (!(p.tau[0] > 0.5) || !(p.tau[1] > 0.5)) return LB_EINVAL;
         if (!(p.rho0 > 0.0) || !(p.radius > 0.0) || !(p.particle_density > 0.0)) return LB_EINVAL;
@@ -217,7 +218,7 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
         for (int b = 0; b < nb; b++) rmax = bx[b].radius > rmax ? bx[b].radius : rmax;
         sh.shell_cap = (int)(12.0 * (rmax + 1.0) * (rmax + 1.0)) + 64;
     }
-    sh.shell_list = cv.take<int>((size_t)NPa * sh.shell_cap);
+    sh.shell_list = cv.take<int4>((size_t)NPa * sh.shell_cap);
     sh.shell_n = cv.take<int>(NPa);
     sh.err = cv.take<int>(1);
     sh.counters = cv.take<unsigned long long>((size_t)nb * 2);

@@ -112,7 +112,8 @@ struct Shared {
     double* ev_rho;             // [cap][2] refill density
     int* ev_count;              // [1]
     int ev_cap;
-    int* shell_list;            // [NP][shell_cap] shell nodes of each particle (this step)
+    int4* shell_list;           // [NP][shell_cap] shell nodes of each particle (this step):
+                                // (node, mask of fluid neighbours, x | y << 16, z)
     int* shell_n;               // [NP]
     int shell_cap;
     int* err;                   // [1] sticky error bits

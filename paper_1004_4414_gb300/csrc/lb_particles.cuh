@@ -486,11 +486,15 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
-    // virtual density of one shell node n of p
-    auto process = [&](int n) {
+    const int scap = sh.shell_cap;
+    int4* __restrict__ slist = sh.shell_list + (size_t)p * scap;
+    // virtual density of one shell node n of p, and its entry k of p's
+    // shell list (node, mask of fluid neighbours, coordinates)
+    auto process = [&](int n, int k) {
         const int gx = n % nx, gy = (n / nx) % ny, gz = n / (nx * ny);
         R s0 = R(0), s1 = R(0);
         int cnt = 0;
+        unsigned fmask = 0;  // bit i: n + c_i is fluid (a link)
 #pragma unroll
         for (int i = 1; i < 19; i++) {
             const int m = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
@@ -498,8 +502,10 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
                 s0 += rcur[m];
                 s1 += rcur[N + m];
                 cnt++;
+                fmask |= 1u << i;
             }
         }
+        if (k < scap) slist[k] = make_int4(n, (int)fmask, gx | (gy << 16), gz);
         R r0 = s0 / (R)cnt, r1 = s1 / (R)cnt;
         if (col > R(0)) r0 += col;
         else if (col < R(0)) r1 -= col;
@@ -511,8 +517,6 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     // Shell nodes are queued as they are found and handled 32 at a time;
     // they are also listed for k_couple.
     const float lim = (R_ + 0.5f) * (R_ + 0.5f);
-    const int cap = sh.shell_cap;
-    int* __restrict__ list = sh.shell_list + (size_t)p * cap;
     int nq = 0, done = 0;  // warp-uniform: queue length (< 64), nodes handled
     for (int base = 0;; base += 32) {
         const int idx = base + lane;
@@ -537,17 +541,14 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
             const int item = lane < k ? s_q[wib][nq - k + lane] : -1;
             __syncwarp();
             nq -= k;
-            if (item >= 0) {
-                if (done + lane < cap) list[done + lane] = item;
-                process(item);
-            }
+            if (item >= 0) process(item, done + lane);
             done += k;
         }
         if (last && nq == 0) break;
     }
     if (lane == 0) {
-        sh.shell_n[p] = done < cap ? done : cap;
-        if (done > cap) set_err(sh.err, ERR_OVERFLOW);
+        sh.shell_n[p] = done < scap ? done : scap;
+        if (done > scap) set_err(sh.err, ERR_OVERFLOW);
     }
 }
 
@@ -591,7 +592,6 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const R* __restrict__ rcur = reinterpret_cast<const R*>(B.rho[rc]);
     R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);
-    const uint8_t* __restrict__ flags = B.flags;
     double* __restrict__ mass_acc = B.mass_acc;
     const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
     const R wax = (R)B.scw_axis, wdg = (R)B.scw_diag;
@@ -603,16 +603,17 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     R dm0 = R(0), dm1 = R(0);
     // the shell nodes found by k_shell_density in this step
     const int ns = sh.shell_n[p];
-    const int* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
+    const int4* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
     // (1) links: one item per (direction i, shell node s), direction-major,
     // so that neighbouring threads touch neighbouring nodes of one array
     for (int k = threadIdx.x; k < 18 * ns; k += COUPLE_THREADS) {
         const int i = 1 + k / ns;
-        const int s = list[k - (i - 1) * ns];
+        const int4 e = list[k - (i - 1) * ns];
+        if (!((e.y >> i) & 1)) continue;  // s + c_i is solid: no link
+        const int s = e.x;
         const int ix = kC[i][0], iy = kC[i][1], iz = kC[i][2];
-        const int gx = s % nx, gy = (s / nx) % ny, gz = s / (nx * ny);
+        const int gx = e.z & 0xffff, gy = e.z >> 16, gz = e.w;
         const int m = wrap1(gx + ix, nx) + nx * (wrap1(gy + iy, ny) + ny * wrap1(gz + iz, nz));
-        if (__ldg(flags + m) & FL_SOLID) continue;
         // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
         const R r0 = mimg_r<R>((R)gx - X0, Lx) + R(0.5) * (R)ix;
         const R r1 = mimg_r<R>((R)gy - X1, Ly) + R(0.5) * (R)iy;
@@ -655,8 +656,9 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     }
     // (2) the Shan-Chen force of the virtual fluid at each shell node
     for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) {
-        const int s = list[k];
-        const int gx = s % nx, gy = (s / nx) % ny, gz = s / (nx * ny);
+        const int4 e = list[k];
+        const int s = e.x;
+        const int gx = e.z & 0xffff, gy = e.z >> 16, gz = e.w;
         R sr0 = R(0), sr1 = R(0), sr2 = R(0), sb0 = R(0), sb1 = R(0), sb2 = R(0);
 #pragma unroll
         for (int i = 1; i < 19; i++) {
