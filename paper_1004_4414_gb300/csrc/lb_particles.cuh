@@ -190,14 +190,17 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
         for (int a = 0; a < 3; a++) s_rq[wib][k][a] = mimgf(qf.X[a] - pf.X[a], Lf[a]);
     }
     __syncwarp();
-    const int half = (int)ceil(R) + 2;
+    // window: every node within R + 1.5 of the centre (a node owned before
+    // the move lies within R + |U| <= R + 1 of the new centre; the 0.5 of
+    // slack covers the FP32 centre)
+    const float reach = (float)R + 1.5f;
     int lo[3], span[3];
     float off[3];  // X_p - lo: node (lo + k) sits at k - off from the centre
     const int dims[3] = {B.nx, B.ny, B.nz};
     for (int a = 0; a < 3; a++) {
-        lo[a] = (int)floorf(pf.X[a]) - half;
+        lo[a] = (int)ceilf(pf.X[a] - reach);
         off[a] = pf.X[a] - (float)lo[a];
-        span[a] = 2 * half + 1;
+        span[a] = (int)floorf(pf.X[a] + reach) - lo[a] + 1;
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
@@ -221,7 +224,7 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
                                     mimg((double)gz - C[2], L[2]));
                 };
                 const int n = gx + B.nx * (gy + B.ny * gz);
-                const int own = B.owner[n];
+                const int own = __ldg(B.owner + n);
                 if (own != OWN_WALL) {
                     double d2p = -1.0;
                     bool inside;
@@ -475,14 +478,16 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     const size_t N = (size_t)B.N;
     const float R_ = (float)B.radius;
     const R col = (R)sh.color[p];
-    const int half = (int)ceilf(R_) + 1;
+    // window: every node within R + 0.5 of the centre (the shell nodes of p
+    // lie within R; the 0.5 of slack covers the FP32 centre)
+    const float reach = R_ + 0.5f;
     int lo[3], span[3];
     float off[3];  // X - lo: node (lo + k) sits at k - off from the centre
     const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; a++) {
-        lo[a] = (int)floorf(pf.X[a]) - half;
+        lo[a] = (int)ceilf(pf.X[a] - reach);
         off[a] = pf.X[a] - (float)lo[a];
-        span[a] = 2 * half + 1;
+        span[a] = (int)floorf(pf.X[a] + reach) - lo[a] + 1;
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
@@ -528,7 +533,7 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
                         dz = mimgf((float)kz - off[2], (float)nz);
             if (dx * dx + dy * dy + dz * dz <= lim) {
                 n = wrapi(lo[0] + kx, nx) + nx * (wrapi(lo[1] + ky, ny) + ny * wrapi(lo[2] + kz, nz));
-                take = (flags[n] & FL_SHELL) && owner[n] == p;
+                take = (__ldg(flags + n) & FL_SHELL) && __ldg(owner + n) == p;
             }
         }
         const unsigned m = __ballot_sync(FULL, take);
