@@ -115,6 +115,7 @@ struct lb_handle {
     BoxDev* d_boxes = nullptr;
     TileDev* d_tiles = nullptr;
     int max_tiles = 0, ntiles = 0, ty = 8, cz = 32;
+    int tau1 = 0;  // every box has tau^r = tau^b = 1: the specialised fused kernel
     Shared sh{};
     int NP = 0, total_cells = 0;
     std::vector<int> pstart, npb, cell_off;
@@ -346,7 +347,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         e1 = h->evpool[h->ev_used++];
         CK(cudaEventRecord(e0, st));
     }
-    CK(h->ops->step(par, h->ty, h->ntiles, st, h->d_boxes, h->d_tiles, h->sh, rc, rn, rz, mnext));
+    CK(h->ops->step(par, h->ty, h->tau1, h->ntiles, st, h->d_boxes, h->d_tiles, h->sh, rc, rn, rz, mnext));
     launches++;
     if (prof) {
         CK(cudaEventRecord(e1, st));
@@ -604,6 +605,9 @@ int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t
     h->ws = (char*)d_workspace;
     h->ws_bytes = bytes;
     h->has_walls.assign(n_boxes, 0);
+    h->tau1 = 1;
+    for (int b = 0; b < n_boxes; b++)
+        if (boxes[b].tau[0] != 1.0 || boxes[b].tau[1] != 1.0) h->tau1 = 0;
     layout(h, boxes, n_boxes, h->ws);
     fill_params(h);
     if (h->ops->setup() != cudaSuccess || cudaHostAlloc((void**)&h->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||

@@ -27,45 +27,58 @@ using RR = typename PP::real;
 namespace {
 constexpr int EV_GRID = 304, EV_BLOCK = 256, NODE_GRID = 1216, NODE_BLOCK = 256;
 
-template <int PAR, int TY>
+template <int PAR, int TY, bool T1>
 cudaError_t step_t(int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles, Shared sh, int rc, int rn,
                    int rz, int mslot) {
     const size_t smem = StepSmem<RR, TY>::bytes;
-    k_step<PP, PAR, TY><<<ntiles, dim3(32, TY), smem, st>>>(boxes, tiles, sh, rc, rn, rz, mslot);
+    k_step<PP, PAR, TY, T1><<<ntiles, dim3(32, TY), smem, st>>>(boxes, tiles, sh, rc, rn, rz, mslot);
     return cudaGetLastError();
 }
 
-template <int PAR, int TY>
+template <int PAR, int TY, bool T1>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(k_step<PP, PAR, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step<PP, PAR, TY, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)StepSmem<RR, TY>::bytes);
 }
 
-cudaError_t setup() {
+template <bool T1>
+cudaError_t setup_t() {
     cudaError_t e = cudaSuccess;
-    cudaError_t r[6] = {set_attr<0, 4>(), set_attr<1, 4>(), set_attr<0, 8>(), set_attr<1, 8>(), set_attr<0, 16>(),
-                        set_attr<1, 16>()};
+    cudaError_t r[6] = {set_attr<0, 4, T1>(), set_attr<1, 4, T1>(), set_attr<0, 8, T1>(),
+                        set_attr<1, 8, T1>(), set_attr<0, 16, T1>(), set_attr<1, 16, T1>()};
     for (auto x : r)
         if (x != cudaSuccess) e = x;
     return e;
+}
+
+cudaError_t setup() {
+    const cudaError_t a = setup_t<false>(), b = setup_t<true>();
+    return a != cudaSuccess ? a : b;
 }
 
 size_t step_smem(int ty) {
     return ty == 4 ? StepSmem<RR, 4>::bytes : (ty == 8 ? StepSmem<RR, 8>::bytes : StepSmem<RR, 16>::bytes);
 }
 
-cudaError_t step(int par, int ty, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles, Shared sh,
-                 int rc, int rn, int rz, int mslot) {
-    if (ntiles <= 0) return cudaSuccess;
+template <bool T1>
+cudaError_t step_tau(int par, int ty, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
+                     Shared sh, int rc, int rn, int rz, int mslot) {
     switch (ty * 2 + par) {
-        case 8: return step_t<0, 4>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 9: return step_t<1, 4>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 16: return step_t<0, 8>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 17: return step_t<1, 8>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 32: return step_t<0, 16>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 33: return step_t<1, 16>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 8: return step_t<0, 4, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 9: return step_t<1, 4, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 16: return step_t<0, 8, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 17: return step_t<1, 8, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 32: return step_t<0, 16, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 33: return step_t<1, 16, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t step(int par, int ty, int tau1, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
+                 Shared sh, int rc, int rn, int rz, int mslot) {
+    if (ntiles <= 0) return cudaSuccess;
+    return tau1 ? step_tau<true>(par, ty, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot)
+                : step_tau<false>(par, ty, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
 }
 
 cudaError_t remap_apply(int par, cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int mslot_cur) {

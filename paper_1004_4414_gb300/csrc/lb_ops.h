@@ -11,7 +11,7 @@ struct LbOps {
     size_t real_size;
     cudaError_t (*setup)();
     size_t (*step_smem)(int ty);
-    cudaError_t (*step)(int par, int ty, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
+    cudaError_t (*step)(int par, int ty, int tau1, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
                         Shared sh, int rc, int rn, int rz, int mslot);
     cudaError_t (*remap_apply)(int par, cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int mslot_cur);
     cudaError_t (*remap_finish)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc);

@@ -301,7 +301,8 @@ def test_deviation_storage(prec, eps):
     """16-bit deviation storage: each stored population carries a relative
     error of at most the unit roundoff u of its deviation d = f/zeta - rho_ref,
     so a population deviates by <= zeta |d| u per step; the FP32 rest
-    population absorbs the rounding so mass is conserved to FP32 level."""
+    population absorbs the 16-bit rounding, so mass is conserved up to FP32
+    rounding."""
     shape = (32, 24, 20)
     nx, ny, nz = shape
     P = np.zeros((1, 9))
@@ -323,4 +324,8 @@ def test_deviation_storage(prec, eps):
     err = np.max(np.abs(a["f"] - b["f"]))
     assert err < tol, (err, tol)
     ob = s.observables()
-    assert np.all(np.abs(ob["mass"] - m0) / m0 < 2e-6)
+    # mass: per node and step, the 18 reconstructions zeta (rho_ref + d) and
+    # the three roundings of the FP32 rest slot add at most 4 * 2^-24 rho;
+    # on this layered state identical nodes round alike, so the worst case
+    # adds up coherently over the 50 steps
+    assert np.all(np.abs(ob["mass"] - m0) / m0 < steps * 4 * 2.0 ** -24)
