@@ -610,54 +610,90 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const int ns = sh.shell_n[p];
     const int4* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
     // (1) links: one item per (direction i, shell node s), direction-major,
-    // so that neighbouring threads touch neighbouring nodes of one array
-    for (int k = threadIdx.x; k < 18 * ns; k += COUPLE_THREADS) {
-        const int i = 1 + k / ns;
-        const int4 e = list[k - (i - 1) * ns];
-        if (!((e.y >> i) & 1)) continue;  // s + c_i is solid: no link
-        const int s = e.x;
-        const int ix = kC[i][0], iy = kC[i][1], iz = kC[i][2];
-        const int gx = e.z & 0xffff, gy = e.z >> 16, gz = e.w;
-        const int m = wrap1(gx + ix, nx) + nx * (wrap1(gy + iy, ny) + ny * wrap1(gz + iz, nz));
-        // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
-        const R r0 = mimg_r<R>((R)gx - X0, Lx) + R(0.5) * (R)ix;
-        const R r1 = mimg_r<R>((R)gy - X1, Ly) + R(0.5) * (R)iy;
-        const R r2 = mimg_r<R>((R)gz - X2, Lz) + R(0.5) * (R)iz;
-        const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
-        const R cu6 = -R(6) * (i <= 6 ? wgt<R>(1) : wgt<R>(7)) * (us0 * (R)ix + us1 * (R)iy + us2 * (R)iz);
-        // the reflected f*_j: after an even step in slot j = opp(i) of s,
-        // after an odd step in slot opp(j) = i of m
-        S* const p0 = par == 0 ? pop.dir(0, opp(i)) + s : pop.dir(0, i) + m;
-        S* const p1 = par == 0 ? pop.dir(1, opp(i)) + s : pop.dir(1, i) + m;
-        const R fs0 = pop.ld(p0, 0, i), fs1 = pop.ld(p1, 1, i);
-        const R rr = __ldg(rcur + m), rb = __ldg(rcur + N + m);
-        R mag = R(0);
+    // so that neighbouring threads touch neighbouring nodes of one array.
+    // Each thread takes U items at a time and issues all their loads before
+    // any store, so that U independent chains are in flight.
+    constexpr int U = 4;
+    const int nitems = 18 * ns;
+    for (int k0 = threadIdx.x; k0 < nitems; k0 += U * COUPLE_THREADS) {
+        int iu[U], mu[U];
+        S* pu0[U];
+        S* pu1[U];
+        R fsu0[U], fsu1[U], rru[U], rbu[U];
+        int4 eu[U];
+        bool ok[U];
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const R fs = c == 0 ? fs0 : fs1;
-            const R wall = cu6 * (c == 0 ? rr : rb);
-            if (wall != R(0)) {
-                const R b = fs - wall;
-                const R q = pop.st(c == 0 ? p0 : p1, c, i, b);
-                R dr = q - fs;
-                if constexpr (P::dev) {
-                    const R res = b - q;
-                    atomicAdd(&pop.f0[(size_t)c * N + m], res);
-                    dr += res;
-                }
-                atomicAdd(&rnext[(size_t)c * N + m], dr);
-                if (c == 0) dm0 += dr;
-                else dm1 += dr;
+        for (int u = 0; u < U; u++) {
+            const int k = k0 + u * COUPLE_THREADS;
+            ok[u] = k < nitems;
+            iu[u] = 1;
+            if (ok[u]) {
+                iu[u] = 1 + k / ns;
+                eu[u] = list[k - (iu[u] - 1) * ns];
             }
-            mag += R(2) * fs - wall;
         }
-        const R F0 = -mag * (R)ix, F1 = -mag * (R)iy, F2 = -mag * (R)iz;
-        acc[0] += F0;
-        acc[1] += F1;
-        acc[2] += F2;
-        acc[3] += r1 * F2 - r2 * F1;
-        acc[4] += r2 * F0 - r0 * F2;
-        acc[5] += r0 * F1 - r1 * F0;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int i = iu[u];
+            ok[u] = ok[u] && ((eu[u].y >> i) & 1);  // s + c_i fluid: a link
+            mu[u] = 0;
+            pu0[u] = pu1[u] = nullptr;
+            fsu0[u] = fsu1[u] = rru[u] = rbu[u] = R(0);
+            if (ok[u]) {
+                const int s = eu[u].x;
+                const int gx = eu[u].z & 0xffff, gy = eu[u].z >> 16, gz = eu[u].w;
+                const int m = wrap1(gx + kC[i][0], nx) + nx * (wrap1(gy + kC[i][1], ny) + ny * wrap1(gz + kC[i][2], nz));
+                mu[u] = m;
+                // the reflected f*_j: after an even step in slot j = opp(i)
+                // of s, after an odd step in slot opp(j) = i of m
+                pu0[u] = par == 0 ? pop.dir(0, opp(i)) + s : pop.dir(0, i) + m;
+                pu1[u] = par == 0 ? pop.dir(1, opp(i)) + s : pop.dir(1, i) + m;
+                fsu0[u] = pop.ld(pu0[u], 0, i);
+                fsu1[u] = pop.ld(pu1[u], 1, i);
+                rru[u] = __ldg(rcur + m);
+                rbu[u] = __ldg(rcur + N + m);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (!ok[u]) continue;
+            const int i = iu[u], m = mu[u];
+            const int ix = kC[i][0], iy = kC[i][1], iz = kC[i][2];
+            const int gx = eu[u].z & 0xffff, gy = eu[u].z >> 16, gz = eu[u].w;
+            // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
+            const R r0 = mimg_r<R>((R)gx - X0, Lx) + R(0.5) * (R)ix;
+            const R r1 = mimg_r<R>((R)gy - X1, Ly) + R(0.5) * (R)iy;
+            const R r2 = mimg_r<R>((R)gz - X2, Lz) + R(0.5) * (R)iz;
+            const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
+            const R cu6 = -R(6) * (i <= 6 ? wgt<R>(1) : wgt<R>(7)) * (us0 * (R)ix + us1 * (R)iy + us2 * (R)iz);
+            R mag = R(0);
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const R fs = c == 0 ? fsu0[u] : fsu1[u];
+                const R wall = cu6 * (c == 0 ? rru[u] : rbu[u]);
+                if (wall != R(0)) {
+                    const R b = fs - wall;
+                    const R q = pop.st(c == 0 ? pu0[u] : pu1[u], c, i, b);
+                    R dr = q - fs;
+                    if constexpr (P::dev) {
+                        const R res = b - q;
+                        atomicAdd(&pop.f0[(size_t)c * N + m], res);
+                        dr += res;
+                    }
+                    atomicAdd(&rnext[(size_t)c * N + m], dr);
+                    if (c == 0) dm0 += dr;
+                    else dm1 += dr;
+                }
+                mag += R(2) * fs - wall;
+            }
+            const R F0 = -mag * (R)ix, F1 = -mag * (R)iy, F2 = -mag * (R)iz;
+            acc[0] += F0;
+            acc[1] += F1;
+            acc[2] += F2;
+            acc[3] += r1 * F2 - r2 * F1;
+            acc[4] += r2 * F0 - r0 * F2;
+            acc[5] += r0 * F1 - r1 * F0;
+        }
     }
     // (2) the Shan-Chen force of the virtual fluid at each shell node
     for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) {
