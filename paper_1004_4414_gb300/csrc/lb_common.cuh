@@ -209,18 +209,32 @@ struct Pop {
     float* f0;
     size_t N;
     R ref[2];
+    // deviation storage: f = zeta_i (rho_ref + d) = zeta_i d + zeta_i rho_ref,
+    // one FMA per load with zr[c][w] = zeta rho_ref (w = 0 axis, 1 diagonal);
+    // stores invert it with one FMA, d = f / zeta - rho_ref
+    float zr[2][2];
     __device__ __forceinline__ Pop(const BoxDev& b) {
         base = reinterpret_cast<S*>(b.f);
         f0 = b.f0;
         N = (size_t)b.N;
         ref[0] = (R)b.rho_ref[0];
         ref[1] = (R)b.rho_ref[1];
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            zr[c][0] = wgt<float>(1) * (float)ref[c];
+            zr[c][1] = wgt<float>(7) * (float)ref[c];
+        }
+    }
+    __device__ __forceinline__ float dev_to_f(int c, int i, S d) const {
+        return fmaf(wgt<float>(i), to_f(d), zr[c][is_axis(i) ? 0 : 1]);
+    }
+    __device__ __forceinline__ S f_to_dev(int c, int i, float v) const {
+        return from_f<S>(fmaf(v, 1.0f / wgt<float>(i), -(float)ref[c]));
     }
     __device__ __forceinline__ R load(int c, int i, int n) const {
         if constexpr (P::dev) {
             if (i == 0) return f0[(size_t)c * N + n];
-            float d = to_f(base[((size_t)c * 18 + (i - 1)) * N + n]);
-            return wgt<float>(i) * (ref[c] + d);
+            return dev_to_f(c, i, base[((size_t)c * 18 + (i - 1)) * N + n]);
         } else {
             return base[((size_t)c * 19 + i) * N + n];
         }
@@ -232,9 +246,9 @@ struct Pop {
                 f0[(size_t)c * N + n] = v;
                 return v;
             }
-            S q = from_f<S>(v * (1.0f / wgt<float>(i)) - ref[c]);
+            const S q = f_to_dev(c, i, v);
             base[((size_t)c * 18 + (i - 1)) * N + n] = q;
-            return wgt<float>(i) * (ref[c] + to_f(q));
+            return dev_to_f(c, i, q);
         } else {
             base[((size_t)c * 19 + i) * N + n] = v;
             return v;
@@ -248,14 +262,14 @@ struct Pop {
     // load / store through a pointer into the array of direction i (or of
     // opp(i): opposite directions share weight and reference density)
     __device__ __forceinline__ R ld(const S* p, int c, int i) const {
-        if constexpr (P::dev) return wgt<float>(i) * (ref[c] + to_f(*p));
+        if constexpr (P::dev) return dev_to_f(c, i, *p);
         else return *p;
     }
     __device__ __forceinline__ R st(S* p, int c, int i, R v) const {
         if constexpr (P::dev) {
-            const S q = from_f<S>(v * (1.0f / wgt<float>(i)) - ref[c]);
+            const S q = f_to_dev(c, i, v);
             *p = q;
-            return wgt<float>(i) * (ref[c] + to_f(q));
+            return dev_to_f(c, i, q);
         } else {
             *p = v;
             return v;
@@ -274,8 +288,7 @@ struct Pop {
     __device__ __forceinline__ R quant(int c, int i, R v) const {
         if constexpr (P::dev) {
             if (i == 0) return v;
-            S q = from_f<S>(v * (1.0f / wgt<float>(i)) - ref[c]);
-            return wgt<float>(i) * (ref[c] + to_f(q));
+            return dev_to_f(c, i, f_to_dev(c, i, v));
         } else {
             return v;
         }
