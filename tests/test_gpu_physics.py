@@ -1,0 +1,72 @@
+"""Physics of the CUDA path against values the paper prints (Sec. 5,
+contact angle measurements).
+
+Setup as in the paper: a 48 x 48 x 256 box, one half (along z) of each
+fluid component, one particle of radius 10 placed at the interface,
+g_br = 0.08, tau = 1.  The contact angle follows from cos(theta) = dh / R
+(Eq. eqn_contactangle_calculation), dh the signed distance from the
+far-field interface (linearly interpolated zero of phi, averaged over the
+columns away from the particle) to the particle centre, positive towards
+the blue (b) side.  The paper starts from pure components; the model needs
+rho^c > 0 for each component's velocity, so the minority component starts
+at 0.02 (the total stays rho_init), close to what demixing leaves there.
+
+Printed values: theta = (107.03 +- 0.26) deg for colour 0.02 at
+rho_init = 0.6 (Fig. 3, averaged over steps 6e5 - 9e5), and the linear fit
+theta = 442 Delta rho + 90 at rho_init = 0.7 (Fig. 4b).  These runs are 20k
+steps (averaging the last 10k), so the tolerances are a few degrees and 10 %
+of the slope."""
+import numpy as np
+import pytest
+
+import lbinputs
+from oracle import analysis
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, NZ, R = 48, 48, 256, 10.0
+
+
+def contact_angle_run(color, rho_tot, steps=20000, every=2000):
+    from paper_1004_4414_gb300 import Simulation, build
+
+    build.build()
+    sim = Simulation(dict(nx=NX, ny=NY, nz=NZ, n_particles=1, radius=R, g_br=0.08, color=color,
+                          rho_init=(rho_tot, rho_tot), particle_density=1.0, noise_amp=0.0, precision="fp32"))
+    # red below z = NZ / 2, blue above
+    rho = lbinputs.lamellae((NX, NY, NZ), axis=2, rho_major=rho_tot - 0.02, rho_minor=0.02, width=NZ // 2)
+    P = np.zeros((1, 9))
+    P[0, :3] = (NX / 2, NY / 2, NZ / 2 - 0.5)
+    sim.init_fields(0, rho, particles=P)
+    yy, xx = np.mgrid[0:NY, 0:NX]
+    thetas = []
+    for t in range(every, steps + 1, every):
+        sim.step(every)
+        assert sim.observables()["error"] == 0
+        Xp = sim.export_state(0, f=False)["particles"][0]
+        phi = sim.phi(0)
+        dx = (xx - Xp[0] + NX / 2) % NX - NX / 2
+        dy = (yy - Xp[1] + NY / 2) % NY - NY / 2
+        far = dx * dx + dy * dy > (R + 8) ** 2
+        z0 = NZ // 2 - 40
+        heights = [z0 + analysis.interface_height(phi[z0:z0 + 80, j, i]) for j, i in zip(*np.nonzero(far))]
+        dh = Xp[2] - np.mean(heights)
+        thetas.append(analysis.contact_angle(dh, R))
+    sim.close()
+    return np.mean(thetas[len(thetas) // 2:])
+
+
+def test_contact_angle_of_the_papers_measurement():
+    """Colour 0.02, rho_init = 0.6: (107.03 +- 0.26) deg in the paper."""
+    theta = contact_angle_run(0.02, 0.6)
+    assert abs(theta - 107.03) < 3.0, theta
+
+
+def test_contact_angle_slope_against_colour():
+    """rho_init = 0.7: theta = 442 Delta rho + 90 (the paper's fit), and a
+    red/blue swap of the colour mirrors the angle about 90 deg."""
+    tp = contact_angle_run(0.05, 0.7)
+    tm = contact_angle_run(-0.05, 0.7)
+    assert abs((tp + tm) - 180.0) < 0.5, (tp, tm)
+    slope = (tp - tm) / 0.1
+    assert abs(slope - 442.0) < 0.1 * 442.0, slope
