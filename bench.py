@@ -422,7 +422,7 @@ def main():
         "config": {"workload": names[args.workload], "precision": args.precision, "nodes": r["nodes"],
                    "fluid_nodes": r["n_fluid"], "particles": r["n_particles"],
                    "l2": "state larger than L2 (no flush needed)",
-                   "tiling": {"ty": r["tiling"][0], "cz": r["tiling"][1]}},
+                   "tiling": {"ty": r["tiling"][0], "cz": r["tiling"][1], "split": r["tiling"][2]}},
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
                      "frac": r["achieved"] / r["peak"], "traffic": traffic,
                      "peak_kind": r["peak_kind"], "kernel": "k_step (fused stream-collide)",

@@ -173,10 +173,13 @@ int lb_particle_forces(lb_handle* h, int32_t box, double* F, double* T);
 /* Number of particles and lattice nodes of a box. */
 int lb_box_info(lb_handle* h, int32_t box, int32_t* n_particles, int64_t* n_nodes);
 
-/* Block shape of the fused step kernel: ty rows of 32 nodes per CTA (4, 8
- * or 16) and cz planes marched per CTA (>= 1).  Rebuilds the launch plan
- * and graphs.  Used by the autotuner. */
-int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz);
+/* Block shape of the fused step kernel, used by the autotuner.  split = 0:
+ * one thread per node, ty rows of 32 nodes per CTA (4, 8 or 16).  split = 1:
+ * one thread per node and component (the two components on the two halves
+ * of a warp), ty rows of 16 nodes per CTA (8 or 16).  cz planes are marched
+ * per CTA (>= 1).  Both give the same results to rounding order.  Rebuilds
+ * the launch plan and graphs; other values return LB_EINVAL. */
+int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz, int32_t split);
 
 /* Kernel timing.  When enabled, lb_step launches the kernels one by one and
  * brackets every launch of the fused stream-collide kernel with CUDA events

@@ -1,14 +1,17 @@
 """Autotuner of the fused step kernel's block shape.
 
-Candidates are (ty, cz): ty rows of 32 nodes per CTA (4, 8 or 16) and cz
-z-planes marched per CTA.  Each candidate is timed with CUDA events around
+Candidates are (ty, cz, split): split 0 runs one thread per node with ty
+rows of 32 nodes per CTA (4, 8 or 16); split 1 runs one thread per node and
+component with ty rows of 16 nodes (8 or 16); cz z-planes are marched per
+CTA.  Each candidate is timed with CUDA events around
 the fused kernel over a few steps of the real boxes (the simulation
 advances while tuning, so run it as part of the warm-up), and the fastest
 is kept.  Results are cached per (box sizes, precision) in memory.
 """
 _CACHE = {}
 
-DEFAULT_CANDIDATES = ((4, 16), (4, 32), (4, 64), (8, 16), (8, 32), (8, 64), (16, 16), (16, 32))
+DEFAULT_CANDIDATES = ((4, 16, 0), (4, 32, 0), (4, 64, 0), (8, 16, 0), (8, 32, 0), (8, 64, 0), (16, 16, 0), (16, 32, 0),
+                      (8, 16, 1), (8, 32, 1), (16, 16, 1), (16, 32, 1))
 
 
 def _key(sim):
@@ -16,7 +19,7 @@ def _key(sim):
 
 
 def autotune(sim, candidates=DEFAULT_CANDIDATES, steps=4, use_cache=True):
-    """Pick the fastest (ty, cz) for this simulation's boxes; returns
+    """Pick the fastest (ty, cz, split) for this simulation's boxes; returns
     (best, {candidate: ms per fused launch})."""
     key = _key(sim)
     if use_cache and key in _CACHE:
@@ -25,17 +28,18 @@ def autotune(sim, candidates=DEFAULT_CANDIDATES, steps=4, use_cache=True):
         return best, table
     maxnz = max(d[2] for d in sim.dims)
     table = {}
-    for ty, cz in candidates:
+    for cand in candidates:
+        ty, cz, split = tuple(cand) + (0,) * (3 - len(cand))
         if cz > maxnz and cz != candidates[0][1]:
             continue
-        sim.set_tiling(ty, cz)
+        sim.set_tiling(ty, cz, split)
         sim.step(2)  # settle
         sim.sync()
         sim.set_profiling(True)
         sim.step(steps)
         ms, n, _ = sim.kernel_time()
         sim.set_profiling(False)
-        table[(ty, cz)] = ms / max(n, 1)
+        table[(ty, cz, split)] = ms / max(n, 1)
     best = min(table, key=table.get)
     sim.set_tiling(*best)
     _CACHE[key] = (best, table)

@@ -112,7 +112,7 @@ def load_library(path=LIB_PATH):
     L.lb_set_particle_colors.argtypes = [vp, C.c_int32, dp]
     L.lb_particle_forces.argtypes = [vp, C.c_int32, dp, dp]
     L.lb_box_info.argtypes = [vp, C.c_int32, ip, C.POINTER(C.c_int64)]
-    L.lb_set_tiling.argtypes = [vp, C.c_int32, C.c_int32]
+    L.lb_set_tiling.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
     L.lb_set_profiling.argtypes = [vp, C.c_int32]
     L.lb_kernel_time.argtypes = [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.lb_destroy.argtypes = [vp]
@@ -321,8 +321,8 @@ class Simulation:
         return F[: self.n_particles[box]], T[: self.n_particles[box]]
 
     # -- tuning and timing ------------------------------------------------------------
-    def set_tiling(self, ty, cz):
-        _ck(load_library().lb_set_tiling(self._h, int(ty), int(cz)), "lb_set_tiling")
+    def set_tiling(self, ty, cz, split=0):
+        _ck(load_library().lb_set_tiling(self._h, int(ty), int(cz), int(split)), "lb_set_tiling")
 
     def set_profiling(self, on):
         _ck(load_library().lb_set_profiling(self._h, 1 if on else 0), "lb_set_profiling")

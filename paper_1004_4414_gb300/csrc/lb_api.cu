@@ -115,7 +115,11 @@ struct lb_handle {
     BoxDev* d_boxes = nullptr;
     TileDev* d_tiles = nullptr;
     int max_tiles = 0, ntiles = 0, ty = 8, cz = 32;
+    int split = 0;  // fused kernel with one component per thread (16-wide tiles)
     int tau1 = 0;  // every box has tau^r = tau^b = 1: the specialised fused kernel
+    // the fused kernel reflects at solid neighbours itself (some box has
+    // static walls, which have no link list); otherwise k_couple does it
+    int reflect = 1;
     Shared sh{};
     int NP = 0, total_cells = 0;
     std::vector<int> pstart, npb, cell_off;
@@ -192,7 +196,9 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
         B.cell_off = cells;
         cells += cg.nc[0] * cg.nc[1] * cg.nc[2];
         maxN = N > maxN ? N : maxN;
-        maxTiles += ((p.nx + 31) / 32) * ((p.ny + 3) / 4) * p.nz;
+        // the most tiles any block shape makes: 32 x 4 or (split) 16 x 8 nodes, one plane each
+        const int t32 = ((p.nx + 31) / 32) * ((p.ny + 3) / 4), t16 = ((p.nx + 15) / 16) * ((p.ny + 7) / 8);
+        maxTiles += (t32 > t16 ? t32 : t16) * p.nz;
         evcap += ev_cap_for(p, np);
     }
     Shared sh{};
@@ -282,17 +288,18 @@ int upload_boxes(lb_handle* h) {
 
 int build_tiles(lb_handle* h) {
     std::vector<TileDev> tl;
+    const int tw = h->split ? 16 : 32;  // tile width in x
     for (int b = 0; b < h->nb; b++) {
         const BoxDev& B = h->hbox[b];
         for (int z0 = 0; z0 < B.nz; z0 += h->cz)
             for (int y0 = 0; y0 < B.ny; y0 += h->ty)
-                for (int x0 = 0; x0 < B.nx; x0 += 32) {
+                for (int x0 = 0; x0 < B.nx; x0 += tw) {
                     TileDev t;
                     t.box = b;
                     t.x0 = x0;
                     t.y0 = y0;
                     t.z0 = z0;
-                    t.w = B.nx - x0 < 32 ? B.nx - x0 : 32;
+                    t.w = B.nx - x0 < tw ? B.nx - x0 : tw;
                     t.h = B.ny - y0 < h->ty ? B.ny - y0 : h->ty;
                     t.d = B.nz - z0 < h->cz ? B.nz - z0 : h->cz;
                     t.pad = 0;
@@ -313,6 +320,9 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     const int mcur = (int)(t & 1), mnext = (int)((t + 1) & 1);
     const int NP = h->NP;
     int launches = 0;
+    h->reflect = 0;
+    for (int b = 0; b < h->nb; b++)
+        if (h->has_walls[b]) h->reflect = 1;
     k_step_begin<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->nb, h->sh, h->total_cells, mnext);
     launches++;
     if (NP > 0) {
@@ -347,7 +357,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         e1 = h->evpool[h->ev_used++];
         CK(cudaEventRecord(e0, st));
     }
-    CK(h->ops->step(par, h->ty, h->tau1, h->ntiles, st, h->d_boxes, h->d_tiles, h->sh, rc, rn, rz, mnext));
+    CK(h->ops->step(par, h->ty, h->split, h->tau1, h->reflect, h->ntiles, st, h->d_boxes, h->d_tiles, h->sh, rc, rn, rz, mnext));
     launches++;
     if (prof) {
         CK(cudaEventRecord(e1, st));
@@ -355,7 +365,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     }
     if (NP > 0) {
         const int pg = (NP + 255) / 256;
-        CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, par, NP));
+        CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, NP));
         k_md_forces<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
         launches += 3;
@@ -911,11 +921,13 @@ int lb_box_info(lb_handle* h, int32_t box, int32_t* n_particles, int64_t* n_node
     return LB_OK;
 }
 
-int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz) {
-    if (!h || (ty != 4 && ty != 8 && ty != 16) || cz < 1) return LB_EINVAL;
+int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz, int32_t split) {
+    if (!h || cz < 1 || (split != 0 && split != 1)) return LB_EINVAL;
+    if (split ? (ty != 8 && ty != 16) : (ty != 4 && ty != 8 && ty != 16)) return LB_EINVAL;
     CK(cudaStreamSynchronize(h->stream));
     h->ty = ty;
     h->cz = cz;
+    h->split = split;
     int rc = build_tiles(h);
     if (rc != LB_OK) return rc;
     // The next step adds into its density buffer at the new tiling's edge

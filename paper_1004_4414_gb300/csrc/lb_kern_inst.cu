@@ -2,6 +2,7 @@
 // population storage type (LB_PREC: 0 FP64, 1 FP32, 2 FP16 deviation,
 // 3 BF16 deviation) and exports their launchers as an LbOps table.
 #include "lb_aux.cuh"
+#include "lb_step_split.cuh"
 #include "lb_ops.h"
 
 #ifndef LB_PREC
@@ -27,58 +28,90 @@ using RR = typename PP::real;
 namespace {
 constexpr int EV_GRID = 304, EV_BLOCK = 256, NODE_GRID = 1216, NODE_BLOCK = 256;
 
-template <int PAR, int TY, bool T1>
+template <int PAR, int TY, bool T1, bool BB>
 cudaError_t step_t(int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles, Shared sh, int rc, int rn,
                    int rz, int mslot) {
     const size_t smem = StepSmem<RR, TY>::bytes;
-    k_step<PP, PAR, TY, T1><<<ntiles, dim3(32, TY), smem, st>>>(boxes, tiles, sh, rc, rn, rz, mslot);
+    k_step<PP, PAR, TY, T1, BB><<<ntiles, dim3(32, TY), smem, st>>>(boxes, tiles, sh, rc, rn, rz, mslot);
     return cudaGetLastError();
 }
 
-template <int PAR, int TY, bool T1>
+template <int PAR, int TY, bool T1, bool BB>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(k_step<PP, PAR, TY, T1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step<PP, PAR, TY, T1, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)StepSmem<RR, TY>::bytes);
 }
 
-template <bool T1>
+template <int PAR, int TY, bool T1, bool BB>
+cudaError_t split_t(int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles, Shared sh, int rc, int rn,
+                    int rz, int mslot) {
+    const size_t smem = SplitSmem<RR, TY>::bytes;
+    k_step_split<PP, PAR, TY, T1, BB><<<ntiles, dim3(32, TY), smem, st>>>(boxes, tiles, sh, rc, rn, rz, mslot);
+    return cudaGetLastError();
+}
+
+template <int PAR, int TY, bool T1, bool BB>
+cudaError_t set_attr_split() {
+    return cudaFuncSetAttribute(k_step_split<PP, PAR, TY, T1, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SplitSmem<RR, TY>::bytes);
+}
+
+template <bool T1, bool BB>
 cudaError_t setup_t() {
     cudaError_t e = cudaSuccess;
-    cudaError_t r[6] = {set_attr<0, 4, T1>(), set_attr<1, 4, T1>(), set_attr<0, 8, T1>(),
-                        set_attr<1, 8, T1>(), set_attr<0, 16, T1>(), set_attr<1, 16, T1>()};
+    cudaError_t r[10] = {set_attr<0, 4, T1, BB>(),       set_attr<1, 4, T1, BB>(),       set_attr<0, 8, T1, BB>(),
+                         set_attr<1, 8, T1, BB>(),       set_attr<0, 16, T1, BB>(),      set_attr<1, 16, T1, BB>(),
+                         set_attr_split<0, 8, T1, BB>(), set_attr_split<1, 8, T1, BB>(), set_attr_split<0, 16, T1, BB>(),
+                         set_attr_split<1, 16, T1, BB>()};
     for (auto x : r)
         if (x != cudaSuccess) e = x;
     return e;
 }
 
 cudaError_t setup() {
-    const cudaError_t a = setup_t<false>(), b = setup_t<true>();
-    return a != cudaSuccess ? a : b;
+    const cudaError_t r[4] = {setup_t<false, false>(), setup_t<false, true>(), setup_t<true, false>(),
+                              setup_t<true, true>()};
+    for (auto x : r)
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
 }
 
-size_t step_smem(int ty) {
+size_t step_smem(int ty, int split) {
+    if (split) return ty == 8 ? SplitSmem<RR, 8>::bytes : SplitSmem<RR, 16>::bytes;
     return ty == 4 ? StepSmem<RR, 4>::bytes : (ty == 8 ? StepSmem<RR, 8>::bytes : StepSmem<RR, 16>::bytes);
 }
 
-template <bool T1>
-cudaError_t step_tau(int par, int ty, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
-                     Shared sh, int rc, int rn, int rz, int mslot) {
+template <bool T1, bool BB>
+cudaError_t step_tau(int par, int ty, int split, int ntiles, cudaStream_t st, const BoxDev* boxes,
+                     const TileDev* tiles, Shared sh, int rc, int rn, int rz, int mslot) {
+    if (split) {
+        switch (ty * 2 + par) {
+            case 16: return split_t<0, 8, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+            case 17: return split_t<1, 8, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+            case 32: return split_t<0, 16, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+            case 33: return split_t<1, 16, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (ty * 2 + par) {
-        case 8: return step_t<0, 4, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 9: return step_t<1, 4, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 16: return step_t<0, 8, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 17: return step_t<1, 8, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 32: return step_t<0, 16, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
-        case 33: return step_t<1, 16, T1>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 8: return step_t<0, 4, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 9: return step_t<1, 4, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 16: return step_t<0, 8, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 17: return step_t<1, 8, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 32: return step_t<0, 16, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+        case 33: return step_t<1, 16, T1, BB>(ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t step(int par, int ty, int tau1, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
-                 Shared sh, int rc, int rn, int rz, int mslot) {
+cudaError_t step(int par, int ty, int split, int tau1, int reflect, int ntiles, cudaStream_t st, const BoxDev* boxes,
+                 const TileDev* tiles, Shared sh, int rc, int rn, int rz, int mslot) {
     if (ntiles <= 0) return cudaSuccess;
-    return tau1 ? step_tau<true>(par, ty, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot)
-                : step_tau<false>(par, ty, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+    if (reflect)
+        return tau1 ? step_tau<true, true>(par, ty, split, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot)
+                    : step_tau<false, true>(par, ty, split, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
+    return tau1 ? step_tau<true, false>(par, ty, split, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot)
+                : step_tau<false, false>(par, ty, split, ntiles, st, boxes, tiles, sh, rc, rn, rz, mslot);
 }
 
 cudaError_t remap_apply(int par, cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int mslot_cur) {
@@ -98,9 +131,10 @@ cudaError_t shell_density(cudaStream_t st, const BoxDev* boxes, Shared sh, int r
     return cudaGetLastError();
 }
 
-cudaError_t couple(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par, int NP) {
+cudaError_t couple(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par, int reflect,
+                   int NP) {
     if (NP <= 0) return cudaSuccess;
-    k_couple<PP><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot, par);
+    k_couple<PP><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot, par, reflect);
     return cudaGetLastError();
 }
 

@@ -10,13 +10,16 @@ struct LbOps {
     int id;
     size_t real_size;
     cudaError_t (*setup)();
-    size_t (*step_smem)(int ty);
-    cudaError_t (*step)(int par, int ty, int tau1, int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles,
-                        Shared sh, int rc, int rn, int rz, int mslot);
+    size_t (*step_smem)(int ty, int split);
+    // fused kernel: split = 0 k_step (32 x ty tiles), 1 k_step_split (16 x ty, ty 8 or 16);
+    // reflect = 1: the fused kernel reflects at solid neighbours itself, 0: k_couple does
+    cudaError_t (*step)(int par, int ty, int split, int tau1, int reflect, int ntiles, cudaStream_t st,
+                        const BoxDev* boxes, const TileDev* tiles, Shared sh, int rc, int rn, int rz, int mslot);
     cudaError_t (*remap_apply)(int par, cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int mslot_cur);
     cudaError_t (*remap_finish)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc);
     cudaError_t (*shell_density)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int NP);
-    cudaError_t (*couple)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par, int NP);
+    cudaError_t (*couple)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par,
+                          int reflect, int NP);
     cudaError_t (*wall_shell)(cudaStream_t st, const BoxDev* boxes, int b, int rc);
     cudaError_t (*init_pop)(cudaStream_t st, const BoxDev* boxes, int b, const double* rho_field,
                             const double* u_field, uint64_t s_red, uint64_t s_blue, double noise, int rc,

@@ -453,9 +453,20 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
             rcur[(size_t)B.N + w] = (R)sh.ev_rho[(size_t)e * 2 + 1];
         }
         B.evmark[w] = 0;
-        shell_update(B, w);
+        // A solid node left without fluid neighbours takes density 0: the
+        // fused step may have counted reflected populations in it while it
+        // was a shell node, and no later pass rewrites it (the particle's
+        // Shan-Chen force reads it through its shell neighbours).
+        auto update = [&](int n) {
+            shell_update(B, n);
+            if (B.flags[n] == FL_SOLID) {
+                rcur[n] = R(0);
+                rcur[(size_t)B.N + n] = R(0);
+            }
+        };
+        update(w);
 #pragma unroll
-        for (int i = 1; i < 19; i++) shell_update(B, nbr_index(B, w, cx(i), cy(i), cz(i)));
+        for (int i = 1; i < 19; i++) update(nbr_index(B, w, cx(i), cy(i), cz(i)));
     }
 }
 
@@ -565,16 +576,20 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
 //     (Eq. eqn_shan_chen_particle): F = sum_c -g Psi^c(s) sum_i W_i
 //     Psi^cbar(s + c_i) c_i, torque (s - X) x F;
 //   * every link from a fluid neighbour x = s + c_i to s, direction
-//     j = opp(i).  The fused step stored the post-collision f*_j of x,
-//     reflected, in slot j of s (even step) or slot i of x (odd step).
-//     Here it gets the moving-wall term, b = f*_j - 6 zeta_j rho^c(x)
+//     j = opp(i).  The post-collision f*_j of x belongs, reflected, in slot
+//     j of s (even step) or slot i of x (odd step).  With reflect = 1 the
+//     fused step stored it there; with reflect = 0 it stored it as if s were
+//     fluid (slot i of x after an even step, slot j of s after an odd one)
+//     and counted it in the density of s, and this kernel moves it.  The
+//     value gets the moving-wall term, b = f*_j - 6 zeta_j rho^c(x)
 //     (u_s . c_j) with u_s =
 //     U + omega x r at the link midpoint r = x + c_j / 2 - X
 //     (Eq. eqn_ladd_bewegtewand), and the particle receives
 //     (2 f*_j - 6 zeta_j rho^c(x) u_s . c_j) c_j with torque r x F
-//     (Eq. eqn_bounce-back-force).  The change of the stored value also
-//     changes rho(t+1) at x and the fluid mass the step produced; in
-//     deviation storage the rest slot of x absorbs the rounding.
+//     (Eq. eqn_bounce-back-force).  rho(t+1) at x gets the change of the
+//     stored value (reflect = 1) or all of it (reflect = 0), and the fluid
+//     mass the step produced gets the change; in deviation storage the rest
+//     slot of x absorbs the rounding.
 // A link belongs to the owner of its solid end, so each slot is written
 // once; the density and rest-slot updates are atomic because several links
 // can share a fluid node.  Static walls (owner -2) reflect without a wall
@@ -583,7 +598,7 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
 constexpr int COUPLE_THREADS = 256;
 template <class P>
 static __global__ void __launch_bounds__(COUPLE_THREADS)
-    k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot, int par) {
+    k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot, int par, int reflect) {
     using R = typename P::real;
     using S = typename P::st;
     const unsigned FULL = 0xffffffffu;
@@ -619,6 +634,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
         int iu[U], mu[U];
         S* pu0[U];
         S* pu1[U];
+        ptrdiff_t mv[U];  // elements from the slot read to the slot written
         R fsu0[U], fsu1[U], rru[U], rbu[U];
         int4 eu[U];
         bool ok[U];
@@ -637,6 +653,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
             const int i = iu[u];
             ok[u] = ok[u] && ((eu[u].y >> i) & 1);  // s + c_i fluid: a link
             mu[u] = 0;
+            mv[u] = 0;
             pu0[u] = pu1[u] = nullptr;
             fsu0[u] = fsu1[u] = rru[u] = rbu[u] = R(0);
             if (ok[u]) {
@@ -644,10 +661,13 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
                 const int gx = eu[u].z & 0xffff, gy = eu[u].z >> 16, gz = eu[u].w;
                 const int m = wrap1(gx + kC[i][0], nx) + nx * (wrap1(gy + kC[i][1], ny) + ny * wrap1(gz + kC[i][2], nz));
                 mu[u] = m;
-                // the reflected f*_j: after an even step in slot j = opp(i)
-                // of s, after an odd step in slot opp(j) = i of m
-                pu0[u] = par == 0 ? pop.dir(0, opp(i)) + s : pop.dir(0, i) + m;
-                pu1[u] = par == 0 ? pop.dir(1, opp(i)) + s : pop.dir(1, i) + m;
+                // the reflected f*_j belongs after an even step in slot
+                // j = opp(i) of s, after an odd step in slot opp(j) = i of
+                // m; unreflected it sits in the other of the two
+                const bool at_s = (par == 0) == (reflect != 0);
+                pu0[u] = at_s ? pop.dir(0, opp(i)) + s : pop.dir(0, i) + m;
+                pu1[u] = at_s ? pop.dir(1, opp(i)) + s : pop.dir(1, i) + m;
+                if (!reflect) mv[u] = at_s ? (pop.dir(0, i) + m) - pu0[u] : (pop.dir(0, opp(i)) + s) - pu0[u];
                 fsu0[u] = pop.ld(pu0[u], 0, i);
                 fsu1[u] = pop.ld(pu1[u], 1, i);
                 rru[u] = __ldg(rcur + m);
@@ -671,16 +691,16 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
             for (int c = 0; c < 2; c++) {
                 const R fs = c == 0 ? fsu0[u] : fsu1[u];
                 const R wall = cu6 * (c == 0 ? rru[u] : rbu[u]);
-                if (wall != R(0)) {
+                if (wall != R(0) || !reflect) {
                     const R b = fs - wall;
-                    const R q = pop.st(c == 0 ? pu0[u] : pu1[u], c, i, b);
+                    const R q = pop.st((c == 0 ? pu0[u] : pu1[u]) + mv[u], c, i, b);
                     R dr = q - fs;
                     if constexpr (P::dev) {
                         const R res = b - q;
                         atomicAdd(&pop.f0[(size_t)c * N + m], res);
                         dr += res;
                     }
-                    atomicAdd(&rnext[(size_t)c * N + m], dr);
+                    atomicAdd(&rnext[(size_t)c * N + m], reflect ? dr : dr + fs);
                     if (c == 0) dm0 += dr;
                     else dm1 += dr;
                 }

@@ -15,12 +15,23 @@
 //     reads its own 19 slots and writes f*_j to slot opp(j) of itself.  Odd
 //     steps: it reads f_i from slot opp(i) of x - c_i and writes f*_j to slot
 //     j of x + c_j.  A population whose stream target y = x + c_j is solid
-//     is reflected into the slot the next step reads it from: slot j of y
-//     after an even step (the odd step at x reads its f_opp(j) there), slot
-//     opp(j) of x after an odd step.  So the loads of both parities never
-//     depend on the status of a neighbour; only the stores select.  Each
-//     slot is read once and written once per step; neighbour offsets are
-//     wrap-aware and computed once per thread.
+//     belongs, reflected, in the slot the next step reads it from: slot j
+//     of y after an even step (the odd step at x reads its f_opp(j) there),
+//     slot opp(j) of x after an odd step.  So the loads of both parities
+//     never depend on the status of a neighbour.  Each slot is read once and
+//     written once per step; neighbour offsets are wrap-aware and computed
+//     once per thread.
+//   * Reflection (template flag BB).  BB = true: the kernel reads the solid
+//     status of the 18 neighbours and selects each store's slot itself.
+//     BB = false: it stores every population as if its target were fluid
+//     (even steps slot opp(j) of x, odd steps slot j of y) and scatters it
+//     to y's density; k_couple then moves each of these values to its
+//     reflected slot, adds the moving-wall term and counts the value in x's
+//     density.  This needs a link list that covers every fluid-solid link,
+//     which the particles' shell lists do; boxes with static walls use
+//     BB = true.  The moved-from slots are never read: the slot of x (even
+//     steps) is read next by y, which is solid, and the slot of y (odd
+//     steps) is refilled before y can become fluid again.
 //   * A CTA owns a column tile of 32 x TY nodes (one warp per x row: all
 //     population traffic is coalesced along x) and marches through a chunk
 //     of z planes.  Psi and the node flags of the tile plus a one-node ring
@@ -108,7 +119,7 @@ struct StepSmem {
 
 // T1: every box has tau^r = tau^b = 1, where BGK gives f* = f^eq: the
 // loaded populations then only feed the moments and need not stay live.
-template <class P, int PAR, int TY, bool T1>
+template <class P, int PAR, int TY, bool T1, bool BB>
 static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     k_step(const BoxDev* __restrict__ boxes, const TileDev* __restrict__ tiles, Shared sh, int rc, int rn, int rz,
            int mslot) {
@@ -244,9 +255,11 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
         R rho[2] = {R(1), R(1)}, ux[2] = {R(0), R(0)}, uy[2] = {R(0), R(0)}, uz[2] = {R(0), R(0)};
         if (fluid) {
             // ------------------------------------------------- fluid node
+            if constexpr (BB) {
 #pragma unroll
-            for (int i = 1; i < 19; i++)
-                smask |= (unsigned)(FLG(slot_dz(cz(i)), ly + 1 + cy(i), lx + 1 + cx(i)) & FL_SOLID) << i;
+                for (int i = 1; i < 19; i++)
+                    smask |= (unsigned)(FLG(slot_dz(cz(i)), ly + 1 + cy(i), lx + 1 + cx(i)) & FL_SOLID) << i;
+            }
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 f[c][0] = pop.ld_rest(c, n);
@@ -345,7 +358,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 // for direction opp(j); odd steps slot opp(j) of x.
                 auto send = [&](auto JC, R fs) {
                     constexpr int j = decltype(JC)::value;
-                    const bool solid = (smask >> j) & 1u;
+                    const bool solid = BB && ((smask >> j) & 1u);
                     S* p;
                     if (PAR == 0) p = solid ? pop.dir(c, j) + (n + off(j)) : pop.dir(c, opp(j)) + n;
                     else p = solid ? pop.dir(c, opp(j)) + n : pop.dir(c, j) + (n + off(j));

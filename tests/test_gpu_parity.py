@@ -229,12 +229,69 @@ def test_retiling_mid_run():
     rho = lbinputs.mixture(shape, amp=0.05, seed=44)
     o.init_fields(rho, particles=P)
     s.init_fields(0, rho, particles=P)
-    for ty, cz in ((8, 4), (4, 7), (16, 20), (8, 1), (4, 3)):
-        s.set_tiling(ty, cz)
+    for ty, cz, split in ((8, 4, 0), (16, 6, 1), (4, 7, 0), (8, 20, 1), (16, 20, 0), (8, 1, 0), (4, 3, 0)):
+        s.set_tiling(ty, cz, split)
         s.step(3)
         o.step(3)
     compare(o, s, ftol=1e-11, ptol=1e-11)
     assert s.observables()["error"] == 0
+
+
+# ------------------------------------- one thread per node and component
+@pytest.mark.parametrize("ty,cz", [(8, 1), (16, 5), (8, 64), (16, 3)])
+def test_split_kernel_moving_particles(ty, cz):
+    """The kernel with the two components on the two halves of a warp
+    (16-wide tiles; 37 = 16 + 16 + 5 leaves a ragged tile) against the
+    oracle, with moving spheres and cover / uncover events."""
+    shape = (37, 29, 23)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 3.5, 4, seed=41, min_gap=0.5, vmax=0.04, wmax=0.02)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=4, radius=3.5, g_br=0.12, color=0.03, particle_density=2.0)
+    s.set_tiling(ty, cz, 1)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=42)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    o.step(12)
+    s.step(12)
+    compare(o, s, ftol=1e-11, ptol=1e-11)
+
+
+@pytest.mark.parametrize("shape", [(16, 12, 10), (40, 9, 7), (8, 8, 8), (5, 3, 4)])
+def test_split_kernel_fluid_tau_not_one(shape):
+    """Split kernel with tau^b != 1 (the general BGK path, not the tau = 1
+    specialisation), boxes narrower than a tile and a box of 5 x 3 nodes
+    where every node is a tile-edge node."""
+    nx, ny, nz = shape
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=0, g_br=0.15, tau=(1.0, 0.8))
+    s.set_tiling(8, 3, 1)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=1)
+    o.init_fields(rho)
+    s.init_fields(0, rho)
+    o.step(7)
+    s.step(7)
+    compare(o, s)
+
+
+@pytest.mark.parametrize("vel_mode,c0", [(0, 0.0), (1, 5.0)])
+def test_split_kernel_velocity_modes_and_mass_correction(vel_mode, c0):
+    """Split kernel with both velocity definitions (the partner's moments
+    enter u' only for vel_mode 0), a body force, and the mass correction."""
+    shape = (26, 22, 20)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 3.3, 5, seed=12, min_gap=0.4, vmax=0.06, wmax=0.03)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=5, radius=3.3, g_br=0.12, color=-0.03, tau=(0.9, 1.2),
+                particle_density=3.0, vel_mode=vel_mode, mass_corr_c0=c0, body_force=(1e-5, -2e-5, 0.0))
+    s.set_tiling(16, 4, 1)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=13)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    for k in range(4):
+        o.step(5)
+        s.step(5)
+        compare(o, s, ftol=1e-11, ptol=1e-11)
+    ob, sb = o.observe(), s.observables()
+    assert ob["n_cover"] > 0 and ob["n_uncover"] > 0
+    assert np.allclose(ob["mass"], sb["mass"], rtol=1e-13)
 
 
 def test_batched_boxes_fp64():
@@ -263,16 +320,18 @@ def test_batched_boxes_fp64():
 
 
 # ------------------------------------------------------------------- FP32
-def test_fp32_non_chaotic_100_steps():
+@pytest.mark.parametrize("split", [0, 1])
+def test_fp32_non_chaotic_100_steps(split):
     """FP32 populations within 1e-5 relative of FP64 after 100 steps on a
     non-chaotic case (a lamella with a resting particle, below the spinodal
-    coupling)."""
+    coupling), with both fused kernels."""
     shape = (32, 24, 20)
     nx, ny, nz = shape
     P = np.zeros((1, 9))
     P[0, 0:3] = (15.3, 11.7, 9.6)
     o, s = pair("fp32", nx=nx, ny=ny, nz=nz, n_particles=1, radius=4.0, g_br=0.05, color=0.02,
                 fixed_particles=1)
+    s.set_tiling(8, 32, split)
     rho = lbinputs.lamellae(shape, axis=2, rho_major=0.6, rho_minor=0.3)
     o.init_fields(rho, particles=P)
     s.init_fields(0, rho, particles=P)
@@ -296,8 +355,9 @@ def test_fp32_mass_conserved():
     assert np.all(np.abs(ob["mass"] - m0) / m0 < 1e-6)
 
 
+@pytest.mark.parametrize("split", [0, 1])
 @pytest.mark.parametrize("prec,eps", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
-def test_deviation_storage(prec, eps):
+def test_deviation_storage(prec, eps, split):
     """16-bit deviation storage: each stored population carries a relative
     error of at most the unit roundoff u of its deviation d = f/zeta - rho_ref,
     so a population deviates by <= zeta |d| u per step; the FP32 rest
@@ -309,6 +369,7 @@ def test_deviation_storage(prec, eps):
     P[0, 0:3] = (15.3, 11.7, 9.6)
     o, s = pair(prec, nx=nx, ny=ny, nz=nz, n_particles=1, radius=4.0, g_br=0.05, color=0.02,
                 fixed_particles=1, rho_init=(0.45, 0.45))
+    s.set_tiling(8, 32, split)
     rho = lbinputs.lamellae(shape, axis=2, rho_major=0.6, rho_minor=0.3)
     o.init_fields(rho, particles=P)
     s.init_fields(0, rho, particles=P)
