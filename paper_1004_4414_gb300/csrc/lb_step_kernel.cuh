@@ -247,6 +247,11 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                    (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
         };
         auto slot_dz = [&](int dz) { return dz < 0 ? sm_ : (dz > 0 ? sp_ : sc_); };
+        // offset of the node (x, y + dy, z + dz) of scatter group q
+        auto yz = [&](int q) -> int {
+            const int dy = grp_dy(q), dz = grp_dz(q);
+            return (dy < 0 ? oym : (dy > 0 ? oyp : 0)) + (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
+        };
 
         const uint8_t fl = active ? FLG(sc_, ly + 1, lx + 1) : FL_SOLID;
         const bool fluid = active && !(fl & FL_SOLID);
@@ -423,22 +428,17 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             // values leaving the tile through x: the first lane sends left,
             // the last active lane sends right
             if (active && (lx == 0 || lx == w - 1)) {
-                const int gxs = lx == 0 ? (x0 == 0 ? nx - 1 : x0 - 1) : (x0 + w >= nx ? x0 + w - nx : x0 + w);
+                // group q arrives at n + (x offset) + yz(q)
+                R* const rx = rnext + (size_t)c * N + n + (lx == 0 ? oxm : oxp);
 #pragma unroll
                 for (int q = 0; q < 5; q++) {
                     const R v = lx == 0 ? dn[q] : up[q];
-                    const R v2 = (lx == 0 && lx == w - 1) ? up[q] : R(0);  // a one-node-wide tile sends both ways
-                    const int dy = grp_dy(q), dz = grp_dz(q);
-                    int gy = y + dy;
-                    gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-                    int gz = z + dz;
-                    gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
-                    const int base = nx * (gy + ny * gz);
-                    if (v != R(0)) red_add(&rnext[(size_t)c * N + base + gxs], v);
-                    if (v2 != R(0)) {
-                        const int gxr = x0 + w >= nx ? x0 + w - nx : x0 + w;
-                        red_add(&rnext[(size_t)c * N + base + gxr], v2);
-                    }
+                    if (v != R(0)) red_add(rx + yz(q), v);
+                }
+                if (w == 1) {  // a one-node-wide tile also sends right
+#pragma unroll
+                    for (int q = 0; q < 5; q++)
+                        if (up[q] != R(0)) red_add(rnext + (size_t)c * N + n + oxp + yz(q), up[q]);
                 }
             }
             // y shift: rows exchange through shared memory; values leaving
@@ -455,14 +455,9 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
 #pragma unroll
                 for (int q = 1; q < 9; q++) {
                     if (yb_of(q) < 0) continue;
-                    const int dy = grp_dy(q), dz = grp_dz(q);
+                    const int dy = grp_dy(q);
                     if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
-                    if (mid[q] == R(0)) continue;
-                    int gy = y + dy;
-                    gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-                    int gz = z + dz;
-                    gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
-                    red_add(&rnext[(size_t)c * N + x + nx * (gy + ny * gz)], mid[q]);
+                    if (mid[q] != R(0)) red_add(rnext + (size_t)c * N + n + yz(q), mid[q]);
                 }
             }
         }
@@ -485,8 +480,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             const bool own_plane = pz >= z0;
             const bool interior = own_plane && pz <= z0 + d - 2 && pz >= z0 + 1 && lx >= 1 && lx <= w - 2 && ly >= 1 &&
                                   ly <= h - 2;
-            const int gz = pz < 0 ? pz + nz : pz;
-            const int m = nxyc + nxy * gz;
+            const int m = n + ozm;
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 if (interior) rnext[(size_t)c * N + m] = acc[0][c];

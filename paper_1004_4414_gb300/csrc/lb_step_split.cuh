@@ -60,6 +60,7 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
     const Pop<P> pop(B);
     const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
     const R itau0 = (R)B.inv_tau[0], itau1 = (R)B.inv_tau[1];
+    R* const rnext_c = rnext + (size_t)(threadIdx.x >> 4) * N;  // this thread's component
     const R wax = (R)B.scw_axis, wdg = (R)B.scw_diag;
     const R bfx = (R)B.body[0], bfy = (R)B.body[1], bfz = (R)B.body[2];
     const int velmode = B.vel_mode;
@@ -183,6 +184,11 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
                    (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
         };
         auto slot_dz = [&](int dz) { return dz < 0 ? sm_ : (dz > 0 ? sp_ : sc_); };
+        // offset of the node (x, y + dy, z + dz) of scatter group q
+        auto yz = [&](int q) -> int {
+            const int dy = grp_dy(q), dz = grp_dz(q);
+            return (dy < 0 ? oym : (dy > 0 ? oyp : 0)) + (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
+        };
 
         const uint8_t fl = active ? FLG(sc_, ly + 1, lx + 1) : FL_SOLID;
         const bool fluid = active && !(fl & FL_SOLID);
@@ -336,22 +342,16 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             mid[q] += fromL + fromR;
         }
         if (active && (lx == 0 || lx == w - 1)) {
-            const int gxs = lx == 0 ? (x0 == 0 ? nx - 1 : x0 - 1) : (x0 + w >= nx ? x0 + w - nx : x0 + w);
+            R* const rx = rnext_c + n + (lx == 0 ? oxm : oxp);
 #pragma unroll
             for (int q = 0; q < 5; q++) {
                 const R v = lx == 0 ? dn[q] : up[q];
-                const R v2 = (lx == 0 && lx == w - 1) ? up[q] : R(0);
-                const int dy = grp_dy(q), dz = grp_dz(q);
-                int gy = y + dy;
-                gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-                int gz = z + dz;
-                gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
-                const int base = nx * (gy + ny * gz);
-                if (v != R(0)) red_add(&rnext[(size_t)c * N + base + gxs], v);
-                if (v2 != R(0)) {
-                    const int gxr = x0 + w >= nx ? x0 + w - nx : x0 + w;
-                    red_add(&rnext[(size_t)c * N + base + gxr], v2);
-                }
+                if (v != R(0)) red_add(rx + yz(q), v);
+            }
+            if (w == 1) {  // a one-node-wide tile also sends right
+#pragma unroll
+                for (int q = 0; q < 5; q++)
+                    if (up[q] != R(0)) red_add(rnext_c + n + oxp + yz(q), up[q]);
             }
         }
         acc[1] += mid[0];
@@ -366,14 +366,9 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
 #pragma unroll
             for (int q = 1; q < 9; q++) {
                 if (yb_of(q) < 0) continue;
-                const int dy = grp_dy(q), dz = grp_dz(q);
+                const int dy = grp_dy(q);
                 if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
-                if (mid[q] == R(0)) continue;
-                int gy = y + dy;
-                gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-                int gz = z + dz;
-                gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
-                red_add(&rnext[(size_t)c * N + x + nx * (gy + ny * gz)], mid[q]);
+                if (mid[q] != R(0)) red_add(rnext_c + n + yz(q), mid[q]);
             }
         }
         __syncthreads();
@@ -392,10 +387,9 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             const bool own_plane = pz >= z0;
             const bool interior = own_plane && pz <= z0 + d - 2 && pz >= z0 + 1 && lx >= 1 && lx <= w - 2 && ly >= 1 &&
                                   ly <= h - 2;
-            const int gz = pz < 0 ? pz + nz : pz;
-            const int m = nxyc + nxy * gz;
-            if (interior) rnext[(size_t)c * N + m] = acc[0];
-            else if (acc[0] != R(0)) red_add(&rnext[(size_t)c * N + m], acc[0]);
+            const int m = n + ozm;
+            if (interior) rnext_c[m] = acc[0];
+            else if (acc[0] != R(0)) red_add(rnext_c + m, acc[0]);
             if (own_plane && !interior) rzero[(size_t)c * N + m] = R(0);
         }
         acc[0] = acc[1];
