@@ -42,7 +42,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PROFILES = os.path.join(ROOT, "profiles")
-KERNEL_SOURCES = ("lb_step_kernel.cuh", "lb_common.cuh")
+KERNEL_SOURCES = ("lb_step_kernel.cuh", "lb_step_split.cuh", "lb_common.cuh")
 
 
 def workload_params(name, precision="fp32"):
@@ -101,14 +101,18 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, precision):
+def fused_kernel_name(split):
+    return "k_step_split" if split else "k_step"
+
+
+def ncu_traffic(workload, precision, split):
     """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the same kernel and its current source."""
     path = os.path.join(PROFILES, "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        e = d.get("%s_%s" % (workload, precision))
+        e = d.get("%s_%s_%s" % (workload, precision, fused_kernel_name(split)))
         if e and e.get("kernel_hash") == kernel_hash():
             return e["dram_bytes_per_launch"]
     except Exception:
@@ -226,7 +230,11 @@ def run_ours(args, rank, world, device):
     # then W plain steps
     from paper_1004_4414_gb300.autotune import autotune
 
-    tiling, _ = autotune(sim)
+    if args.tiling:
+        tiling = tuple(int(v) for v in args.tiling.split(","))
+        sim.set_tiling(*tiling)
+    else:
+        tiling, _ = autotune(sim)
     # the timed steps start from the seeded state again
     sim.init_from_seed(seed + 1000 * rank)
     sim.step(args.warmup)
@@ -372,6 +380,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sequential", action="store_true", help="batch: skip the one-box-at-a-time comparison")
+    ap.add_argument("--tiling", default=None, metavar="TY,CZ,SPLIT",
+                    help="fixed block shape of the fused kernel instead of the autotuner's (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -413,7 +423,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         c = oracle_sample(args.workload)
         cpu = {"value": c["value"], "unit": "MLUPS", "cores": c["cores"], "kind": "oracle", "sample": c["sample"]}
-    traffic = ncu_traffic(args.workload, args.precision)
+    traffic = ncu_traffic(args.workload, args.precision, r["tiling"][2])
     line = {
         "metric": metric, "value": r["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -425,7 +435,7 @@ def main():
                    "tiling": {"ty": r["tiling"][0], "cz": r["tiling"][1], "split": r["tiling"][2]}},
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
                      "frac": r["achieved"] / r["peak"], "traffic": traffic,
-                     "peak_kind": r["peak_kind"], "kernel": "k_step (fused stream-collide)",
+                     "peak_kind": r["peak_kind"], "kernel": fused_kernel_name(r["tiling"][2]) + " (fused stream-collide)",
                      "bytes_per_launch": r["bytes"], "launch_ms": r["fused_ms"]},
         "cpu_baseline": cpu,
         "e2e": r["e2e"],
