@@ -42,6 +42,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PROFILES = os.path.join(ROOT, "profiles")
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 KERNEL_SOURCES = ("lb_step_kernel.cuh", "lb_step_split.cuh", "lb_common.cuh")
 
 
@@ -436,7 +437,10 @@ def main():
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
                      "frac": r["achieved"] / r["peak"], "traffic": traffic,
                      "peak_kind": r["peak_kind"], "kernel": fused_kernel_name(r["tiling"][2]) + " (fused stream-collide)",
-                     "bytes_per_launch": r["bytes"], "launch_ms": r["fused_ms"]},
+                     "bytes_per_launch": r["bytes"], "launch_ms": r["fused_ms"],
+                     "frac_nominal": r["achieved"] / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+                     "dram_gbs": traffic / (r["fused_ms"] * 1e6) if traffic else None},
+        "fluid_mlups": r["value"] * r["n_fluid"] / r["nodes"],
         "cpu_baseline": cpu,
         "e2e": r["e2e"],
         "clocks": r["clocks"],
