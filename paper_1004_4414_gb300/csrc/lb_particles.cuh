@@ -173,6 +173,7 @@ constexpr int DETECT_WARPS = 4;
 static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     __shared__ float s_rq[DETECT_WARPS][NL_MAX][3];  // X_q - X_p, minimum image
     __shared__ int s_nid[DETECT_WARPS][NL_MAX];
+    __shared__ int s_cl[DETECT_WARPS][NL_MAX];  // entries of neighbours within 2R (+ slack)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * DETECT_WARPS + wib;
     if (p >= NP) return;  // the whole warp leaves together
@@ -183,11 +184,29 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
     const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
     const float Lf[3] = {(float)B.nx, (float)B.ny, (float)B.nz};
     const int nn = sh.nlist_n[p];
-    for (int k = lane; k < nn; k += 32) {
-        const int q = sh.nlist[(size_t)p * NL_MAX + k];
-        s_nid[wib][k] = q;
-        const PartStateF qf = sh.partf[q];
-        for (int a = 0; a < 3; a++) s_rq[wib][k][a] = mimgf(qf.X[a] - pf.X[a], Lf[a]);
+    // A node inside p can also be inside q only if |X_q - X_p| <= 2R: those
+    // neighbours (the close list; 0.05 of slack covers the FP32 centres)
+    // decide the claims of nodes inside p.  A node p owned but left may lie
+    // within 2R + 1.5 of q, so that rare case scans the whole list.
+    const float rcl = 2.0f * (float)R + 0.05f;
+    int ncl = 0;
+    {
+        bool close = false;
+        if (lane < nn) {  // nn <= NL_MAX = 32
+            const int q = sh.nlist[(size_t)p * NL_MAX + lane];
+            s_nid[wib][lane] = q;
+            const PartStateF qf = sh.partf[q];
+            float d2 = 0.f;
+            for (int a = 0; a < 3; a++) {
+                const float v = mimgf(qf.X[a] - pf.X[a], Lf[a]);
+                s_rq[wib][lane][a] = v;
+                d2 += v * v;
+            }
+            close = d2 <= rcl * rcl;
+        }
+        const unsigned cm = __ballot_sync(0xffffffffu, close);
+        if (close) s_cl[wib][__popc(cm & ((1u << lane) - 1u))] = lane;
+        ncl = __popc(cm);
     }
     __syncwarp();
     // window: every node within R + 1.5 of the centre (a node owned before
@@ -236,7 +255,9 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
                     }
                     if (inside || own == p) {
                         bool other = false, anyone = false;
-                        for (int k = 0; k < nn; k++) {
+                        const int nk = inside ? ncl : nn;
+                        for (int kk = 0; kk < nk; kk++) {
+                            const int k = inside ? s_cl[wib][kk] : kk;
                             const float ex = mimgf(fx - s_rq[wib][k][0], Lf[0]);
                             const float ey = mimgf(fy - s_rq[wib][k][1], Lf[1]);
                             const float ez = mimgf(fz - s_rq[wib][k][2], Lf[2]);
@@ -476,6 +497,8 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
 template <class R>
 static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh, int rc, int NP) {
     __shared__ int s_q[4][64];
+    __shared__ int s_qc[4][64];  // x | y << 16 of the queued node
+    __shared__ int s_qz[4][64];  // z of the queued node
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * 4 + wib;
@@ -506,14 +529,19 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     int4* __restrict__ slist = sh.shell_list + (size_t)p * scap;
     // virtual density of one shell node n of p, and its entry k of p's
     // shell list (node, mask of fluid neighbours, coordinates)
-    auto process = [&](int n, int k) {
-        const int gx = n % nx, gy = (n / nx) % ny, gz = n / (nx * ny);
+    const int nxy = nx * ny;
+    auto process = [&](int n, int gx, int gy, int gz, int k) {
+        // wrap-aware offsets to the neighbours along each axis
+        const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
+        const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
+        const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
         R s0 = R(0), s1 = R(0);
         int cnt = 0;
         unsigned fmask = 0;  // bit i: n + c_i is fluid (a link)
 #pragma unroll
         for (int i = 1; i < 19; i++) {
-            const int m = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
+            const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) + (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) +
+                          (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
             if (!(flags[m] & FL_SOLID)) {
                 s0 += rcur[m];
                 s1 += rcur[N + m];
@@ -521,7 +549,7 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
                 fmask |= 1u << i;
             }
         }
-        if (k < scap) slist[k] = make_int4(n, (int)fmask, gx | (gy << 16), gz);
+        if (k < scap) slist[k] = make_int4(n, (int)fmask, (int)((unsigned)gx | ((unsigned)gy << 16)), gz);
         R r0 = s0 / (R)cnt, r1 = s1 / (R)cnt;
         if (col > R(0)) r0 += col;
         else if (col < R(0)) r1 -= col;
@@ -537,27 +565,37 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     for (int base = 0;; base += 32) {
         const int idx = base + lane;
         bool take = false;
-        int n = 0;
+        int n = 0, gx = 0, gy = 0, gz = 0;
         if (idx < total) {
             const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
             const float dx = mimgf((float)kx - off[0], (float)nx), dy = mimgf((float)ky - off[1], (float)ny),
                         dz = mimgf((float)kz - off[2], (float)nz);
             if (dx * dx + dy * dy + dz * dz <= lim) {
-                n = wrapi(lo[0] + kx, nx) + nx * (wrapi(lo[1] + ky, ny) + ny * wrapi(lo[2] + kz, nz));
+                gx = wrapi(lo[0] + kx, nx);
+                gy = wrapi(lo[1] + ky, ny);
+                gz = wrapi(lo[2] + kz, nz);
+                n = gx + nx * (gy + ny * gz);
                 take = (__ldg(flags + n) & FL_SHELL) && __ldg(owner + n) == p;
             }
         }
         const unsigned m = __ballot_sync(FULL, take);
-        if (take) s_q[wib][nq + __popc(m & ((1u << lane) - 1u))] = n;
+        if (take) {
+            const int pos = nq + __popc(m & ((1u << lane) - 1u));
+            s_q[wib][pos] = n;
+            s_qc[wib][pos] = (int)((unsigned)gx | ((unsigned)gy << 16));
+            s_qz[wib][pos] = gz;
+        }
         nq += __popc(m);
         __syncwarp();
         const bool last = base + 32 >= total;  // the final round drains the queue
         if (nq >= 32 || (last && nq > 0)) {
             const int k = nq < 32 ? nq : 32;
             const int item = lane < k ? s_q[wib][nq - k + lane] : -1;
+            const int ic = lane < k ? s_qc[wib][nq - k + lane] : 0;
+            const int iz = lane < k ? s_qz[wib][nq - k + lane] : 0;
             __syncwarp();
             nq -= k;
-            if (item >= 0) process(item, done + lane);
+            if (item >= 0) process(item, ic & 0xffff, (int)((unsigned)ic >> 16), iz, done + lane);
             done += k;
         }
         if (last && nq == 0) break;
@@ -658,7 +696,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
             fsu0[u] = fsu1[u] = rru[u] = rbu[u] = R(0);
             if (ok[u]) {
                 const int s = eu[u].x;
-                const int gx = eu[u].z & 0xffff, gy = eu[u].z >> 16, gz = eu[u].w;
+                const int gx = eu[u].z & 0xffff, gy = (int)((unsigned)eu[u].z >> 16), gz = eu[u].w;
                 const int m = wrap1(gx + kC[i][0], nx) + nx * (wrap1(gy + kC[i][1], ny) + ny * wrap1(gz + kC[i][2], nz));
                 mu[u] = m;
                 // the reflected f*_j belongs after an even step in slot
@@ -679,7 +717,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
             if (!ok[u]) continue;
             const int i = iu[u], m = mu[u];
             const int ix = kC[i][0], iy = kC[i][1], iz = kC[i][2];
-            const int gx = eu[u].z & 0xffff, gy = eu[u].z >> 16, gz = eu[u].w;
+            const int gx = eu[u].z & 0xffff, gy = (int)((unsigned)eu[u].z >> 16), gz = eu[u].w;
             // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
             const R r0 = mimg_r<R>((R)gx - X0, Lx) + R(0.5) * (R)ix;
             const R r1 = mimg_r<R>((R)gy - X1, Ly) + R(0.5) * (R)iy;
@@ -719,7 +757,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) {
         const int4 e = list[k];
         const int s = e.x;
-        const int gx = e.z & 0xffff, gy = e.z >> 16, gz = e.w;
+        const int gx = e.z & 0xffff, gy = (int)((unsigned)e.z >> 16), gz = e.w;
         R sr0 = R(0), sr1 = R(0), sr2 = R(0), sb0 = R(0), sb1 = R(0), sb2 = R(0);
 #pragma unroll
         for (int i = 1; i < 19; i++) {

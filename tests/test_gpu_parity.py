@@ -294,6 +294,28 @@ def test_split_kernel_velocity_modes_and_mass_correction(vel_mode, c0):
     assert np.allclose(ob["mass"], sb["mass"], rtol=1e-13)
 
 
+def test_long_y_axis_beyond_16_bit_signed():
+    """Node coordinates are packed as x | y << 16 in the shell lists; a box
+    with y up to 32809 puts a moving, rotating sphere across y = 32767 so that
+    its shell nodes carry y >= 2^15 (read back unsigned)."""
+    shape = (12, 32810, 12)
+    nx, ny, nz = shape
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (5.6, 32767.3, 6.2)
+    P[0, 3:6] = (0.01, 0.03, -0.02)
+    P[0, 6:9] = (0.0, 0.02, 0.01)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=1, radius=3.2, g_br=0.1, color=0.03, particle_density=2.0)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=51)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    o.step(4)
+    s.step(4)
+    compare(o, s, ftol=1e-11, ptol=1e-11)
+    Fo, To = o.particle_forces()
+    Fs, Ts = s.particle_forces()
+    assert np.max(np.abs(Fo - Fs)) < 1e-9 and np.max(np.abs(To - Ts)) < 1e-9
+
+
 def test_batched_boxes_fp64():
     """Uneven boxes stepped together in one launch per phase."""
     from paper_1004_4414_gb300 import Simulation
