@@ -259,6 +259,85 @@ def test_moving_wall_term_galilean():
     assert e3 < 1e-9 and m3 < 2e-9
 
 
+def _droplet_pressure_jump(radius, g=0.15, L=48, steps=2500):
+    """Cylindrical red droplet in blue (nz = 1), started from the flat
+    interface's coexisting bulk densities at this g (0.840 / 0.005, found by
+    relaxing a flat lamella); returns (p_in - p_out, equimolar radius)."""
+    yy, xx = np.mgrid[0:L, 0:L]
+    r = np.sqrt((xx - L / 2 + 0.5) ** 2 + (yy - L / 2 + 0.5) ** 2)
+    inside = 0.5 * (1.0 - np.tanh((r - radius) / 1.5))
+    rho = np.zeros((2, L * L))
+    rho[0] = (0.00485 + 0.83474 * inside).reshape(-1)
+    rho[1] = (0.00485 + 0.83474 * (1.0 - inside)).reshape(-1)
+    o = ref.Oracle(nx=L, ny=L, nz=1, n_particles=0, g_br=g, noise_amp=0.0)
+    o.init_fields(rho)
+    o.step(steps)
+    rr = o.rho()
+    psi = 1.0 - np.exp(-rr)  # Eq. eqn_ref_dens with rho0 = 1
+    # bulk pressure of the two-component Shan-Chen fluid: the force of Eq.
+    # eqn_shan-chen-F is -g A grad(Psi^r Psi^b) to leading order, A =
+    # sum_i W_i c_ix^2 = 2 * 2 + 8 * 1 = 12 for the (2, 1) weights
+    p = (CS2 * (rr[0] + rr[1]) + g * 12.0 * psi[0] * psi[1]).reshape(L, L)
+    c = L // 2
+    p_in = p[c - 2:c + 2, c - 2:c + 2].mean()
+    p_out = p[0:3, 0:3].mean()
+    red = rr[0].reshape(L, L)
+    area = np.sum((red - red[0, 0]) / (red[c, c] - red[0, 0]))
+    return p_in - p_out, np.sqrt(area / np.pi)
+
+
+def test_laplace_law_static_droplet():
+    """Laplace law for a static droplet (the theory behind the interfaces of
+    Secs. II and V): in two dimensions the pressure jump across a circular
+    interface is sigma / R with one surface tension sigma for every radius.
+    A wrong sign or a dropped factor in the force either dissolves the
+    droplet or breaks the 1/R scaling."""
+    res = [_droplet_pressure_jump(R0) for R0 in (7.0, 10.0, 14.0)]
+    dp = np.array([d for d, _ in res])
+    R = np.array([r for _, r in res])
+    assert np.all(dp > 0), dp
+    sigma = dp * R
+    assert np.max(np.abs(sigma / sigma.mean() - 1.0)) < 0.04, sigma
+    slope, icpt = np.polyfit(1.0 / R, dp, 1)
+    assert abs(icpt) < 0.1 * dp.min(), (slope, icpt)
+
+
+def test_stokes_drag_periodic_array():
+    """Drag on a fixed sphere in a periodic box of side L with the fluid
+    driven by a body force (bounce-back and momentum exchange of Eqs.
+    eqn_bounce-back and eqn_bounce-back-force): Stokes' 6 pi eta a U times
+    Hasimoto's periodic-array factor K(phi) (J. Fluid Mech. 5, 317 (1959);
+    the series of Sangani & Acrivos, Int. J. Multiphase Flow 8, 343 (1982)),
+    U the mean velocity over the cell and eta = rho c_s^2 (tau - 1/2).  The
+    flow starts at about its steady mean velocity so that it settles within
+    a few hundred steps.  Bounce-back places the wall within a fraction of a
+    node of the input radius; 5 % covers that at R = 4."""
+    L, R, gb = 32, 4.0, 1e-6
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (L / 2 - 0.3, L / 2 + 0.2, L / 2 - 0.1)
+    o = ref.Oracle(nx=L, ny=L, nz=L, n_particles=1, radius=R, g_br=0.0, noise_amp=0.0, fixed_particles=1,
+                   body_force=(gb, 0.0, 0.0), rho_init=(0.5, 0.5))
+    u0 = np.zeros((3, L ** 3))
+    u0[0] = 1.7e-3
+    o.init_fields(np.full((2, L ** 3), 0.5), u=u0, particles=P)
+    o.step(750)
+    F, _ = o.particle_forces()
+    st = o.get_state()
+    fluid = st["owner"] == -1
+    c, _, _ = ref.lattice()
+    rho = st["f"].sum(axis=(0, 1))
+    jx = np.einsum("cin,i->n", st["f"], c[:, 0].astype(np.float64))
+    # physical momentum includes half the body force (Sec. II velocity shift)
+    U = np.sum(jx[fluid] + 0.5 * rho[fluid] * gb) / 1.0 / L ** 3
+    eta = 1.0 * CS2 * (1.0 - 0.5)
+    phi = 4.0 / 3.0 * np.pi * R ** 3 / L ** 3
+    K = 1.0 / (1 - 1.7601 * phi ** (1 / 3) + phi - 1.5593 * phi ** 2 + 3.9799 * phi ** (8 / 3)
+               - 3.0734 * phi ** (10 / 3))
+    ratio = F[0, 0] / (6 * np.pi * eta * R * U * K)
+    assert abs(ratio - 1.0) < 0.05, ratio
+    assert np.all(np.abs(F[0, 1:]) < 1e-3 * F[0, 0]), F
+
+
 def test_static_sphere_in_fluid_at_rest():
     """No flow appears around a resting sphere in a resting fluid, and the
     bounce-back force on a sphere centred on a node is zero by symmetry."""
