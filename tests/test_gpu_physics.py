@@ -1,5 +1,6 @@
 """Physics of the CUDA path against values the paper prints (Sec. 5,
-contact angle measurements).
+contact angle measurements) and against closed forms (Laplace law of a
+droplet, Stokes drag on a periodic array of spheres).
 
 Setup as in the paper: a 48 x 48 x 256 box, one half (along z) of each
 fluid component, one particle of radius 10 placed at the interface,
@@ -70,3 +71,69 @@ def test_contact_angle_slope_against_colour():
     assert abs((tp + tm) - 180.0) < 0.5, (tp, tm)
     slope = (tp - tm) / 0.1
     assert abs(slope - 442.0) < 0.1 * 442.0, slope
+
+
+def test_laplace_law_fp32():
+    """The CUDA path in FP32 on the oracle's Laplace case (a 2-D droplet in a
+    box one node thick in z): p_in - p_out = sigma / R with one sigma for
+    R = 7, 10 and 14, within 4 %."""
+    from paper_1004_4414_gb300 import Simulation, build
+
+    build.build()
+    L, g = 48, 0.15
+    sig = []
+    for R0 in (7.0, 10.0, 14.0):
+        yy, xx = np.mgrid[0:L, 0:L]
+        r = np.sqrt((xx - L / 2 + 0.5) ** 2 + (yy - L / 2 + 0.5) ** 2)
+        inside = 0.5 * (1.0 - np.tanh((r - R0) / 1.5))
+        rho = np.zeros((2, L * L))
+        rho[0] = (0.00485 + 0.83474 * inside).reshape(-1)
+        rho[1] = (0.00485 + 0.83474 * (1.0 - inside)).reshape(-1)
+        sim = Simulation(dict(nx=L, ny=L, nz=1, n_particles=0, g_br=g, noise_amp=0.0, precision="fp32"))
+        sim.init_fields(0, rho)
+        sim.step(2500)
+        assert sim.observables()["error"] == 0
+        rr = sim.rho(0)
+        sim.close()
+        psi = 1.0 - np.exp(-rr)
+        p = ((rr[0] + rr[1]) / 3.0 + g * 12.0 * psi[0] * psi[1]).reshape(L, L)
+        c = L // 2
+        dp = p[c - 2:c + 2, c - 2:c + 2].mean() - p[0:3, 0:3].mean()
+        red = rr[0].reshape(L, L)
+        Rm = np.sqrt(np.sum((red - red[0, 0]) / (red[c, c] - red[0, 0])) / np.pi)
+        assert dp > 0
+        sig.append(dp * Rm)
+    sig = np.array(sig)
+    assert np.max(np.abs(sig / sig.mean() - 1.0)) < 0.04, sig
+
+
+def test_stokes_drag_periodic_array_fp32():
+    """The CUDA path in FP32 on the oracle's drag case: a fixed sphere (R = 4)
+    in a periodic 32^3 box with the fluid driven by a body force feels
+    6 pi eta a U K(phi) (Hasimoto's periodic-array factor) within 5 %."""
+    from paper_1004_4414_gb300 import Simulation, build
+
+    build.build()
+    L, R, gb = 32, 4.0, 1e-6
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (L / 2 - 0.3, L / 2 + 0.2, L / 2 - 0.1)
+    sim = Simulation(dict(nx=L, ny=L, nz=L, n_particles=1, radius=R, g_br=0.0, noise_amp=0.0, fixed_particles=1,
+                          body_force=(gb, 0.0, 0.0), rho_init=(0.5, 0.5), precision="fp32"))
+    u0 = np.zeros((3, L ** 3))
+    u0[0] = 1.7e-3
+    sim.init_fields(0, np.full((2, L ** 3), 0.5), u=u0, particles=P)
+    sim.step(750)
+    F, _ = sim.particle_forces(0)
+    st = sim.export_state(0)
+    sim.close()
+    fluid = st["owner"] == -1
+    cx = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0], np.float64)
+    rho = st["f"].sum(axis=(0, 1))
+    jx = np.einsum("cin,i->n", st["f"], cx)
+    U = np.sum(jx[fluid] + 0.5 * rho[fluid] * gb) / L ** 3
+    eta = (1.0 / 3.0) * 0.5
+    phi = 4.0 / 3.0 * np.pi * R ** 3 / L ** 3
+    K = 1.0 / (1 - 1.7601 * phi ** (1 / 3) + phi - 1.5593 * phi ** 2 + 3.9799 * phi ** (8 / 3)
+               - 3.0734 * phi ** (10 / 3))
+    ratio = F[0, 0] / (6 * np.pi * eta * R * U * K)
+    assert abs(ratio - 1.0) < 0.05, ratio
