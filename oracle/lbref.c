@@ -101,6 +101,7 @@ struct orc_state {
     double* force;      /* [2][3][N] */
     uint8_t* shell;     /* [N] */
     double *X, *U, *W, *F, *T, *color; /* [np][3] / [np] */
+    double* E;          /* [np][3] body axis of a spheroid (unit vector) */
     double Flast[1], *Fsave, *Tsave;
     double mass0[2];
     int64_t n_cover, n_uncover;
@@ -142,14 +143,109 @@ static inline void cross3(const double* a, const double* b, double* o) {
 }
 #define FIDX(s, c, i, n) (((int64_t)(c) * Q + (i)) * (s)->N + (n))
 
+/* Non-spherical particles (the generality the paper claims for its
+ * coupling, Secs. I and III; reading): spheroids with semi-axes R, R and
+ * c = aspect R about a body axis e.  aspect = 1 is the sphere, which keeps
+ * the plain distance test and the scalar moment of inertia, so sphere runs
+ * are unchanged.  The coupling itself (bounce-back, momentum exchange,
+ * cover/uncover, virtual fluid) only needs the set of solid nodes and
+ * u_s = U + omega x r, whatever the shape. */
+static inline int is_sphere(const orc_params* p) { return p->aspect == 1.0; }
+static inline double bound_radius(const orc_params* p) {
+    return p->aspect > 1.0 ? p->aspect * p->radius : p->radius;
+}
+static inline double particle_volume(const orc_params* p) {
+    return 4.0 / 3.0 * M_PI * p->radius * p->radius * (p->aspect * p->radius);
+}
+
+/* Inside test of a displacement d from the centre: R^2 (d.e)^2 +
+ * c^2 (|d|^2 - (d.e)^2) <= R^2 c^2, each product and sum rounded in this
+ * order (no contraction) so that both implementations decide alike. */
+static int inside_spheroid(const orc_params* p, const double d[3], const double e[3]) {
+    const double R2 = p->radius * p->radius, c = p->aspect * p->radius, c2 = c * c;
+    const double s = ((d[0] * e[0]) + (d[1] * e[1])) + (d[2] * e[2]);
+    const double d2 = ((d[0] * d[0]) + (d[1] * d[1])) + (d[2] * d[2]);
+    const double s2 = s * s;
+    return (R2 * s2) + (c2 * (d2 - s2)) <= R2 * c2;
+}
+int32_t orc_inside(const orc_params* p, const double d[3], const double e[3]) {
+    if (is_sphere(p)) {
+        const double d2 = ((d[0] * d[0]) + (d[1] * d[1])) + (d[2] * d[2]);
+        return d2 <= p->radius * p->radius;
+    }
+    return inside_spheroid(p, d, e);
+}
+
+/* Distance from the centre to the surface along the unit vector n:
+ * (n_par^2 / c^2 + n_perp^2 / R^2)^(-1/2). */
+static double support_radius(const orc_params* p, const double n[3], const double e[3]) {
+    const double R = p->radius, c = p->aspect * p->radius;
+    double t = dot3(n, e);
+    double t2 = t * t;
+    if (t2 > 1.0) t2 = 1.0;
+    return 1.0 / sqrt(t2 / (c * c) + (1.0 - t2) / (R * R));
+}
+/* Contact distance of two particles along the line of centres r_hat
+ * (reading: the paper's Hertz and lubrication laws are for spheres; for
+ * spheroids the surfaces are taken to meet along the line of centres at
+ * sigma = rho_p(r_hat) + rho_q(r_hat), and the laws use the gap r - sigma
+ * with the sphere radius replaced by sigma / 2). */
+double orc_contact_distance(const orc_params* p, const double rh[3], const double ep[3], const double eq[3]) {
+    if (is_sphere(p)) return 2.0 * p->radius;
+    return support_radius(p, rh, ep) + support_radius(p, rh, eq);
+}
+
+/* Rotational update of one particle with torque T (leap-frog, reading):
+ * angular momentum L = I(e) omega, L += T; the symmetry axis of a spheroid
+ * moves as de/dt = omega x e = (L x e) / I_perp (the part of omega along e
+ * does not move it), so it is turned about L by |L| / I_perp (Rodrigues),
+ * which is exact for torque-free motion; then omega = I(e_new)^-1 L.
+ * I(e) = I_perp (1 - e e) + I_par e e with I_par = 2/5 m R^2 and I_perp =
+ * 1/5 m (R^2 + c^2).  Spheres keep omega += T / J and a fixed axis. */
+static void apply_inertia(double Ipar, double Iperp, const double e[3], const double v[3], double o[3], int inv) {
+    const double a = inv ? 1.0 / Iperp : Iperp, b = inv ? 1.0 / Ipar : Ipar;
+    const double t = dot3(e, v);
+    for (int k = 0; k < 3; k++) o[k] = a * v[k] + (b - a) * t * e[k];
+}
+static void rotate_particle(const orc_params* p, double m, double W[3], double e[3], const double T[3]) {
+    const double R = p->radius;
+    if (is_sphere(p)) {
+        const double J = 0.4 * m * R * R;
+        for (int a = 0; a < 3; a++) W[a] += T[a] / J;
+        return;
+    }
+    const double c = p->aspect * R;
+    const double Ipar = 0.4 * m * R * R, Iperp = 0.2 * m * (R * R + c * c);
+    double L[3];
+    apply_inertia(Ipar, Iperp, e, W, L, 0);
+    for (int a = 0; a < 3; a++) L[a] += T[a];
+    const double Lm = sqrt(dot3(L, L));
+    if (Lm > 0.0) {
+        const double k[3] = {L[0] / Lm, L[1] / Lm, L[2] / Lm};
+        const double th = Lm / Iperp;
+        double kxe[3];
+        cross3(k, e, kxe);
+        const double ct = cos(th), st = sin(th), ke = dot3(k, e);
+        double en[3];
+        for (int a = 0; a < 3; a++) en[a] = e[a] * ct + kxe[a] * st + k[a] * ke * (1.0 - ct);
+        const double nn = sqrt(dot3(en, en));
+        for (int a = 0; a < 3; a++) e[a] = en[a] / nn;
+    }
+    apply_inertia(Ipar, Iperp, e, L, W, 1);
+}
+void orc_rotate(const orc_params* p, double W[3], double e[3], const double T[3]) {
+    rotate_particle(p, p->particle_density * particle_volume(p), W, e, T);
+}
+
 static double particle_mass(const orc_state* s) {
-    return s->p.particle_density * 4.0 / 3.0 * M_PI * s->p.radius * s->p.radius * s->p.radius;
+    if (is_sphere(&s->p)) return s->p.particle_density * 4.0 / 3.0 * M_PI * s->p.radius * s->p.radius * s->p.radius;
+    return s->p.particle_density * particle_volume(&s->p);
 }
 
 static int derive_np(const orc_params* p) {
     if (p->n_particles >= 0) return p->n_particles;
     double N = (double)p->nx * p->ny * p->nz;
-    double v = 4.0 / 3.0 * M_PI * p->radius * p->radius * p->radius;
+    double v = is_sphere(p) ? 4.0 / 3.0 * M_PI * p->radius * p->radius * p->radius : particle_volume(p);
     return (int)floor(p->volume_fraction * N / v + 0.5);
 }
 
@@ -179,7 +275,9 @@ orc_state* orc_create(const orc_params* p, int32_t n_particles) {
     s->Fsave = (double*)calloc(3 * np, sizeof(double));
     s->Tsave = (double*)calloc(3 * np, sizeof(double));
     s->color = (double*)calloc(np, sizeof(double));
+    s->E = (double*)calloc(3 * np, sizeof(double));
     for (int q = 0; q < s->np; q++) s->color[q] = p->color;
+    for (int q = 0; q < s->np; q++) s->E[3 * q + 2] = 1.0;
     for (size_t n = 0; n < N; n++) s->owner[n] = -1;
     return s;
 }
@@ -190,6 +288,7 @@ void orc_destroy(orc_state* s) {
     free(s->rho); free(s->psi); free(s->force); free(s->shell);
     free(s->X); free(s->U); free(s->W); free(s->F); free(s->T); free(s->Fsave); free(s->Tsave);
     free(s->color);
+    free(s->E);
     free(s);
 }
 
@@ -198,6 +297,9 @@ int32_t orc_n_particles(const orc_state* s) { return s->np; }
 void orc_set_particle_colors(orc_state* s, const double* colors) {
     for (int q = 0; q < s->np; q++) s->color[q] = colors[q];
 }
+
+void orc_get_axes(const orc_state* s, double* e) { memcpy(e, s->E, sizeof(double) * 3 * (size_t)s->np); }
+void orc_set_axes(orc_state* s, const double* e) { memcpy(s->E, e, sizeof(double) * 3 * (size_t)s->np); }
 
 /* Squared minimum-image distance from node (x,y,z) to the centre of
  * particle q, evaluated without contraction so that both implementations
@@ -213,11 +315,13 @@ static double node_dist2(const orc_state* s, int x, int y, int z, int q) {
 }
 
 /* Node ownership: a node is solid when it lies inside a sphere
- * (|x - X_p|^2 <= R^2, minimum image); the nearer centre wins; ties go to
- * the lower particle index (reading: the paper only says "inside").
- * Static walls never change.  Result in s->newown. */
+ * (|x - X_p|^2 <= R^2, minimum image) or spheroid (inside_spheroid); the
+ * nearer centre wins; ties go to the lower particle index (reading: the
+ * paper only says "inside").  Static walls never change.  Result in
+ * s->newown. */
 static void claim_nodes(orc_state* s) {
-    const double R = s->p.radius, R2 = R * R;
+    const double R = bound_radius(&s->p), R2 = s->p.radius * s->p.radius;
+    const int sphere = is_sphere(&s->p);
     for (int64_t n = 0; n < s->N; n++) {
         s->newown[n] = (s->owner[n] == -2) ? -2 : -1;
         s->best[n] = 0.0;
@@ -238,7 +342,14 @@ static void claim_nodes(orc_state* s) {
                     int64_t n = nidx(s, x, y, z);
                     if (s->newown[n] == -2) continue;
                     double d2 = node_dist2(s, x, y, z, q);
-                    if (d2 > R2) continue;
+                    if (sphere) {
+                        if (d2 > R2) continue;
+                    } else {
+                        const double d[3] = {mimg((double)x - s->X[3 * q + 0], (double)s->nx),
+                                             mimg((double)y - s->X[3 * q + 1], (double)s->ny),
+                                             mimg((double)z - s->X[3 * q + 2], (double)s->nz)};
+                        if (!inside_spheroid(&s->p, d, &s->E[3 * q])) continue;
+                    }
                     int cur = s->newown[n];
                     if (cur == -1 || d2 < s->best[n] || (d2 == s->best[n] && q < cur)) {
                         s->newown[n] = q;
@@ -542,12 +653,12 @@ static void stream_bounce(orc_state* s) {
  *                 h_min (reading: the printed "-1" would make the force jump
  *                 at the stated cut-off 2/3; 1/h_c keeps it continuous);
  *   nu = c_s^2 (tau - 1/2) with tau the mean of the two components.
- * Then leap-frog: U += F/m, omega += T/J, X += U. */
+ * (Spheroids: 2R becomes the contact distance sigma, R becomes sigma / 2.)
+ * Then leap-frog: U += F/m, the rotation of rotate_particle, X += U. */
 /* Pair force on particle p from particle q (Hertz + lubrication, see
  * md_update); r = X_p - X_q with the minimum image. */
 static void pair_force(const orc_params* P, const double Lb[3], const double* Xp, const double* Xq,
-                       const double* Up, const double* Uq, double Fp[3]) {
-    const double R = P->radius;
+                       const double* Up, const double* Uq, const double* ep, const double* eq, double Fp[3]) {
     double nu = (1.0 / 3.0) * (0.5 * (P->tau[0] + P->tau[1]) - 0.5);
     double r[3];
     Fp[0] = Fp[1] = Fp[2] = 0.0;
@@ -555,11 +666,14 @@ static void pair_force(const orc_params* P, const double Lb[3], const double* Xp
     double d = sqrt(dot3(r, r));
     if (d <= 0.0) return;
     double rh[3] = {r[0] / d, r[1] / d, r[2] / d};
-    if (d < 2.0 * R) {
-        double mag = 2.5 * P->k_hertz * pow(2.0 * R - d, 1.5);
+    /* contact distance: 2R for spheres; for spheroids the sum of the
+     * support radii along r_hat, with sigma / 2 in place of R below */
+    const double sigma = orc_contact_distance(P, rh, ep, eq), R = 0.5 * sigma;
+    if (d < sigma) {
+        double mag = 2.5 * P->k_hertz * pow(sigma - d, 1.5);
         for (int a = 0; a < 3; a++) Fp[a] += mag * rh[a];
     }
-    double h = d - 2.0 * R;
+    double h = d - sigma;
     if (h < P->lub_cut) {
         double he = h < P->lub_min ? P->lub_min : h;
         double du[3] = {Up[0] - Uq[0], Up[1] - Uq[1], Up[2] - Uq[2]};
@@ -571,12 +685,12 @@ static void pair_force(const orc_params* P, const double Lb[3], const double* Xp
 void orc_pair_force(const orc_params* P, const double Xp[3], const double Xq[3], const double Up[3],
                     const double Uq[3], double Fp[3]) {
     double Lb[3] = {(double)P->nx, (double)P->ny, (double)P->nz};
-    pair_force(P, Lb, Xp, Xq, Up, Uq, Fp);
+    const double ez[3] = {0.0, 0.0, 1.0};
+    pair_force(P, Lb, Xp, Xq, Up, Uq, ez, ez, Fp);
 }
 
 static void md_update(orc_state* s) {
     const int np = s->np;
-    const double R = s->p.radius;
     memcpy(s->Fsave, s->F, 3 * sizeof(double) * (np > 0 ? np : 1));
     memcpy(s->Tsave, s->T, 3 * sizeof(double) * (np > 0 ? np : 1));
     if (np == 0) return;
@@ -584,18 +698,19 @@ static void md_update(orc_state* s) {
     for (int p = 0; p < np; p++)
         for (int q = p + 1; q < np; q++) {
             double Fp[3];
-            pair_force(&s->p, Lb, &s->X[3 * p], &s->X[3 * q], &s->U[3 * p], &s->U[3 * q], Fp);
+            pair_force(&s->p, Lb, &s->X[3 * p], &s->X[3 * q], &s->U[3 * p], &s->U[3 * q], &s->E[3 * p], &s->E[3 * q],
+                       Fp);
             for (int a = 0; a < 3; a++) {
                 s->F[3 * p + a] += Fp[a];
                 s->F[3 * q + a] -= Fp[a];
             }
         }
-    double m = particle_mass(s), J = 0.4 * m * R * R;
+    double m = particle_mass(s);
     for (int p = 0; p < np; p++) {
         if (!s->p.fixed_particles) {
+            rotate_particle(&s->p, m, &s->W[3 * p], &s->E[3 * p], &s->T[3 * p]);
             for (int a = 0; a < 3; a++) {
                 s->U[3 * p + a] += s->F[3 * p + a] / m;
-                s->W[3 * p + a] += s->T[3 * p + a] / J;
                 double xn = s->X[3 * p + a] + s->U[3 * p + a];
                 xn -= Lb[a] * floor(xn / Lb[a]);
                 if (xn >= Lb[a]) xn -= Lb[a];
@@ -663,8 +778,10 @@ int orc_init_fields(orc_state* s, const double* rho, const double* u, const doub
 
 /* Seeded init.  Stream 0 of SplitMix64(seed) drives random sequential
  * addition: candidate centres X = L * u (three draws), accepted when the
- * minimum-image distance to every earlier centre is at least 2R; at most
- * 10^6 candidates.  Stream 1 + c gives the node noise of component c:
+ * minimum-image distance to every earlier centre is at least 2R (2 c for
+ * prolate spheroids); at most 10^6 candidates.  Spheroids take their axes
+ * from stream 3: z = 2 u - 1, phi = 2 pi u' (draws 2q, 2q + 1), e =
+ * (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z).  Stream 1 + c gives the node noise of component c:
  * rho^c(n) = rho_init^c + a (2 u - 1) with u the n-th draw.  Stream seeds
  * are the first outputs of SplitMix64(seed): s_k = splitmix64(seed, k). */
 int orc_init_from_seed(orc_state* s, uint64_t seed) {
@@ -675,7 +792,7 @@ int orc_init_from_seed(orc_state* s, uint64_t seed) {
     double* parts = (double*)calloc(9 * (size_t)(s->np > 0 ? s->np : 1), sizeof(double));
     uint64_t draw = 0;
     int placed = 0;
-    const double dmin2 = 4.0 * s->p.radius * s->p.radius;
+    const double dmin2 = 4.0 * bound_radius(&s->p) * bound_radius(&s->p);
     for (int64_t attempt = 0; placed < s->np; attempt++) {
         if (attempt >= 1000000) {
             free(parts);
@@ -694,6 +811,17 @@ int orc_init_from_seed(orc_state* s, uint64_t seed) {
         if (!ok) continue;
         for (int a = 0; a < 3; a++) parts[9 * placed + a] = c[a];
         placed++;
+    }
+    if (!is_sphere(&s->p)) {
+        const uint64_t se = orc_splitmix64(seed, 3);
+        for (int q = 0; q < s->np; q++) {
+            const double zc = 2.0 * orc_unit(se, 2 * (uint64_t)q) - 1.0;
+            const double ph = 2.0 * M_PI * orc_unit(se, 2 * (uint64_t)q + 1);
+            const double rr = sqrt(1.0 - zc * zc);
+            s->E[3 * q + 0] = rr * cos(ph);
+            s->E[3 * q + 1] = rr * sin(ph);
+            s->E[3 * q + 2] = zc;
+        }
     }
     double* rho = (double*)malloc(2 * (size_t)N * sizeof(double));
     for (int c = 0; c < 2; c++)

@@ -16,7 +16,8 @@
  *                0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = the 12 face
  *                diagonals in opposite pairs (odd i, i+1).
  *   owner[n]     -1 fluid, -2 static wall, p >= 0 solid node of particle p.
- *   particle     9 doubles: X[3], U[3], omega[3].
+ *   particle     9 doubles: X[3], U[3], omega[3]; spheroids also carry a
+ *                body axis e[3] (orc_get_axes / orc_set_axes).
  */
 #ifndef LBREF_H
 #define LBREF_H
@@ -45,6 +46,7 @@ typedef struct {
     int32_t fixed_particles;    /* 1: particles never move (test-only) */
     int32_t pad_;
     uint64_t seed;
+    double aspect;              /* spheroid: semi-axes R, R, aspect R about the body axis e; 1 = sphere */
 } orc_params;
 
 typedef struct orc_state orc_state;
@@ -84,6 +86,15 @@ int orc_set_state(orc_state* s, const double* f, const int32_t* owner, const dou
 void orc_get_rho(const orc_state* s, double* rho);     /* rho[2][N]: sum of populations, 0 on solid */
 void orc_get_forces(const orc_state* s, double* F, double* T); /* last step's particle F, T before MD */
 void orc_set_particle_colors(orc_state* s, const double* colors);
+/* body axes e[np][3] of the particles (unit vectors; (0,0,1) by default) */
+void orc_get_axes(const orc_state* s, double* e);
+void orc_set_axes(orc_state* s, const double* e);
+/* test hooks for spheroids: inside test of a displacement d (minimum image)
+ * for a particle with axis e; contact distance of two particles along r_hat */
+int32_t orc_inside(const orc_params* p, const double d[3], const double e[3]);
+double orc_contact_distance(const orc_params* p, const double rh[3], const double ep[3], const double eq[3]);
+/* one rotational MD update of a free particle: omega (in/out), e (in/out), torque T */
+void orc_rotate(const orc_params* p, double W[3], double e[3], const double T[3]);
 void orc_observe(const orc_state* s, orc_obs* o);
 /* per-step internals exposed for pins */
 void orc_last_psi(const orc_state* s, double* psi);    /* Psi[2][N] of the last step */

@@ -38,6 +38,7 @@ class OrcParams(C.Structure):
         ("fixed_particles", C.c_int32),
         ("pad_", C.c_int32),
         ("seed", C.c_uint64),
+        ("aspect", C.c_double),
     ]
 
 
@@ -58,7 +59,7 @@ DEFAULTS = dict(
     sc_weight=(2.0, 1.0), rho_init=(0.7, 0.7), noise_amp=0.01, volume_fraction=0.0,
     radius=5.0, particle_density=1.0, color=0.0, k_hertz=100.0, lub_cut=2.0 / 3.0,
     lub_min=0.1, mass_corr_c0=0.0, body_force=(0.0, 0.0, 0.0), vel_mode=0,
-    virtual_fluid=1, fixed_particles=0, seed=1,
+    virtual_fluid=1, fixed_particles=0, seed=1, aspect=1.0,
 )
 
 _lib = None
@@ -96,6 +97,13 @@ def lib():
         L.orc_set_threads.argtypes = [C.c_int32]
         L.orc_pair_force.argtypes = [C.POINTER(OrcParams), dp, dp, dp, dp, dp]
         L.orc_debug_remap.argtypes = [C.c_void_p]
+        L.orc_get_axes.argtypes = [C.c_void_p, dp]
+        L.orc_set_axes.argtypes = [C.c_void_p, dp]
+        L.orc_inside.argtypes = [C.POINTER(OrcParams), dp, dp]
+        L.orc_inside.restype = C.c_int32
+        L.orc_contact_distance.argtypes = [C.POINTER(OrcParams), dp, dp, dp]
+        L.orc_contact_distance.restype = C.c_double
+        L.orc_rotate.argtypes = [C.POINTER(OrcParams), dp, dp, dp]
         _lib = L
     return _lib
 
@@ -155,6 +163,29 @@ def pair_force(Xp, Xq, Up, Uq, **params):
     out = np.zeros(3)
     lib().orc_pair_force(C.byref(P), *[_dp(v) for v in a], _dp(out))
     return out
+
+
+def inside(d, e, **params):
+    """Inside test of displacement d for a particle with body axis e."""
+    P = make_params(**params)
+    dd, ee = np.ascontiguousarray(d, np.float64), np.ascontiguousarray(e, np.float64)
+    return bool(lib().orc_inside(C.byref(P), _dp(dd), _dp(ee)))
+
+
+def contact_distance(rh, ep, eq, **params):
+    P = make_params(**params)
+    a = [np.ascontiguousarray(v, np.float64) for v in (rh, ep, eq)]
+    return float(lib().orc_contact_distance(C.byref(P), *[_dp(v) for v in a]))
+
+
+def rotate(W, e, T, **params):
+    """One rotational MD update of a free particle; returns (omega, e)."""
+    P = make_params(**params)
+    W = np.array(W, np.float64)
+    e = np.array(e, np.float64)
+    T = np.ascontiguousarray(T, np.float64)
+    lib().orc_rotate(C.byref(P), _dp(W), _dp(e), _dp(T))
+    return W, e
 
 
 def set_threads(n):
@@ -230,6 +261,15 @@ class Oracle:
         T = np.zeros((max(self.np, 1), 3))
         lib().orc_get_forces(self._h, _dp(F), _dp(T))
         return F[: self.np], T[: self.np]
+
+    def axes(self):
+        e = np.zeros((max(self.np, 1), 3))
+        lib().orc_get_axes(self._h, _dp(e))
+        return e[: self.np]
+
+    def set_axes(self, e):
+        ee = np.ascontiguousarray(e, np.float64).reshape(-1, 3)
+        lib().orc_set_axes(self._h, _dp(ee))
 
     def set_colors(self, colors):
         col = np.ascontiguousarray(colors, np.float64)

@@ -636,3 +636,131 @@ def test_coverage_brute_force():
     phi2[1, 1, 2] = 1.0
     phi2[1, 1, 3] = -1.0
     assert oan.coverage(phi2, owner, 3) == 0.0
+
+
+# ------------------------------------------------------------- spheroids
+SPH = dict(radius=4.0, aspect=1.75)  # semi-axes 4, 4, 7
+
+
+def _unit(v):
+    v = np.asarray(v, np.float64)
+    return v / np.linalg.norm(v)
+
+
+def test_spheroid_inside_test_and_volume():
+    """Spheroid with semi-axes R, R, c about e (the generality the paper
+    claims for the coupling, Secs. I and III): the oracle's inside test
+    equals (d.e)^2 / c^2 + |d x e|^2 / R^2 <= 1 away from the boundary, and
+    the lattice nodes it counts approach 4/3 pi R^2 c."""
+    rng = np.random.default_rng(5)
+    R, c = SPH["radius"], SPH["radius"] * SPH["aspect"]
+    for _ in range(2000):
+        e = _unit(rng.normal(size=3))
+        d = rng.uniform(-8, 8, size=3)
+        q = np.dot(d, e) ** 2 / c ** 2 + np.sum(np.cross(d, e) ** 2) / R ** 2
+        if abs(q - 1.0) < 1e-9:
+            continue
+        assert ref.inside(d, e, **SPH) == (q <= 1.0)
+    e = _unit([0.3, -0.5, 0.8])
+    X = np.array([0.37, 0.21, 0.64])
+    g = np.arange(-9, 10)
+    D = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) - X
+    n = sum(ref.inside(d, e, **SPH) for d in D)
+    assert abs(n / (4.0 / 3.0 * np.pi * R * R * c) - 1.0) < 0.03, n
+
+
+def test_spheroid_claims_and_placement():
+    """Seeded spheroids: each solid node lies inside its owner (the inside
+    test with the particle's own axis), axes are unit vectors, and the node
+    count per particle is near the volume."""
+    o = ref.Oracle(nx=40, ny=40, nz=40, n_particles=6, g_br=0.0, **SPH)
+    o.init_from_seed(7)
+    st = o.get_state()
+    E = o.axes()
+    assert np.allclose(np.linalg.norm(E, axis=1), 1.0)
+    assert not np.allclose(E, [0, 0, 1])
+    z, y, x = np.unravel_index(np.arange(40 ** 3), (40, 40, 40))
+    own = st["owner"]
+    R, c = SPH["radius"], SPH["radius"] * SPH["aspect"]
+    for q in range(6):
+        sel = np.nonzero(own == q)[0]
+        Xq = st["particles"][q, :3]
+        d = np.stack([x[sel], y[sel], z[sel]], 1) - Xq
+        d -= 40 * np.round(d / 40)
+        assert all(ref.inside(v, E[q], **SPH) for v in d[::7])
+        assert abs(len(sel) / (4.0 / 3.0 * np.pi * R * R * c) - 1.0) < 0.05
+
+
+def test_spheroid_contact_distance():
+    """Contact distance along the line of centres: 2R for spheres, 2c end to
+    end, 2R side by side, R + c for a T configuration."""
+    R, c = SPH["radius"], SPH["radius"] * SPH["aspect"]
+    ez, ex = np.array([0, 0, 1.0]), np.array([1.0, 0, 0])
+    assert ref.contact_distance(ez, ex, ex, radius=R) == 2 * R
+    assert abs(ref.contact_distance(ez, ez, ez, **SPH) - 2 * c) < 1e-12
+    assert abs(ref.contact_distance(ez, ex, ex, **SPH) - 2 * R) < 1e-12
+    assert abs(ref.contact_distance(ez, ez, ex, **SPH) - (R + c)) < 1e-12
+
+
+def test_free_rotation_of_a_spheroid():
+    """Torque-free rotation (Euler's equations of a symmetric top): spin
+    about the symmetry axis leaves e fixed; spin perpendicular to it turns e
+    by |omega| per step in that plane; in general L = I(e) omega is
+    conserved and e precesses about L at |L| / I_perp while keeping its
+    angle to L (exactly, for the update that turns e about L).  A swapped
+    I_par / I_perp or a wrong inverse fails this."""
+    m = SPH.get("particle_density", 1.0) * 4.0 / 3.0 * np.pi * SPH["radius"] ** 2 * SPH["radius"] * SPH["aspect"]
+    R, c = SPH["radius"], SPH["radius"] * SPH["aspect"]
+    Ipar, Iperp = 0.4 * m * R * R, 0.2 * m * (R * R + c * c)
+    T0 = np.zeros(3)
+    e0 = _unit([0.2, -0.3, 0.9])
+    W, e = ref.rotate(0.01 * e0, e0, T0, **SPH)
+    assert np.allclose(e, e0, atol=1e-15) and np.allclose(W, 0.01 * e0, atol=1e-15)
+    w = 0.003
+    W, e = np.array([0.0, w, 0.0]), np.array([0.0, 0.0, 1.0])
+    for _ in range(100):
+        W, e = ref.rotate(W, e, T0, **SPH)
+    assert np.allclose(e, [np.sin(100 * w), 0.0, np.cos(100 * w)], atol=1e-12)
+    e = _unit([0.1, 0.2, 0.97])
+    W = np.array([0.004, -0.002, 0.006])
+
+    def Lof(W, e):
+        return Iperp * W + (Ipar - Iperp) * np.dot(e, W) * e
+
+    L0 = Lof(W, e)
+    Lh = L0 / np.linalg.norm(L0)
+    cos0 = np.dot(e, Lh)
+    e_perp0 = _unit(e - cos0 * Lh)
+    n = 400
+    for _ in range(n):
+        W, e = ref.rotate(W, e, T0, **SPH)
+    assert np.allclose(Lof(W, e), L0, rtol=1e-12, atol=1e-16)
+    assert abs(np.dot(e, Lh) - cos0) < 1e-12
+    ep = _unit(e - np.dot(e, Lh) * Lh)
+    ang = np.arctan2(np.dot(np.cross(e_perp0, ep), Lh), np.dot(e_perp0, ep))
+    expect = np.mod(n * np.linalg.norm(L0) / Iperp + np.pi, 2 * np.pi) - np.pi
+    assert abs(ang - expect) < 1e-9, (ang, expect)
+
+
+def test_spheroid_momentum_conserved_in_fluid():
+    """Moving, rotating spheroids exchange momentum with the fluid through
+    the same links, cover/uncover and contact forces as spheres: fluid plus
+    particle momentum is conserved to rounding."""
+    o = ref.Oracle(nx=28, ny=24, nz=30, n_particles=3, g_br=0.1, color=0.02, particle_density=3.0, **SPH)
+    o.init_from_seed(11)
+    st = o.get_state()
+    P = st["particles"].copy()
+    P[:, 3:6] = [[0.05, -0.03, 0.02], [-0.04, 0.02, 0.03], [0.01, 0.05, -0.04]]
+    P[:, 6:9] = [[0.01, 0.02, -0.01], [0.0, -0.02, 0.015], [0.02, 0.0, 0.01]]
+    E = o.axes()
+    o2 = ref.Oracle(nx=28, ny=24, nz=30, n_particles=3, g_br=0.1, color=0.02, particle_density=3.0, **SPH)
+    o2.set_axes(E)
+    o2.init_fields(lbinputs.mixture((28, 24, 30), amp=0.05, seed=12), particles=P)
+    ob0 = o2.observe()
+    p0 = ob0["mom_fluid"] + ob0["mom_part"]
+    o2.step(30)
+    ob = o2.observe()
+    assert ob["n_cover"] > 0 and ob["n_uncover"] > 0
+    p1 = ob["mom_fluid"] + ob["mom_part"]
+    assert np.all(np.abs(p1 - p0) < 1e-12 * (ob["mass"].sum() + 1)), p1 - p0
+    assert not np.allclose(o2.axes(), E)
