@@ -73,8 +73,8 @@ typedef struct {
     double rho_init[2];          /* mean initial density per component */
     double noise_amp;            /* seeded init: rho^c = rho_init^c + U(-a, a) per node */
     double volume_fraction;      /* alpha, used when n_particles < 0 */
-    double radius;               /* sphere radius r_par (all particles) */
-    double particle_density;     /* m = rho_p 4/3 pi R^3, J = 2/5 m R^2 */
+    double radius;               /* sphere radius r_par (all particles); for spheroids the equatorial semi-axis R */
+    double particle_density;     /* m = rho_p 4/3 pi R^3 (spheroids: R^2 c), J = 2/5 m R^2 */
     double color;                /* particle colour Delta rho; used when contact_angle_deg is NaN */
     double contact_angle_deg;    /* if finite: Delta rho = (theta - 90) / 442 (fit of Fig. 4b) */
     double k_hertz;              /* K_Hertz of Eq. eq:hertz */
@@ -86,6 +86,8 @@ typedef struct {
     int32_t fixed_particles;     /* 1: particles keep X, U, omega (prescribed motion; tests) */
     int32_t precision;           /* LB_FP64 / LB_FP32 / LB_FP16_DEV / LB_BF16_DEV, same for all boxes */
     int32_t reserved;            /* must be 0 */
+    double aspect;               /* particle shape: 0 or 1 sphere; otherwise a spheroid with semi-axes
+                                    R, R, c = aspect R about a body axis (0.1 <= aspect <= 10); see lb_set_axes */
 } lb_params;
 
 /* Observables of one box (lb_observables). */
@@ -164,6 +166,20 @@ int lb_export_rho(lb_handle* h, int32_t box, double* rho);
  * lb_init_from_seed, lb_init_fields and lb_import_state give every particle
  * the box colour, so call this after them. */
 int lb_set_particle_colors(lb_handle* h, int32_t box, const double* colors);
+
+/* Body axes of the particles of one box, e[n_particles][3] unit vectors
+ * (spheroids; spheres ignore them).  The paper's coupling is written for any
+ * particle shape (Secs. I and III); for spheroids the node claims use the
+ * spheroid inside test, the contact laws the distance at which the surfaces
+ * meet along the line of centres, and the MD turns the axis about the
+ * angular momentum (exact for torque-free motion).  lb_init_from_seed draws
+ * the axes (stream 3 of the box seed); lb_init_fields uses the last axes set
+ * here ((0, 0, 1) by default), so call lb_set_axes before it; after an init
+ * it also updates the running state.  lb_get_axes reads the current axes.
+ * LB_EINVAL for a vector whose length differs from 1 by 1e-6 or more.
+ * Synchronise. */
+int lb_set_axes(lb_handle* h, int32_t box, const double* e);
+int lb_get_axes(lb_handle* h, int32_t box, double* e);
 
 /* Fluid-coupling force and torque on each particle of one box in the last
  * step (momentum exchange, cover/uncover, Shan-Chen), before the MD pair

@@ -44,6 +44,7 @@ class LbParams(C.Structure):
         ("fixed_particles", C.c_int32),
         ("precision", C.c_int32),
         ("reserved", C.c_int32),
+        ("aspect", C.c_double),
     ]
 
 
@@ -70,12 +71,13 @@ DEFAULTS = dict(
     sc_weight=(2.0, 1.0), rho_init=(0.7, 0.7), noise_amp=0.01, volume_fraction=0.0,
     radius=5.0, particle_density=1.0, color=0.0, contact_angle_deg=math.nan,
     k_hertz=100.0, lub_cut=2.0 / 3.0, lub_min=0.1, mass_corr_c0=0.0,
-    body_force=(0.0, 0.0, 0.0), vel_mode=0, fixed_particles=0, precision=LB_FP32, reserved=0,
+    body_force=(0.0, 0.0, 0.0), vel_mode=0, fixed_particles=0, precision=LB_FP32, reserved=0, aspect=1.0,
 )
 
 ABI_FUNCTIONS = (
     "lb_workspace_bytes", "lb_create", "lb_init_from_seed", "lb_init_fields", "lb_step", "lb_sync",
     "lb_observables", "lb_export_state", "lb_import_state", "lb_export_rho", "lb_set_particle_colors",
+    "lb_set_axes", "lb_get_axes",
     "lb_particle_forces", "lb_box_info", "lb_set_tiling", "lb_set_profiling", "lb_kernel_time",
     "lb_destroy", "lb_strerror", "lb_field_moments",
 )
@@ -110,6 +112,8 @@ def load_library(path=LIB_PATH):
     L.lb_import_state.argtypes = [vp, C.c_int32, dp, ip, dp, dp]
     L.lb_export_rho.argtypes = [vp, C.c_int32, dp]
     L.lb_set_particle_colors.argtypes = [vp, C.c_int32, dp]
+    L.lb_set_axes.argtypes = [vp, C.c_int32, dp]
+    L.lb_get_axes.argtypes = [vp, C.c_int32, dp]
     L.lb_particle_forces.argtypes = [vp, C.c_int32, dp, dp]
     L.lb_box_info.argtypes = [vp, C.c_int32, ip, C.POINTER(C.c_int64)]
     L.lb_set_tiling.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
@@ -308,6 +312,16 @@ class Simulation:
         nx, ny, nz = self.dims[box]
         r = self.rho(box)
         return (r[0] - r[1]).reshape(nz, ny, nx)
+
+    def set_axes(self, box, e):
+        """Body axes [n_particles][3] of spheroids (unit vectors)."""
+        ee = np.ascontiguousarray(e, np.float64).reshape(-1, 3)
+        _ck(load_library().lb_set_axes(self._h, box, _dp(ee)), "lb_set_axes")
+
+    def axes(self, box=0):
+        e = np.zeros((max(self.n_particles[box], 1), 3))
+        _ck(load_library().lb_get_axes(self._h, box, _dp(e)), "lb_get_axes")
+        return e[: self.n_particles[box]]
 
     def set_colors(self, box, colors):
         c = np.ascontiguousarray(colors, np.float64)

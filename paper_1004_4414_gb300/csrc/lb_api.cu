@@ -42,11 +42,23 @@ const LbOps* ops_for(int prec) {
     }
 }
 
+// spheroid aspect ratio c / R (0 in the struct means a sphere)
+double aspect_of(const lb_params& p) { return p.aspect == 0.0 ? 1.0 : p.aspect; }
+// bounding radius of a particle
+double bound_radius(const lb_params& p) {
+    const double a = aspect_of(p);
+    return a > 1.0 ? a * p.radius : p.radius;
+}
+double particle_volume(const lb_params& p) {
+    const double a = aspect_of(p);
+    if (a == 1.0) return 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
+    return 4.0 / 3.0 * M_PI * p.radius * p.radius * (a * p.radius);
+}
+
 int derive_np(const lb_params& p) {
     if (p.n_particles >= 0) return p.n_particles;
     const double N = (double)p.nx * p.ny * p.nz;
-    const double v = 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
-    return (int)std::floor(p.volume_fraction * N / v + 0.5);
+    return (int)std::floor(p.volume_fraction * N / particle_volume(p) + 0.5);
 }
 
 double box_color(const lb_params& p) {
@@ -68,6 +80,7 @@ int validate(const lb_params* bx, int nb) {
         if (p.precision != bx[0].precision || !ops_for(p.precision)) return LB_EINVAL;
         if (p.vel_mode != 0 && p.vel_mode != 1) return LB_EINVAL;
         if (p.reserved != 0) return LB_EINVAL;
+        if (!(p.aspect >= 0.0 && p.aspect <= 10.0) || (p.aspect != 0.0 && !(p.aspect >= 0.1))) return LB_EINVAL;
         if (derive_np(p) < 0) return LB_EINVAL;
         if (!(p.lub_min > 0.0) || !(p.lub_cut > p.lub_min)) return LB_EINVAL;
     }
@@ -82,7 +95,7 @@ CellGeom cell_geom(const lb_params& p) {
     // cells at least 2R + 2 wide: neighbour list for node claims (centre
     // distance <= 2R + 2) and lubrication (gap < lub_cut <= 2) fit in +-1 cell
     CellGeom g;
-    const double cmin = 2.0 * p.radius + 2.0 + (p.lub_cut > 2.0 ? p.lub_cut - 2.0 : 0.0);
+    const double cmin = 2.0 * bound_radius(p) + 2.0 + (p.lub_cut > 2.0 ? p.lub_cut - 2.0 : 0.0);
     const int L[3] = {p.nx, p.ny, p.nz};
     for (int a = 0; a < 3; a++) {
         int n = (int)std::floor(L[a] / cmin);
@@ -96,7 +109,7 @@ CellGeom cell_geom(const lb_params& p) {
 int ev_cap_for(const lb_params& p, int np) {
     // per step a sphere moving less than one node changes at most the nodes
     // of a shell of width one around its surface
-    const double R = p.radius;
+    const double R = bound_radius(p);
     const double per = 4.0 * M_PI * (R + 1.5) * (R + 1.5) * 1.5 + 64.0;
     return (int)(np * per) + 1024;
 }
@@ -124,6 +137,7 @@ struct lb_handle {
     int NP = 0, total_cells = 0;
     std::vector<int> pstart, npb, cell_off;
     std::vector<int> has_walls;
+    std::vector<std::vector<double>> axes;  // per box: body axes [np][3] used by the next init
     double* stage = nullptr;
     size_t stage_doubles = 0;
     double* obs_buf = nullptr;   // [OBS_BLOCKS * OBS_W + OBS_W]
@@ -222,7 +236,7 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     {
         // shell nodes of one sphere: a one-node layer around its surface
         double rmax = 0.0;
-        for (int b = 0; b < nb; b++) rmax = bx[b].radius > rmax ? bx[b].radius : rmax;
+        for (int b = 0; b < nb; b++) rmax = bound_radius(bx[b]) > rmax ? bound_radius(bx[b]) : rmax;
         sh.shell_cap = (int)(12.0 * (rmax + 1.0) * (rmax + 1.0)) + 64;
     }
     sh.shell_list = cv.take<int4>((size_t)NPa * sh.shell_cap);
@@ -270,8 +284,14 @@ void fill_params(lb_handle* h) {
         B.scw_diag = p.sc_weight[1];
         for (int a = 0; a < 3; a++) B.body[a] = p.body_force[a];
         B.radius = p.radius;
-        B.mass = p.particle_density * 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
+        B.aspect = aspect_of(p);
+        B.rb = bound_radius(p);
+        B.mass = p.particle_density * particle_volume(p);
         B.inertia = 0.4 * B.mass * p.radius * p.radius;
+        // spheroid (semi-axes R, R, c): about the axis 2/5 m R^2, across it
+        // 1/5 m (R^2 + c^2)
+        B.ipar = B.inertia;
+        B.iperp = 0.2 * B.mass * (p.radius * p.radius + (B.aspect * p.radius) * (B.aspect * p.radius));
         B.k_hertz = p.k_hertz;
         B.lub_cut = p.lub_cut;
         B.lub_min = p.lub_min;
@@ -437,10 +457,11 @@ int read_err(lb_handle* h) {
 int rsa_place(const lb_params& p, int np, uint64_t s0, std::vector<double>& parts) {
     parts.assign((size_t)np * 9, 0.0);
     const double L[3] = {(double)p.nx, (double)p.ny, (double)p.nz};
-    const double dmin2 = 4.0 * p.radius * p.radius;
+    const double rb = bound_radius(p);
+    const double dmin2 = 4.0 * rb * rb;
     int gc[3];
     for (int a = 0; a < 3; a++) {
-        gc[a] = (int)std::floor(L[a] / (2.0 * p.radius));
+        gc[a] = (int)std::floor(L[a] / (2.0 * rb));
         if (gc[a] < 1) gc[a] = 1;
     }
     std::vector<std::vector<int>> grid((size_t)gc[0] * gc[1] * gc[2]);
@@ -496,11 +517,13 @@ int init_box(lb_handle* h, int b, const double* parts_host, const int32_t* walls
         std::vector<PartState> ps(np);
         std::vector<int> pb(np, b);
         std::vector<double> col(np, box_color(h->params[b]));
+        const std::vector<double>& ax = h->axes[b];
         for (int q = 0; q < np; q++)
             for (int a = 0; a < 3; a++) {
                 ps[q].X[a] = parts_host[9 * q + a];
                 ps[q].U[a] = parts_host[9 * q + 3 + a];
                 ps[q].W[a] = parts_host[9 * q + 6 + a];
+                ps[q].E[a] = ax[3 * q + a];
             }
         CK(cudaMemcpyAsync(h->sh.part + B.pstart, ps.data(), sizeof(PartState) * np, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(h->sh.pbox + B.pstart, pb.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
@@ -620,6 +643,11 @@ int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t
         if (boxes[b].tau[0] != 1.0 || boxes[b].tau[1] != 1.0) h->tau1 = 0;
     layout(h, boxes, n_boxes, h->ws);
     fill_params(h);
+    h->axes.resize(n_boxes);
+    for (int b = 0; b < n_boxes; b++) {
+        h->axes[b].assign((size_t)3 * h->hbox[b].np, 0.0);
+        for (int q = 0; q < h->hbox[b].np; q++) h->axes[b][3 * q + 2] = 1.0;
+    }
     if (h->ops->setup() != cudaSuccess || cudaHostAlloc((void**)&h->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming) != cudaSuccess) {
         lb_destroy(h);
@@ -660,6 +688,20 @@ int lb_init_from_seed(lb_handle* h, uint64_t seed) {
         std::vector<double> parts;
         int rc = rsa_place(h->params[b], h->hbox[b].np, s0, parts);
         if (rc != LB_OK) return rc;
+        // spheroid axes from stream 3: z = 2u - 1, phi = 2 pi u' (draws
+        // 2q, 2q + 1), e = (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z)
+        if (aspect_of(h->params[b]) != 1.0) {
+            const uint64_t se = sm64(sb, 3);
+            std::vector<double>& ax = h->axes[b];
+            for (int q = 0; q < h->hbox[b].np; q++) {
+                const double zc = 2.0 * sm64_unit(se, 2 * (uint64_t)q) - 1.0;
+                const double ph = 2.0 * M_PI * sm64_unit(se, 2 * (uint64_t)q + 1);
+                const double rr = std::sqrt(1.0 - zc * zc);
+                ax[3 * q + 0] = rr * std::cos(ph);
+                ax[3 * q + 1] = rr * std::sin(ph);
+                ax[3 * q + 2] = zc;
+            }
+        }
         rc = init_box(h, b, parts.data(), nullptr, nullptr, nullptr, s_red, s_blue, h->params[b].noise_amp);
         if (rc != LB_OK) return rc;
     }
@@ -830,11 +872,19 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
         std::vector<PartState> ps(B.np);
         std::vector<int> pb(B.np, box);
         std::vector<double> col(B.np, box_color(h->params[box]));
+        // spheroid axes are not part of this format: a box that was stepped
+        // keeps its current axes, otherwise those of the last lb_set_axes
+        std::vector<double> ax = h->axes[box];
+        if (h->initialised) {
+            int rc = lb_get_axes(h, box, ax.data());
+            if (rc != LB_OK) return rc;
+        }
         for (int q = 0; q < B.np; q++)
             for (int a = 0; a < 3; a++) {
                 ps[q].X[a] = particles[9 * q + a];
                 ps[q].U[a] = particles[9 * q + 3 + a];
                 ps[q].W[a] = particles[9 * q + 6 + a];
+                ps[q].E[a] = ax[3 * q + a];
             }
         CK(cudaMemcpyAsync(h->sh.part + B.pstart, ps.data(), sizeof(PartState) * B.np, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(h->sh.pbox + B.pstart, pb.data(), sizeof(int) * B.np, cudaMemcpyHostToDevice, st));
@@ -894,6 +944,34 @@ int lb_set_particle_colors(lb_handle* h, int32_t box, const double* colors) {
     const BoxDev& B = h->hbox[box];
     if (B.np == 0) return LB_OK;
     CK(cudaMemcpyAsync(h->sh.color + B.pstart, colors, sizeof(double) * B.np, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_set_axes(lb_handle* h, int32_t box, const double* e) {
+    if (!h || !e || box < 0 || box >= h->nb) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    if (B.np == 0) return LB_OK;
+    std::vector<double> v((size_t)3 * B.np);
+    for (int q = 0; q < B.np; q++) {
+        const double n = std::sqrt(e[3 * q] * e[3 * q] + e[3 * q + 1] * e[3 * q + 1] + e[3 * q + 2] * e[3 * q + 2]);
+        if (!(std::fabs(n - 1.0) < 1e-6)) return LB_EINVAL;
+        for (int a = 0; a < 3; a++) v[3 * q + a] = e[3 * q + a];
+    }
+    h->axes[box] = v;
+    // the device copy (strided into the particle records)
+    CK(cudaMemcpy2DAsync(reinterpret_cast<char*>(h->sh.part + B.pstart) + offsetof(PartState, E), sizeof(PartState),
+                         v.data(), 3 * sizeof(double), 3 * sizeof(double), B.np, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_get_axes(lb_handle* h, int32_t box, double* e) {
+    if (!h || !e || box < 0 || box >= h->nb) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    if (B.np == 0) return LB_OK;
+    CK(cudaMemcpy2DAsync(e, 3 * sizeof(double), reinterpret_cast<const char*>(h->sh.part + B.pstart) + offsetof(PartState, E),
+                         sizeof(PartState), 3 * sizeof(double), B.np, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return LB_OK;
 }

@@ -12,10 +12,11 @@ static __global__ void k_fill(T* __restrict__ p, T v, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
-// Claim of the nodes inside each sphere for a state with no previous status:
-// pass 1 keeps the smallest squared distance per node (FP64 bits, which
-// order like the values for non-negative numbers), pass 2 the lowest
-// particle index among the particles at that distance.
+// Claim of the nodes inside each particle (sphere or spheroid, inside_shape)
+// for a state with no previous status: pass 1 keeps the smallest squared
+// centre distance per node (FP64 bits, which order like the values for
+// non-negative numbers), pass 2 the lowest particle index among the
+// particles at that distance.
 template <int PASS>
 static __global__ void k_claim(const BoxDev* __restrict__ boxes, Shared sh, int b, unsigned long long* __restrict__ key,
                         int* __restrict__ idbuf) {
@@ -25,7 +26,7 @@ static __global__ void k_claim(const BoxDev* __restrict__ boxes, Shared sh, int 
     if (lp >= B.np) return;
     const int p = B.pstart + lp;
     const PartState ps = sh.part[p];
-    const double R = B.radius, R2 = R * R;
+    const double R = B.rb;
     const int dims[3] = {B.nx, B.ny, B.nz};
     int lo[3], span[3];
     for (int a = 0; a < 3; a++) {
@@ -37,9 +38,10 @@ static __global__ void k_claim(const BoxDev* __restrict__ boxes, Shared sh, int 
     for (int idx = lane; idx < total; idx += 32) {
         const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
         const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
-        const double d2 = dist2_nc(mimg((double)gx - ps.X[0], B.nx), mimg((double)gy - ps.X[1], B.ny),
-                                   mimg((double)gz - ps.X[2], B.nz));
-        if (d2 > R2) continue;
+        const double dx = mimg((double)gx - ps.X[0], B.nx), dy = mimg((double)gy - ps.X[1], B.ny),
+                     dz = mimg((double)gz - ps.X[2], B.nz);
+        if (!inside_shape(B, dx, dy, dz, ps.E)) continue;
+        const double d2 = dist2_nc(dx, dy, dz);
         const int n = gx + B.nx * (gy + B.ny * gz);
         if (B.owner[n] == OWN_WALL) continue;
         const unsigned long long k = (unsigned long long)__double_as_longlong(d2);

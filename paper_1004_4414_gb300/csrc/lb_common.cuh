@@ -43,6 +43,7 @@ constexpr int ERR_UNSTABLE = 1, ERR_OVERFLOW = 2, ERR_FAST_PARTICLE = 4;
 // ---------------------------------------------------------------- particles
 struct PartState {        // per particle, FP64
     double X[3], U[3], W[3];
+    double E[3];          // body axis of a spheroid (unit vector; unused for spheres)
 };
 struct PartStateF {       // FP32 copy read by the FP32 fluid kernels (GB300's FP64 rate is low)
     float X[3], U[3], W[3];
@@ -78,6 +79,9 @@ struct BoxDev {
     double rho_ref[2];          // reference density of the deviation storage
     double body[3];
     double radius, mass, inertia, k_hertz, lub_cut, lub_min, nu;
+    double aspect;              // spheroid semi-axes radius, radius, aspect * radius; 1 = sphere
+    double rb;                  // bounding radius: max(radius, aspect * radius)
+    double ipar, iperp;         // spheroid moments of inertia about / across the axis
     double c0, rho_init[2];
     double mass0[2];            // initial fluid mass
     double* mass_acc;           // [2 slots][2 components] fluid mass produced by the step kernel
@@ -323,5 +327,35 @@ __device__ __forceinline__ double dist2_nc(double dx, double dy, double dz) {
 }
 
 __device__ __forceinline__ void set_err(int* err, int bits) { atomicOr(err, bits); }
+
+// ------------------------------------------------- particle shapes
+// Spheres, or spheroids with semi-axes R, R, c = aspect R about the body
+// axis e.  Inside test of a displacement d (minimum image): |d|^2 <= R^2,
+// or R^2 (d.e)^2 + c^2 (|d|^2 - (d.e)^2) <= R^2 c^2, each product and sum
+// rounded in this order without contraction, so that every implementation
+// decides alike.
+__device__ __forceinline__ bool inside_shape(const BoxDev& B, double dx, double dy, double dz, const double* e) {
+    const double R2 = B.radius * B.radius;
+    const double d2 = dist2_nc(dx, dy, dz);
+    if (B.aspect == 1.0) return d2 <= R2;
+    const double c = B.aspect * B.radius, c2 = c * c;
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, e[0]), __dmul_rn(dy, e[1])), __dmul_rn(dz, e[2]));
+    const double s2 = __dmul_rn(s, s);
+    return __dadd_rn(__dmul_rn(R2, s2), __dmul_rn(c2, __dsub_rn(d2, s2))) <= R2 * c2;
+}
+// distance from the centre to the surface along the unit vector n
+__device__ __forceinline__ double support_radius(const BoxDev& B, const double* n, const double* e) {
+    const double R = B.radius, c = B.aspect * B.radius;
+    double t2 = n[0] * e[0] + n[1] * e[1] + n[2] * e[2];
+    t2 *= t2;
+    if (t2 > 1.0) t2 = 1.0;
+    return 1.0 / sqrt(t2 / (c * c) + (1.0 - t2) / (R * R));
+}
+// contact distance of two particles along the line of centres r_hat: 2R for
+// spheres, the sum of the support radii for spheroids
+__device__ __forceinline__ double contact_distance(const BoxDev& B, const double* rh, const double* ep, const double* eq) {
+    if (B.aspect == 1.0) return 2.0 * B.radius;
+    return support_radius(B, rh, ep) + support_radius(B, rh, eq);
+}
 
 }  // namespace lbp

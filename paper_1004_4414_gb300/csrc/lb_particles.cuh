@@ -96,7 +96,7 @@ static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev*
     if (p >= NP) return;  // the whole warp leaves together
     const BoxDev& B = boxes[sh.pbox[p]];
     const PartStateF pf = sh.partf[p];
-    const float reach = 2.0f * (float)B.radius + fmaxf(2.0f, (float)B.lub_cut);
+    const float reach = 2.0f * (float)B.rb + fmaxf(2.0f, (float)B.lub_cut);
     const float lim2 = reach * reach * 1.0001f + 1e-3f;
     const float Lf[3] = {(float)B.nx, (float)B.ny, (float)B.nz};
     // the block of cells around the cell of p (from its FP64 position)
@@ -180,14 +180,18 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
     const int b = sh.pbox[p];
     const BoxDev& B = boxes[b];
     const PartStateF pf = sh.partf[p];
-    const double R = B.radius, R2 = R * R;
+    // spheres: FP32 distances decide away from R^2 and FP64 within a band
+    // of it; spheroids: the FP64 inside test (inside_shape) for every node
+    const bool sph = B.aspect == 1.0;
+    const double R = B.rb, R2 = B.radius * B.radius;
     const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
     const float Lf[3] = {(float)B.nx, (float)B.ny, (float)B.nz};
     const int nn = sh.nlist_n[p];
-    // A node inside p can also be inside q only if |X_q - X_p| <= 2R: those
-    // neighbours (the close list; 0.05 of slack covers the FP32 centres)
-    // decide the claims of nodes inside p.  A node p owned but left may lie
-    // within 2R + 1.5 of q, so that rare case scans the whole list.
+    // A node inside p can also be inside q only if |X_q - X_p| <= 2R (R the
+    // bounding radius): those neighbours (the close list; 0.05 of slack
+    // covers the FP32 centres) decide the claims of nodes inside p.  A node
+    // p owned but left may lie within 2R + 1.5 of q, so that rare case scans
+    // the whole list.
     const float rcl = 2.0f * (float)R + 0.05f;
     int ncl = 0;
     {
@@ -225,7 +229,8 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
     const int total = span[0] * span[1] * span[2];
     const float Rf2o = (float)((R + 1.5) * (R + 1.5));
     const float R2f = (float)R2;
-    const float band = (float)(0.02 + 2e-3 * R2);
+    const float band = (float)(0.02 + 2e-3 * R * R);
+    const float qlim = (float)(R * R) + band;  // no node beyond this is inside q
     for (int base = 0; base < total; base += 32) {
         const int idx = base + lane;
         int ev_old = 0, ev_new = 0, node = 0;
@@ -237,22 +242,22 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
             const float d2f = fx * fx + fy * fy + fz * fz;
             if (d2f <= Rf2o) {
                 const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
-                auto exact_d2 = [&](int q) {
+                // FP64 inside test of this node for particle q; d2 = squared
+                // centre distance (the claim goes to the nearest centre)
+                auto exact_in = [&](int q, double& d2) {
                     const double* C = sh.part[q].X;
-                    return dist2_nc(mimg((double)gx - C[0], L[0]), mimg((double)gy - C[1], L[1]),
-                                    mimg((double)gz - C[2], L[2]));
+                    const double dx = mimg((double)gx - C[0], L[0]), dy = mimg((double)gy - C[1], L[1]),
+                                 dz = mimg((double)gz - C[2], L[2]);
+                    d2 = dist2_nc(dx, dy, dz);
+                    return inside_shape(B, dx, dy, dz, sh.part[q].E);
                 };
                 const int n = gx + B.nx * (gy + B.ny * gz);
                 const int own = __ldg(B.owner + n);
                 if (own != OWN_WALL) {
                     double d2p = -1.0;
                     bool inside;
-                    if (fabsf(d2f - R2f) > band) {
-                        inside = d2f < R2f;
-                    } else {
-                        d2p = exact_d2(p);
-                        inside = d2p <= R2;
-                    }
+                    if (sph && fabsf(d2f - R2f) > band) inside = d2f < R2f;
+                    else inside = exact_in(p, d2p);
                     if (inside || own == p) {
                         bool other = false, anyone = false;
                         const int nk = inside ? ncl : nn;
@@ -261,13 +266,13 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
                             const float ex = mimgf(fx - s_rq[wib][k][0], Lf[0]);
                             const float ey = mimgf(fy - s_rq[wib][k][1], Lf[1]);
                             const float ez = mimgf(fz - s_rq[wib][k][2], Lf[2]);
-                            if (ex * ex + ey * ey + ez * ez > R2f + band) continue;
+                            if (ex * ex + ey * ey + ez * ez > qlim) continue;
                             const int q = s_nid[wib][k];
-                            const double d2q = exact_d2(q);
-                            if (d2q <= R2) {
+                            double d2q;
+                            if (exact_in(q, d2q)) {
                                 anyone = true;
                                 if (inside) {
-                                    if (d2p < 0.0) d2p = exact_d2(p);
+                                    if (d2p < 0.0) exact_in(p, d2p);
                                     if (d2q < d2p || (d2q == d2p && q < p)) other = true;
                                 }
                             }
@@ -510,7 +515,7 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     const int32_t* __restrict__ owner = B.owner;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const size_t N = (size_t)B.N;
-    const float R_ = (float)B.radius;
+    const float R_ = (float)B.rb;  // bounding radius (the radius for spheres)
     const R col = (R)sh.color[p];
     // window: every node within R + 0.5 of the centre (the shell nodes of p
     // lie within R; the 0.5 of slack covers the FP32 centre)
@@ -834,12 +839,14 @@ static __global__ void k_wall_shell(const BoxDev* __restrict__ boxes, int b, int
 //   Hertz (Eq. eq:hertz): -dV/dr = 5/2 K (2R - r)^{3/2} along r_hat, r < 2R;
 //   lubrication (Eq. eqn_ladd_lubrikation): -6 pi nu R^4/(2R)^2 r_hat
 //   [r_hat.(U_p - U_q)] (1/h - 1/h_c) for gap h < h_c, h clamped at h_min.
+// Spheroids: 2R becomes the contact distance along r_hat (contact_distance)
+// and R half of it.
 __device__ __forceinline__ void pair_force(const BoxDev& B, const PartState& a, const PartState& b, double F[3]) {
-    const double R = B.radius;
     double r[3] = {mimg(a.X[0] - b.X[0], B.nx), mimg(a.X[1] - b.X[1], B.ny), mimg(a.X[2] - b.X[2], B.nz)};
     const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
     if (d <= 0.0) return;
     const double rh[3] = {r[0] / d, r[1] / d, r[2] / d};
+    const double sigma = contact_distance(B, rh, a.E, b.E), R = 0.5 * sigma;
     if (d < 2.0 * R) {
         const double ov = 2.0 * R - d;
         const double mag = 2.5 * B.k_hertz * ov * sqrt(ov);
@@ -893,7 +900,35 @@ static __global__ void __launch_bounds__(32 * MD_WARPS) k_md_forces(const BoxDev
     if (lane < 3) fp[lane] = mine + F[lane];
 }
 
-// leap-frog: U += F/m, omega += T/J, X += U (periodic); accumulators zeroed
+// Rotation of a spheroid with torque T: L = I(e) omega, L += T, the axis
+// turns about L by |L| / I_perp (exact for torque-free motion: de/dt =
+// (L x e) / I_perp), then omega = I(e_new)^-1 L; I(e) = I_perp (1 - e e) +
+// I_par e e.
+__device__ __forceinline__ void rotate_spheroid(const BoxDev& B, double W[3], double e[3], const double T[3]) {
+    auto inertia = [&](const double* v, double* o, bool inv) {
+        const double a = inv ? 1.0 / B.iperp : B.iperp, b = inv ? 1.0 / B.ipar : B.ipar;
+        const double t = e[0] * v[0] + e[1] * v[1] + e[2] * v[2];
+        for (int k = 0; k < 3; k++) o[k] = a * v[k] + (b - a) * t * e[k];
+    };
+    double L[3];
+    inertia(W, L, false);
+    for (int a = 0; a < 3; a++) L[a] += T[a];
+    const double Lm = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+    if (Lm > 0.0) {
+        const double k[3] = {L[0] / Lm, L[1] / Lm, L[2] / Lm};
+        const double th = Lm / B.iperp;
+        const double kxe[3] = {k[1] * e[2] - k[2] * e[1], k[2] * e[0] - k[0] * e[2], k[0] * e[1] - k[1] * e[0]};
+        const double ct = cos(th), st = sin(th), ke = k[0] * e[0] + k[1] * e[1] + k[2] * e[2];
+        double en[3];
+        for (int a = 0; a < 3; a++) en[a] = e[a] * ct + kxe[a] * st + k[a] * ke * (1.0 - ct);
+        const double nn = sqrt(en[0] * en[0] + en[1] * en[1] + en[2] * en[2]);
+        for (int a = 0; a < 3; a++) e[a] = en[a] / nn;
+    }
+    inertia(L, W, true);
+}
+
+// leap-frog: U += F/m, omega += T/J (spheroids: rotate_spheroid), X += U
+// (periodic); accumulators zeroed
 static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NP) return;
@@ -902,9 +937,10 @@ static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared s
     PartState ps = sh.part[p];
     if (!B.fixed) {
         const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
+        if (B.aspect != 1.0) rotate_spheroid(B, ps.W, ps.E, fp + 3);
         for (int a = 0; a < 3; a++) {
             ps.U[a] += fp[a] / B.mass;
-            ps.W[a] += fp[3 + a] / B.inertia;
+            if (B.aspect == 1.0) ps.W[a] += fp[3 + a] / B.inertia;
             double xn = ps.X[a] + ps.U[a];
             xn -= L[a] * floor(xn / L[a]);
             if (xn >= L[a]) xn -= L[a];

@@ -412,3 +412,55 @@ def test_deviation_storage(prec, eps, split):
     # on this layered state identical nodes round alike, so the worst case
     # adds up coherently over the 50 steps
     assert np.all(np.abs(ob["mass"] - m0) / m0 < steps * 4 * 2.0 ** -24)
+
+
+# --------------------------------------------------------------- spheroids
+@pytest.mark.parametrize("aspect", [1.75, 0.6])
+def test_spheroid_seeded_init_matches_oracle(aspect):
+    """Seeded spheroids (semi-axes R, R, aspect R): the same axes from stream
+    3, the same placement and bit-identical node owners."""
+    params = dict(nx=36, ny=36, nz=36, n_particles=8, radius=4.0, aspect=aspect, noise_amp=0.01)
+    o, s = pair(**params)
+    o.init_from_seed(3)
+    s.init_from_seed(3)
+    a, b = s.export_state(), o.get_state()
+    assert np.array_equal(a["particles"], b["particles"])
+    assert np.array_equal(s.axes(), o.axes())
+    assert np.array_equal(a["owner"], b["owner"])
+    assert np.max(np.abs(a["f"] - b["f"])) < 1e-15
+
+
+@pytest.mark.parametrize("aspect,split", [(1.75, 0), (0.6, 0), (1.75, 1)])
+def test_moving_spheroids_with_events_fp64(aspect, split):
+    """Moving, rotating spheroids: claims with the spheroid inside test and
+    turning axes, cover / uncover on both parities, contact forces along the
+    line of centres, rotation about the angular momentum; owners bit-exact,
+    populations, particle state and axes to the FP64 rounding level."""
+    shape = (30, 28, 32)
+    nx, ny, nz = shape
+    params = dict(nx=nx, ny=ny, nz=nz, n_particles=4, radius=3.5, aspect=aspect, g_br=0.12, color=0.03,
+                  particle_density=3.0)
+    o0 = ref.Oracle(**params)
+    o0.init_from_seed(9)
+    P = o0.get_state()["particles"].copy()
+    E = o0.axes()
+    P[:, 3:6] = [[0.05, -0.03, 0.02], [-0.04, 0.02, 0.03], [0.01, 0.05, -0.04], [0.03, 0.01, 0.04]]
+    P[:, 6:9] = [[0.01, 0.02, -0.01], [0.0, -0.02, 0.015], [0.02, 0.0, 0.01], [-0.01, 0.01, 0.02]]
+    o, s = pair(**params)
+    if split:
+        s.set_tiling(8, 5, 1)
+    o.set_axes(E)
+    s.set_axes(0, E)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=14)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    for k in range(5):
+        o.step(5)
+        s.step(5)
+        compare(o, s, ftol=1e-11, ptol=1e-11)
+        assert np.max(np.abs(s.axes() - o.axes())) < 1e-11
+    ob, sb = o.observe(), s.observables()
+    assert ob["n_cover"] > 0 and ob["n_uncover"] > 0
+    assert (ob["n_cover"], ob["n_uncover"]) == (sb["n_cover"], sb["n_uncover"])
+    assert not np.allclose(s.axes(), E)
+    assert np.allclose(ob["mom_fluid"] + ob["mom_part"], sb["mom_fluid"] + sb["mom_part"], atol=1e-10)
