@@ -60,6 +60,11 @@ def workload_params(name, precision="fp32"):
         # profiling case: the c256 parameters on a 128^3 box (state > L2, ~1 GB)
         return [dict(base, nx=128, ny=128, nz=128, n_particles=-1, volume_fraction=0.20,
                      rho_init=(0.42, 0.28), contact_angle_deg=77.0)], 3
+    if name == "c256s":
+        # the 256^3 fluid with prolate spheroids (semi-axes 4, 4, 6) at a
+        # volume fraction their bounding spheres can be placed at (0.27)
+        return [dict(base, nx=256, ny=256, nz=256, n_particles=-1, volume_fraction=0.12, radius=4.0, aspect=1.5,
+                     rho_init=(0.42, 0.28), contact_angle_deg=77.0)], 3
     if name == "c128":
         return [dict(base, nx=128, ny=128, nz=128, n_particles=-1, volume_fraction=0.15,
                      rho_init=(0.35, 0.35), contact_angle_deg=90.0)], 2
@@ -377,7 +382,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c256", choices=["c256", "c256p", "c128", "c512", "c32", "batch"])
+    ap.add_argument("--workload", default="c256", choices=["c256", "c256p", "c256s", "c128", "c512", "c32", "batch"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sequential", action="store_true", help="batch: skip the one-box-at-a-time comparison")
@@ -392,6 +397,7 @@ def main():
     metric = "MLUPS and % of HBM roofline: FP32 vs BF16/FP16-storage vs batched, same GPU"
     names = {"c256": "256^3 60:40 alpha=0.20 R=5 theta=77deg", "c128": "128^3 50:50 alpha=0.15 R=5 theta=90deg",
              "c256p": "128^3 with the 256^3 parameters (profiling case)",
+             "c256s": "256^3 60:40 alpha=0.12 prolate spheroids 4x4x6 theta=77deg",
              "c512": "512^3 50:50 alpha=0.20 R=5 theta=90deg", "c32": "32^3 16 spheres R=4",
              "batch": "64 boxes {48,64,96,128}^3 theta 60-120 alpha 0.05-0.25 ratio 50:50-70:30"}
 
