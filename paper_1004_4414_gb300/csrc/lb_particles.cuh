@@ -180,8 +180,8 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
     const int b = sh.pbox[p];
     const BoxDev& B = boxes[b];
     const PartStateF pf = sh.partf[p];
-    // spheres: FP32 distances decide away from R^2 and FP64 within a band
-    // of it; spheroids: the FP64 inside test (inside_shape) for every node
+    // FP32 distances (spheres) or quadratic forms (spheroids) decide away
+    // from the surface, the FP64 test (inside_shape) within a band of it
     const bool sph = B.aspect == 1.0;
     const double R = B.rb, R2 = B.radius * B.radius;
     const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
@@ -229,8 +229,22 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
     const int total = span[0] * span[1] * span[2];
     const float Rf2o = (float)((R + 1.5) * (R + 1.5));
     const float R2f = (float)R2;
-    const float band = (float)(0.02 + 2e-3 * R * R);
+    // FP32 positions near L are off by up to about L * 2^-24; the bands below
+    // keep every FP32 decision at least twice that error away from the surface
+    const double eps_pos = 1.2e-7 * (double)max(B.nx, max(B.ny, B.nz));
+    const float band = (float)(0.02 + 2e-3 * R * R + 4.0 * (R + 1.5) * eps_pos);
     const float qlim = (float)(R * R) + band;  // no node beyond this is inside q
+    // spheroid prefilter: F = R^2 (d.e)^2 + c^2 (|d|^2 - (d.e)^2) against
+    // R^2 c^2 in FP32.  |grad F| <= 2 max(R^2, c^2) |d| within the window, so
+    // the position error moves F by at most that times eps_pos; FP32
+    // rounding of F adds a few ulps of R^2 c^2; FP64 decides within sband
+    const double* Ep = sh.part[p].E;
+    const float ex_ = (float)Ep[0], ey_ = (float)Ep[1], ez_ = (float)Ep[2];
+    const double cRd = B.aspect * B.radius;
+    const float cR = (float)cRd;
+    const float R2s = (float)R2, c2s = cR * cR, R2c2 = R2s * c2s;
+    const double gmax = 2.0 * fmax(R2, cRd * cRd) * (R + 1.5);
+    const float sband = (float)(0.05 + 4.0 * gmax * eps_pos + 1e-6 * R2 * cRd * cRd);
     for (int base = 0; base < total; base += 32) {
         const int idx = base + lane;
         int ev_old = 0, ev_new = 0, node = 0;
@@ -256,8 +270,15 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const
                 if (own != OWN_WALL) {
                     double d2p = -1.0;
                     bool inside;
-                    if (sph && fabsf(d2f - R2f) > band) inside = d2f < R2f;
-                    else inside = exact_in(p, d2p);
+                    if (sph) {
+                        if (fabsf(d2f - R2f) > band) inside = d2f < R2f;
+                        else inside = exact_in(p, d2p);
+                    } else {
+                        const float sf = fx * ex_ + fy * ey_ + fz * ez_;
+                        const float Ff = R2s * sf * sf + c2s * (d2f - sf * sf);
+                        if (fabsf(Ff - R2c2) > sband) inside = Ff < R2c2;
+                        else inside = exact_in(p, d2p);
+                    }
                     if (inside || own == p) {
                         bool other = false, anyone = false;
                         const int nk = inside ? ncl : nn;
