@@ -158,6 +158,12 @@ struct lb_handle {
     int* h_err = nullptr;  // pinned mirror of the device error word
     cudaEvent_t err_ev = nullptr;
     bool err_pending = false;
+    // state transfers: copies run on xstream while the conversion kernels run
+    // on the handle's stream; ev_k[b] = conversion of staging half b done,
+    // ev_c[b] = copy of staging half b done
+    cudaStream_t xstream = nullptr;
+    cudaEvent_t ev_k[2] = {nullptr, nullptr}, ev_c[2] = {nullptr, nullptr};
+    std::vector<int> graph_walls;  // the per-box wall flags the graphs were captured with
 };
 
 namespace {
@@ -433,6 +439,7 @@ int build_graphs(lb_handle* h) {
     int rc = capture(h, 0, 6, &h->g6);
     if (rc != LB_OK) return rc;
     h->graphs_ok = true;
+    h->graph_walls = h->has_walls;
     return LB_OK;
 }
 
@@ -588,10 +595,14 @@ int after_init(lb_handle* h, int64_t t) {
     h->t = t;
     h->initialised = true;
     h->err_pending = false;
-    // graphs bake in the per-box wall flags, so they are rebuilt here; the
+    // graphs bake in the per-box wall flags (the wall-shell launches and the
+    // reflection mode), so they are rebuilt only when those changed; the
     // legacy default stream cannot be captured, steps then launch directly
-    destroy_graphs(h);
-    if (h->stream == nullptr) return LB_OK;
+    if (h->stream == nullptr) {
+        destroy_graphs(h);
+        return LB_OK;
+    }
+    if (h->graphs_ok && h->graph_walls == h->has_walls) return LB_OK;
     return build_graphs(h);
 }
 
@@ -649,7 +660,12 @@ int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t
         for (int q = 0; q < h->hbox[b].np; q++) h->axes[b][3 * q + 2] = 1.0;
     }
     if (h->ops->setup() != cudaSuccess || cudaHostAlloc((void**)&h->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->xstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_k[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_k[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_c[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_c[1], cudaEventDisableTiming) != cudaSuccess) {
         lb_destroy(h);
         return LB_ECUDA;
     }
@@ -823,19 +839,28 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
     const int par = (int)(h->t & 1);
     CK(cudaStreamSynchronize(st));
     if (f) {
-        for (int c = 0; c < 2; c++)
-            for (int i = 0; i < 19; i++) {
-                CK(h->ops->export_dir(st, h->d_boxes, box, c, i, par, h->stage));
-                CK(cudaMemcpyAsync(f + ((size_t)c * 19 + i) * B.N, h->stage, sizeof(double) * B.N,
-                                   cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-            }
+        // direction d is converted into staging half d % 2 on the handle's
+        // stream and copied out on xstream, so the conversion of d + 1
+        // overlaps the copy of d
+        for (int d = 0; d < 38; d++) {
+            const int k = d & 1;
+            double* buf = h->stage + (size_t)k * B.N;
+            if (d >= 2) CK(cudaStreamWaitEvent(st, h->ev_c[k], 0));
+            CK(h->ops->export_dir(st, h->d_boxes, box, d / 19, d % 19, par, buf));
+            CK(cudaEventRecord(h->ev_k[k], st));
+            CK(cudaStreamWaitEvent(h->xstream, h->ev_k[k], 0));
+            CK(cudaMemcpyAsync(f + (size_t)d * B.N, buf, sizeof(double) * B.N, cudaMemcpyDeviceToHost, h->xstream));
+            CK(cudaEventRecord(h->ev_c[k], h->xstream));
+        }
+        CK(cudaStreamSynchronize(h->xstream));
+        CK(cudaStreamSynchronize(st));
     }
     if (owner) {
         CK(cudaMemcpyAsync(owner, B.owner, sizeof(int32_t) * B.N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        for (int n = 0; n < B.N; n++)
-            if (owner[n] >= 0) owner[n] -= B.pstart;
+        if (B.pstart != 0)
+            for (int n = 0; n < B.N; n++)
+                if (owner[n] >= 0) owner[n] -= B.pstart;
     }
     if (particles && B.np > 0) {
         std::vector<PartState> ps(B.np);
@@ -894,15 +919,23 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
         k_part_to_float<<<(B.np + 255) / 256, 256, 0, st>>>(h->sh, B.pstart, B.np);
         CK(cudaGetLastError());
     }
-    std::vector<int32_t> own(N);
-    h->has_walls[box] = 0;
-    for (int n = 0; n < N; n++) {
-        const int o = owner[n];
-        if (o >= B.np || o < -2) return LB_EINVAL;
-        own[n] = o >= 0 ? o + B.pstart : o;
-        if (o == OWN_WALL) h->has_walls[box] = 1;
+    {
+        // validated and remapped on the device (scratch after the two
+        // staging halves), then copied into the box only if every entry is valid
+        int32_t* raw = reinterpret_cast<int32_t*>(h->stage + 2 * (size_t)N);
+        int32_t* mapped = raw + N;
+        int* flags = reinterpret_cast<int*>(h->mass_tmp);
+        int fl = 0;
+        CK(cudaMemsetAsync(flags, 0, sizeof(int), st));
+        CK(cudaMemcpyAsync(raw, owner, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+        k_owner_import<<<SMALL_GRID * 4, 256, 0, st>>>(raw, mapped, N, B.np, B.pstart, flags);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&fl, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (fl & 1) return LB_EINVAL;
+        h->has_walls[box] = (fl & 2) ? 1 : 0;
+        CK(cudaMemcpyAsync(B.owner, mapped, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
     }
-    CK(cudaMemcpyAsync(B.owner, own.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     B.mass0[0] = meta[1];
     B.mass0[1] = meta[2];
@@ -913,11 +946,20 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
     k_shell_all<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, box);
     CK(cudaGetLastError());
     const int par = (int)(t & 1), rcs = (int)(t % 3);
-    for (int c = 0; c < 2; c++)
-        for (int i = 0; i < 19; i++) {
-            CK(cudaMemcpyAsync(h->stage, f + ((size_t)c * 19 + i) * N, sizeof(double) * N, cudaMemcpyHostToDevice, st));
-            CK(h->ops->import_dir(st, h->d_boxes, box, c, i, par, h->stage));
-        }
+    // direction d is copied into staging half d % 2 on xstream and converted
+    // on the handle's stream, so the copy of d + 1 overlaps the conversion of d
+    CK(cudaEventRecord(h->ev_k[0], st));  // xstream starts after the work above
+    CK(cudaStreamWaitEvent(h->xstream, h->ev_k[0], 0));
+    for (int d = 0; d < 38; d++) {
+        const int k = d & 1;
+        double* buf = h->stage + (size_t)k * N;
+        if (d >= 2) CK(cudaStreamWaitEvent(h->xstream, h->ev_k[k], 0));
+        CK(cudaMemcpyAsync(buf, f + (size_t)d * N, sizeof(double) * N, cudaMemcpyHostToDevice, h->xstream));
+        CK(cudaEventRecord(h->ev_c[k], h->xstream));
+        CK(cudaStreamWaitEvent(st, h->ev_c[k], 0));
+        CK(h->ops->import_dir(st, h->d_boxes, box, d / 19, d % 19, par, buf));
+        CK(cudaEventRecord(h->ev_k[k], st));
+    }
     for (int k = 0; k < 3; k++) CK(cudaMemsetAsync(B.rho[k], 0, (size_t)2 * N * h->ops->real_size, st));
     CK(cudaMemsetAsync(B.evmark, 0, sizeof(int32_t) * N, st));
     CK(cudaMemsetAsync(h->mass_tmp, 0, 2 * sizeof(double), st));
@@ -1056,6 +1098,14 @@ void lb_destroy(lb_handle* h) {
     destroy_graphs(h);
     for (auto e : h->evpool) cudaEventDestroy(e);
     if (h->err_ev) cudaEventDestroy(h->err_ev);
+    if (h->xstream) {
+        cudaStreamSynchronize(h->xstream);
+        cudaStreamDestroy(h->xstream);
+    }
+    for (int b = 0; b < 2; b++) {
+        if (h->ev_k[b]) cudaEventDestroy(h->ev_k[b]);
+        if (h->ev_c[b]) cudaEventDestroy(h->ev_c[b]);
+    }
     if (h->h_err) cudaFreeHost(h->h_err);
     delete h;
 }

@@ -68,6 +68,23 @@ static __global__ void k_shell_all(const BoxDev* __restrict__ boxes, int b) {
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) shell_update(B, n);
 }
 
+// Owner map of one box from the caller (box-local particle indices) into
+// global indices in out; bit 1 of *flags: an entry outside [-2, np), bit 2:
+// a static wall node.
+static __global__ void k_owner_import(const int32_t* __restrict__ in, int32_t* __restrict__ out, int N, int np,
+                                      int pstart, int* flags) {
+    int bad = 0, wall = 0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const int o = in[n];
+        if (o >= np || o < -2) bad = 1;
+        if (o == OWN_WALL) wall = 1;
+        out[n] = o >= 0 ? o + pstart : o;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    wall = __any_sync(0xffffffffu, wall);
+    if ((threadIdx.x & 31) == 0 && (bad | wall)) atomicOr(flags, bad | (wall << 1));
+}
+
 // owner map given by the caller (global particle indices already applied)
 static __global__ void k_flags_from_owner(const BoxDev* __restrict__ boxes, int b) {
     const BoxDev& B = boxes[b];
