@@ -426,6 +426,11 @@ def test_spheroid_seeded_init_matches_oracle(aspect):
     a, b = s.export_state(), o.get_state()
     assert np.array_equal(a["particles"], b["particles"])
     assert np.array_equal(s.axes(), o.axes())
+    bad = s.axes().copy()
+    bad[0] *= 1.01  # not a unit vector: rejected, axes unchanged
+    with pytest.raises(Exception):
+        s.set_axes(0, bad)
+    assert np.array_equal(s.axes(), o.axes())
     assert np.array_equal(a["owner"], b["owner"])
     assert np.max(np.abs(a["f"] - b["f"])) < 1e-15
 
