@@ -247,6 +247,7 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     }
     sh.shell_list = cv.take<int4>((size_t)NPa * sh.shell_cap);
     sh.shell_n = cv.take<int>(NPa);
+    sh.shell_dirty = cv.take<int>(NPa);
     sh.err = cv.take<int>(1);
     sh.counters = cv.take<unsigned long long>((size_t)nb * 2);
     BoxDev* d_boxes = cv.take<BoxDev>(nb);
@@ -595,6 +596,11 @@ int after_init(lb_handle* h, int64_t t) {
     h->t = t;
     h->initialised = true;
     h->err_pending = false;
+    // every shell list is rebuilt at the first step of a new state
+    if (h->NP > 0) {
+        CK(cudaMemsetAsync(h->sh.shell_dirty, 1, sizeof(int) * h->NP, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
     // graphs bake in the per-box wall flags (the wall-shell launches and the
     // reflection mode), so they are rebuilt only when those changed; the
     // legacy default stream cannot be captured, steps then launch directly

@@ -119,6 +119,7 @@ struct Shared {
     int4* shell_list;           // [NP][shell_cap] shell nodes of each particle (this step):
                                 // (node, mask of fluid neighbours, x | y << 16, z)
     int* shell_n;               // [NP]
+    int* shell_dirty;           // [NP] nonzero: rebuild the shell list (events nearby, or a new state)
     int shell_cap;
     int* err;                   // [1] sticky error bits
     unsigned long long* counters; // [n_boxes][2] n_cover, n_uncover

@@ -500,6 +500,16 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
             rcur[(size_t)B.N + w] = (R)sh.ev_rho[(size_t)e * 2 + 1];
         }
         B.evmark[w] = 0;
+        // the particles whose shell lists this event can change: the old and
+        // new owner of w and the owners of its solid neighbours (their
+        // fluid-neighbour masks)
+        if (ev.z >= 0) sh.shell_dirty[ev.z] = 1;
+        if (ev.w >= 0) sh.shell_dirty[ev.w] = 1;
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            const int o = B.owner[nbr_index(B, w, cx(i), cy(i), cz(i))];
+            if (o >= 0) sh.shell_dirty[o] = 1;
+        }
         // A solid node left without fluid neighbours takes density 0: the
         // fused step may have counted reflected populations in it while it
         // was a shell node, and no later pass rewrites it (the particle's
@@ -553,6 +563,38 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     const int total = span[0] * span[1] * span[2];
     const int scap = sh.shell_cap;
     int4* __restrict__ slist = sh.shell_list + (size_t)p * scap;
+    if (!sh.shell_dirty[p]) {
+        // No event near p since its list was built: the shell nodes and
+        // their fluid-neighbour masks are unchanged, only the densities are
+        // new (the whole warp takes this branch together).
+        const int ns = sh.shell_n[p];
+        const int nxy = nx * ny;
+        for (int k = lane; k < ns; k += 32) {
+            const int4 e = slist[k];
+            const int n = e.x;
+            const unsigned fmask = (unsigned)e.y;
+            const int gx = e.z & 0xffff, gy = (int)((unsigned)e.z >> 16), gz = e.w;
+            const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
+            const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
+            const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
+            R s0 = R(0), s1 = R(0);
+#pragma unroll
+            for (int i = 1; i < 19; i++) {
+                if (!((fmask >> i) & 1u)) continue;
+                const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) +
+                              (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) + (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
+                s0 += rcur[m];
+                s1 += rcur[N + m];
+            }
+            const R cnt = (R)__popc(fmask);
+            R r0 = s0 / cnt, r1 = s1 / cnt;
+            if (col > R(0)) r0 += col;
+            else if (col < R(0)) r1 -= col;
+            rcur[n] = r0;
+            rcur[N + n] = r1;
+        }
+        return;
+    }
     // virtual density of one shell node n of p, and its entry k of p's
     // shell list (node, mask of fluid neighbours, coordinates)
     const int nxy = nx * ny;
@@ -629,6 +671,7 @@ static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __re
     if (lane == 0) {
         sh.shell_n[p] = done < scap ? done : scap;
         if (done > scap) set_err(sh.err, ERR_OVERFLOW);
+        else sh.shell_dirty[p] = 0;
     }
 }
 
