@@ -170,7 +170,7 @@ static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev*
 // plain sequential evaluation, decides.  FP64 is slow on this GPU, so it is
 // kept off the common path.
 constexpr int DETECT_WARPS = 4;
-static __global__ void __launch_bounds__(32 * DETECT_WARPS) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     __shared__ float s_rq[DETECT_WARPS][NL_MAX][3];  // X_q - X_p, minimum image
     __shared__ int s_nid[DETECT_WARPS][NL_MAX];
     __shared__ int s_cl[DETECT_WARPS][NL_MAX];  // entries of neighbours within 2R (+ slack)
