@@ -531,7 +531,7 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
 // Shell nodes get the mean density of their fluid neighbours plus the
 // particle colour on red (Delta rho > 0) or blue (Delta rho < 0) (Sec. IV).
 template <class R>
-static __global__ void __launch_bounds__(128) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh, int rc, int NP) {
+static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh, int rc, int NP) {
     __shared__ int s_q[4][64];
     __shared__ int s_qc[4][64];  // x | y << 16 of the queued node
     __shared__ int s_qz[4][64];  // z of the queued node
