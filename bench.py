@@ -376,6 +376,35 @@ def oracle_sample(workload, budget_s=12.0):
                        (steps, workload, p["nx"], o.np))
 
 
+def oracle_steps(workload, steps, warmup, edge=64):
+    """Reference arm: the FP64 oracle on the host cores, W untimed and K
+    timed steps, each step one oracle step of a bounded sample of the
+    workload: a box of at most edge^3 nodes with the parameters of its first
+    box (same volume fraction, radius, densities and wetting, so the
+    particle count scales with the volume)."""
+    from oracle import ref
+
+    boxes, seed = workload_params(workload, "fp64")
+    p = {k: v for k, v in boxes[0].items() if k not in ("precision", "contact_angle_deg")}
+    theta = boxes[0].get("contact_angle_deg", 90.0)
+    p["color"] = (theta - 90.0) / 442.0 if theta is not None and not math.isnan(theta) else 0.0
+    full = (p["nx"], p["ny"], p["nz"])
+    for k in ("nx", "ny", "nz"):
+        p[k] = min(p[k], edge)
+    o = ref.Oracle(**p)
+    o.init_from_seed(seed)
+    o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    spent = time.perf_counter() - t0
+    N = p["nx"] * p["ny"] * p["nz"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=N * steps / spent / 1e6, steps=steps, seconds=spent, cores=cores, N=N,
+                sample="%d timed step(s) after %d warm-up step(s) of a %dx%dx%d box with the parameters of box 0 "
+                       "of %s (%dx%dx%d; %d particles in the sample)" %
+                       (steps, warmup, p["nx"], p["ny"], p["nz"], workload, full[0], full[1], full[2], o.np))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,7 +433,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        r = oracle_sample(args.workload)
+        r = oracle_steps(args.workload, args.steps, args.warmup)
         line = {"impl": "reference", "metric": metric, "value": r["value"], "unit": "MLUPS", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["seconds"] / r["steps"] * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
