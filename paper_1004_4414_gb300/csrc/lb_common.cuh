@@ -88,7 +88,6 @@ struct BoxDev {
     int nc[3];                  // cells per axis
     int cell_off;               // offset into the global cell arrays
     double cell_len[3];
-    uint8_t* vf_dummy;
 };
 
 struct TileDev {                // one CTA work item of the fused step kernel

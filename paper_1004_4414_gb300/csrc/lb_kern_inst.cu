@@ -76,11 +76,6 @@ cudaError_t setup() {
     return cudaSuccess;
 }
 
-size_t step_smem(int ty, int split) {
-    if (split) return ty == 8 ? SplitSmem<RR, 8>::bytes : SplitSmem<RR, 16>::bytes;
-    return ty == 4 ? StepSmem<RR, 4>::bytes : (ty == 8 ? StepSmem<RR, 8>::bytes : StepSmem<RR, 16>::bytes);
-}
-
 template <bool T1, bool BB>
 cudaError_t step_tau(int par, int ty, int split, int ntiles, cudaStream_t st, const BoxDev* boxes,
                      const TileDev* tiles, Shared sh, int rc, int rn, int rz, int mslot) {
@@ -170,7 +165,7 @@ cudaError_t obs_partial(cudaStream_t st, const BoxDev* boxes, int b, int par, do
 }
 }  // namespace
 
-const LbOps OPS_NAME = {PP::id,       sizeof(RR),   setup,         step_smem,  step,       remap_apply, remap_finish,
+const LbOps OPS_NAME = {PP::id,       sizeof(RR),   setup,         step,       remap_apply, remap_finish,
                         shell_density, couple,     wall_shell,     init_pop,   export_dir, import_dir,   rho_from_pop,
                         obs_partial};
 

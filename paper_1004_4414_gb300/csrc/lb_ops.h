@@ -10,7 +10,6 @@ struct LbOps {
     int id;
     size_t real_size;
     cudaError_t (*setup)();
-    size_t (*step_smem)(int ty, int split);
     // fused kernel: split = 0 k_step (32 x ty tiles), 1 k_step_split (16 x ty, ty 8 or 16);
     // reflect = 1: the fused kernel reflects at solid neighbours itself, 0: k_couple does
     cudaError_t (*step)(int par, int ty, int split, int tau1, int reflect, int ntiles, cudaStream_t st,
