@@ -469,3 +469,31 @@ def test_moving_spheroids_with_events_fp64(aspect, split):
     assert (ob["n_cover"], ob["n_uncover"]) == (sb["n_cover"], sb["n_uncover"])
     assert not np.allclose(s.axes(), E)
     assert np.allclose(ob["mom_fluid"] + ob["mom_part"], sb["mom_fluid"] + sb["mom_part"], atol=1e-10)
+
+
+def test_overlapping_spheroids_fp64():
+    """Two overlapping spheroids moving apart: the initial claims (nearest
+    centre among the spheroids a node lies in), then claims in the remap
+    with the close-neighbour list, against the oracle bit for bit."""
+    L = 24
+    P = np.zeros((2, 9))
+    P[0, :3] = (10.3, 11.6, 12.2)
+    P[1, :3] = (14.1, 12.4, 11.7)
+    P[0, 3:6] = (-0.04, -0.01, 0.02)
+    P[1, 3:6] = (0.05, 0.02, -0.01)
+    E = np.array([[0.98, 0.196, 0.098], [-0.28, 0.93, 0.24]])
+    E /= np.linalg.norm(E, axis=1, keepdims=True)
+    params = dict(nx=L, ny=L, nz=L, n_particles=2, radius=4.0, aspect=1.75, g_br=0.1, color=0.02,
+                  particle_density=3.0, k_hertz=20.0)
+    o, s = pair(**params)
+    o.set_axes(E)
+    s.set_axes(0, E)
+    rho = lbinputs.mixture((L, L, L), amp=0.05, seed=21)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    compare(o, s)
+    for k in range(4):
+        o.step(4)
+        s.step(4)
+        compare(o, s, ftol=1e-11, ptol=1e-11)
+    assert o.observe()["n_uncover"] > 0

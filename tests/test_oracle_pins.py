@@ -764,3 +764,34 @@ def test_spheroid_momentum_conserved_in_fluid():
     p1 = ob["mom_fluid"] + ob["mom_part"]
     assert np.all(np.abs(p1 - p0) < 1e-12 * (ob["mass"].sum() + 1)), p1 - p0
     assert not np.allclose(o2.axes(), E)
+
+
+def test_overlapping_spheroids_claims_brute_force():
+    """Two overlapping spheroids (reading #12 with the spheroid inside test):
+    a node inside either is solid, and a node inside both goes to the nearer
+    centre (the lower index on a tie); checked against a brute-force loop."""
+    L = 24
+    P = np.zeros((2, 9))
+    P[0, :3] = (10.3, 11.6, 12.2)
+    P[1, :3] = (14.1, 12.4, 11.7)
+    E = np.array([_unit([1.0, 0.2, 0.1]), _unit([-0.3, 1.0, 0.4])])
+    o = ref.Oracle(nx=L, ny=L, nz=L, n_particles=2, g_br=0.0, fixed_particles=1, **SPH)
+    o.set_axes(E)
+    o.init_fields(np.full((2, L ** 3), 0.5), particles=P)
+    own = o.get_state()["owner"].reshape(L, L, L)
+    both = 0
+    for z in range(L):
+        for y in range(L):
+            for x in range(L):
+                best, bd = -1, None
+                for q in range(2):
+                    d = np.array([x, y, z], float) - P[q, :3]
+                    d -= L * np.round(d / L)
+                    if ref.inside(d, E[q], **SPH):
+                        d2 = float(np.dot(d, d))
+                        if best >= 0:
+                            both += 1
+                        if bd is None or d2 < bd:
+                            best, bd = q, d2
+                assert own[z, y, x] == best, (x, y, z, own[z, y, x], best)
+    assert both > 20
