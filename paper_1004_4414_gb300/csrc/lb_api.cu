@@ -899,6 +899,23 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
     if (h->nb > 1 && h->initialised && t != h->t) return LB_EINVAL;
     cudaStream_t st = h->stream;
     const int N = B.N;
+    {
+        // validated and remapped on the device (scratch after the two
+        // staging halves) before anything of the box changes; copied into the
+        // box below, after the particles
+        int32_t* raw = reinterpret_cast<int32_t*>(h->stage + 2 * (size_t)N);
+        int32_t* mapped = raw + N;
+        int* flags = reinterpret_cast<int*>(h->mass_tmp);
+        int fl = 0;
+        CK(cudaMemsetAsync(flags, 0, sizeof(int), st));
+        CK(cudaMemcpyAsync(raw, owner, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+        k_owner_import<<<SMALL_GRID * 4, 256, 0, st>>>(raw, mapped, N, B.np, B.pstart, flags);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&fl, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (fl & 1) return LB_EINVAL;
+        h->has_walls[box] = (fl & 2) ? 1 : 0;
+    }
     if (B.np > 0) {
         std::vector<PartState> ps(B.np);
         std::vector<int> pb(B.np, box);
@@ -925,23 +942,8 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
         k_part_to_float<<<(B.np + 255) / 256, 256, 0, st>>>(h->sh, B.pstart, B.np);
         CK(cudaGetLastError());
     }
-    {
-        // validated and remapped on the device (scratch after the two
-        // staging halves), then copied into the box only if every entry is valid
-        int32_t* raw = reinterpret_cast<int32_t*>(h->stage + 2 * (size_t)N);
-        int32_t* mapped = raw + N;
-        int* flags = reinterpret_cast<int*>(h->mass_tmp);
-        int fl = 0;
-        CK(cudaMemsetAsync(flags, 0, sizeof(int), st));
-        CK(cudaMemcpyAsync(raw, owner, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
-        k_owner_import<<<SMALL_GRID * 4, 256, 0, st>>>(raw, mapped, N, B.np, B.pstart, flags);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(&fl, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (fl & 1) return LB_EINVAL;
-        h->has_walls[box] = (fl & 2) ? 1 : 0;
-        CK(cudaMemcpyAsync(B.owner, mapped, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
-    }
+    CK(cudaMemcpyAsync(B.owner, reinterpret_cast<int32_t*>(h->stage + 2 * (size_t)N) + N, sizeof(int32_t) * N,
+                       cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     B.mass0[0] = meta[1];
     B.mass0[1] = meta[2];

@@ -497,3 +497,24 @@ def test_overlapping_spheroids_fp64():
         s.step(4)
         compare(o, s, ftol=1e-11, ptol=1e-11)
     assert o.observe()["n_uncover"] > 0
+
+
+def test_import_rejects_invalid_owner_without_changes():
+    """lb_import_state with an owner entry outside [-2, n_particles) returns
+    LB_EINVAL before any part of the box changes."""
+    shape = (16, 12, 10)
+    nx, ny, nz = shape
+    P = lbinputs.spheres(shape, 2.5, 2, seed=5, min_gap=1.0, vmax=0.02)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=2, radius=2.5, g_br=0.1)
+    rho = lbinputs.mixture(shape, amp=0.05, seed=6)
+    s.init_fields(0, rho, particles=P)
+    s.step(3)
+    before = s.export_state(0)
+    bad = dict(before, owner=before["owner"].copy(), particles=before["particles"] + 0.5)
+    bad["owner"][7] = 5  # no particle 5 in this box
+    with pytest.raises(Exception):
+        s.import_state(0, bad)
+    after = s.export_state(0)
+    assert np.array_equal(after["owner"], before["owner"])
+    assert np.array_equal(after["particles"], before["particles"])
+    assert np.array_equal(after["f"], before["f"])
