@@ -472,31 +472,50 @@ def test_moving_spheroids_with_events_fp64(aspect, split):
 
 
 def test_overlapping_spheroids_fp64():
-    """Two overlapping spheroids moving apart: the initial claims (nearest
-    centre among the spheroids a node lies in), then claims in the remap
-    with the close-neighbour list, against the oracle bit for bit."""
+    """Overlapping spheroids against the oracle, bit for bit on the owners:
+    (a) deep overlap, particles held fixed: the initial claims (nearest
+    centre among the spheroids a node lies in) and the remap's claims with
+    the close-neighbour list; (b) a shallow overlap (0.5 along the line of
+    centres, soft contact) moving apart, so nodes change hands."""
     L = 24
+    E = np.array([[1.0, 0.2, 0.1], [-0.3, 1.0, 0.4]])
+    E /= np.linalg.norm(E, axis=1, keepdims=True)
+    base = dict(nx=L, ny=L, nz=L, n_particles=2, radius=4.0, aspect=1.75, g_br=0.1, color=0.02,
+                particle_density=3.0)
+    rho = lbinputs.mixture((L, L, L), amp=0.05, seed=21)
+    # (a) deep overlap, fixed
     P = np.zeros((2, 9))
     P[0, :3] = (10.3, 11.6, 12.2)
     P[1, :3] = (14.1, 12.4, 11.7)
-    P[0, 3:6] = (-0.04, -0.01, 0.02)
-    P[1, 3:6] = (0.05, 0.02, -0.01)
-    E = np.array([[0.98, 0.196, 0.098], [-0.28, 0.93, 0.24]])
-    E /= np.linalg.norm(E, axis=1, keepdims=True)
-    params = dict(nx=L, ny=L, nz=L, n_particles=2, radius=4.0, aspect=1.75, g_br=0.1, color=0.02,
-                  particle_density=3.0, k_hertz=20.0)
-    o, s = pair(**params)
+    o, s = pair(**base, fixed_particles=1)
     o.set_axes(E)
     s.set_axes(0, E)
-    rho = lbinputs.mixture((L, L, L), amp=0.05, seed=21)
     o.init_fields(rho, particles=P)
     s.init_fields(0, rho, particles=P)
     compare(o, s)
+    o.step(4)
+    s.step(4)
+    compare(o, s, ftol=1e-11, ptol=1e-11)
+    # (b) shallow overlap along r_hat (contact distance 10.76 for these axes), moving apart
+    rh = np.array([1.0, 0.2, -0.1]) / np.linalg.norm([1.0, 0.2, -0.1])
+    P = np.zeros((2, 9))
+    P[0, :3] = (6.3, 11.6, 12.2)
+    P[1, :3] = P[0, :3] + 10.26 * rh
+    P[0, 3:6] = -0.02 * rh
+    P[1, 3:6] = 0.02 * rh
+    P[1, 6:9] = (0.0, 0.01, 0.005)
+    o, s = pair(**base, k_hertz=1.0)
+    o.set_axes(E)
+    s.set_axes(0, E)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
     for k in range(4):
-        o.step(4)
-        s.step(4)
+        o.step(5)
+        s.step(5)
         compare(o, s, ftol=1e-11, ptol=1e-11)
-    assert o.observe()["n_uncover"] > 0
+        assert np.max(np.abs(s.axes() - o.axes())) < 1e-11
+    ob = o.observe()
+    assert ob["n_uncover"] > 0 and ob["n_cover"] > 0
 
 
 def test_import_rejects_invalid_owner_without_changes():
