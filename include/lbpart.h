@@ -120,8 +120,9 @@ int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t
               void* cuda_stream, lb_handle** out);
 
 /* Seeded synthetic initial state of every box (box b uses seed + b):
- * spheres by random sequential addition (minimum-image centre distance
- * >= 2R, at most 10^6 candidates, LB_EPLACE otherwise), node densities
+ * particles by random sequential addition (minimum-image centre distance
+ * >= 2R, for spheroids twice the bounding radius; at most 10^6 candidates,
+ * LB_EPLACE otherwise; spheroid axes from stream 3), node densities
  * rho_init^c + U(-a, a), f = f^eq(rho, 0) on fluid nodes.  The random
  * numbers come from SplitMix64 (Steele, Lea & Flood 2014): stream k of seed
  * s is seeded with output k of SplitMix64(s); stream 0 places spheres
@@ -132,7 +133,8 @@ int lb_init_from_seed(lb_handle* h, uint64_t seed);
 /* Initial state of one box from macroscopic fields (host arrays):
  * rho[2][N], u[3][N] (NULL: fluid at rest), particles[n_particles][9],
  * walls[N] (NULL: none; -2 marks a static wall node).  f = f^eq(rho, u) on
- * fluid nodes; nodes within R of a centre are solid.  Synchronous. */
+ * fluid nodes; nodes inside a particle (within R of a sphere's centre, or
+ * inside a spheroid with the axes of lb_set_axes) are solid.  Synchronous. */
 int lb_init_fields(lb_handle* h, int32_t box, const double* rho, const double* u,
                    const double* particles, const int32_t* walls);
 
@@ -155,7 +157,12 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
                     double* meta);
 
 /* Replace the state of one box (same layout as lb_export_state; f, owner,
- * particles and meta are required).  Synchronous. */
+ * particles and meta are required).  An owner entry outside [-2,
+ * n_particles) returns LB_EINVAL before anything of the box changes.
+ * Spheroid axes are not part of this format: a box that was stepped keeps
+ * its current axes, otherwise those of the last lb_set_axes.  Host-device
+ * copies overlap the per-direction conversion (two staging halves, a second
+ * stream).  Synchronous. */
 int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* owner,
                     const double* particles, const double* meta);
 
