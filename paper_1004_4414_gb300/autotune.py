@@ -6,7 +6,7 @@ component with ty rows of 16 nodes (8 or 16); cz z-planes are marched per
 CTA.  Each candidate is timed with CUDA events around
 the fused kernel over a few steps of the real boxes (the simulation
 advances while tuning, so run it as part of the warm-up), and the fastest
-is kept.  Results are cached per (box sizes, precision) in memory.
+is kept.  Results are cached per (box sizes, precision, tau) in memory.
 """
 _CACHE = {}
 
@@ -15,7 +15,9 @@ DEFAULT_CANDIDATES = ((4, 16, 0), (4, 32, 0), (4, 64, 0), (8, 16, 0), (8, 32, 0)
 
 
 def _key(sim):
-    return (tuple(sim.dims), tuple(p.precision for p in sim._params))
+    # box sizes, storage and relaxation times (tau = 1 selects a specialised kernel)
+    return (tuple(sim.dims), tuple(p.precision for p in sim._params),
+            tuple((p.tau[0], p.tau[1]) for p in sim._params))
 
 
 def autotune(sim, candidates=DEFAULT_CANDIDATES, steps=4, use_cache=True):

@@ -1,0 +1,85 @@
+"""Host-side logic that needs no GPU: the autotuner's candidate filtering,
+selection and cache, run against a stand-in for the simulation whose fused
+kernel times are given."""
+from types import SimpleNamespace
+
+import pytest
+
+from paper_1004_4414_gb300 import autotune as at
+
+
+class FakeSim:
+    """Records the calls the autotuner makes; kernel_time returns the time
+    assigned to the tiling that was set last."""
+
+    def __init__(self, dims, times, precision=1, tau=(1.0, 1.0)):
+        self.dims = list(dims)
+        self._params = [SimpleNamespace(precision=precision, tau=tau) for _ in dims]
+        self.times = times
+        self.tiling = None
+        self.steps = 0
+        self.profiling = False
+        self.timed = []
+
+    def set_tiling(self, ty, cz, split=0):
+        self.tiling = (ty, cz, split)
+
+    def step(self, n=1):
+        self.steps += n
+
+    def sync(self):
+        pass
+
+    def set_profiling(self, on):
+        self.profiling = on
+
+    def kernel_time(self):
+        self.timed.append(self.tiling)
+        return self.times.get(self.tiling, 9.0) * 4, 4, 60
+
+
+@pytest.fixture(autouse=True)
+def clear_cache():
+    at._CACHE.clear()
+    yield
+    at._CACHE.clear()
+
+
+def test_picks_the_fastest_candidate_and_leaves_it_set():
+    times = {c: 2.0 for c in at.DEFAULT_CANDIDATES}
+    times[(16, 32, 1)] = 1.1
+    sim = FakeSim([(256, 256, 256)], times)
+    best, table = at.autotune(sim)
+    assert best == (16, 32, 1) and sim.tiling == best
+    assert table[best] == pytest.approx(1.1)
+    assert set(table) == set(at.DEFAULT_CANDIDATES)
+    assert not sim.profiling
+
+
+def test_candidates_deeper_than_the_box_are_skipped():
+    sim = FakeSim([(64, 64, 20)], {})
+    _, table = at.autotune(sim)
+    assert all(cz <= 20 or cz == at.DEFAULT_CANDIDATES[0][1] for _, cz, _ in table)
+    assert (8, 32, 0) not in table and (4, 16, 0) in table
+
+
+def test_cache_is_keyed_by_sizes_precision_and_tau():
+    times = {c: 2.0 for c in at.DEFAULT_CANDIDATES}
+    times[(8, 16, 1)] = 1.0
+    a = FakeSim([(128, 128, 128)], times)
+    at.autotune(a)
+    b = FakeSim([(128, 128, 128)], {})
+    best, _ = at.autotune(b)
+    assert best == (8, 16, 1) and b.timed == [] and b.tiling == best
+    c = FakeSim([(128, 128, 128)], {}, tau=(1.0, 0.8))
+    at.autotune(c)
+    assert c.timed  # a different tau is tuned again
+    d = FakeSim([(128, 128, 128)], {}, precision=2)
+    at.autotune(d)
+    assert d.timed
+
+
+def test_two_element_candidates_default_to_one_thread_per_node():
+    sim = FakeSim([(64, 64, 64)], {(8, 16, 0): 1.0, (4, 16, 0): 2.0})
+    best, _ = at.autotune(sim, candidates=((4, 16), (8, 16)))
+    assert best == (8, 16, 0)
