@@ -380,8 +380,8 @@ def oracle_steps(workload, steps, warmup, edge=64):
     """Reference arm: the FP64 oracle on the host cores, W untimed and K
     timed steps, each step one oracle step of a bounded sample of the
     workload: a box of at most edge^3 nodes with the parameters of its first
-    box (same volume fraction, radius, densities and wetting, so the
-    particle count scales with the volume)."""
+    box (same volume fraction, radius, densities and wetting; the particle
+    count scales with the volume)."""
     from oracle import ref
 
     boxes, seed = workload_params(workload, "fp64")
@@ -391,6 +391,9 @@ def oracle_steps(workload, steps, warmup, edge=64):
     full = (p["nx"], p["ny"], p["nz"])
     for k in ("nx", "ny", "nz"):
         p[k] = min(p[k], edge)
+    if p.get("n_particles", -1) >= 0:  # an explicit count scales with the volume
+        frac = p["nx"] * p["ny"] * p["nz"] / float(full[0] * full[1] * full[2])
+        p["n_particles"] = int(round(p["n_particles"] * frac))
     o = ref.Oracle(**p)
     o.init_from_seed(seed)
     o.step(warmup)

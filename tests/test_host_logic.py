@@ -83,3 +83,27 @@ def test_two_element_candidates_default_to_one_thread_per_node():
     sim = FakeSim([(64, 64, 64)], {(8, 16, 0): 1.0, (4, 16, 0): 2.0})
     best, _ = at.autotune(sim, candidates=((4, 16), (8, 16)))
     assert best == (8, 16, 0)
+
+
+def test_traffic_is_used_only_for_the_same_kernel_and_sources(tmp_path, monkeypatch):
+    import json
+
+    import bench
+
+    entry = {"kernel_hash": bench.kernel_hash(), "dram_bytes_per_launch": 123.0}
+    (tmp_path / "traffic.json").write_text(json.dumps({"c256_fp32_k_step_split": entry}))
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    assert bench.ncu_traffic("c256", "fp32", 1) == 123.0
+    assert bench.ncu_traffic("c256", "fp32", 0) is None  # the other fused kernel
+    assert bench.ncu_traffic("c256", "fp16", 1) is None
+    stale = dict(entry, kernel_hash="0" * 16)
+    (tmp_path / "traffic.json").write_text(json.dumps({"c256_fp32_k_step_split": stale}))
+    assert bench.ncu_traffic("c256", "fp32", 1) is None
+
+
+def test_reference_arm_times_a_bounded_sample():
+    import bench
+
+    r = bench.oracle_steps("c32", steps=2, warmup=1, edge=16)
+    assert r["steps"] == 2 and r["N"] == 16 ** 3 and r["value"] > 0
+    assert "16x16x16" in r["sample"] and "32x32x32" in r["sample"]
