@@ -60,10 +60,23 @@ def test_invalid_parameters_rejected(lib):
 
     n = C.c_size_t(0)
     for bad in (dict(nx=0), dict(tau=(0.5, 1.0)), dict(precision=7), dict(reserved=1), dict(radius=0.0),
-                dict(rho_init=(0.0, 0.7)), dict(lub_min=0.0), dict(lub_cut=0.1, lub_min=0.1)):
+                dict(rho_init=(0.0, 0.7)), dict(lub_min=0.0), dict(lub_cut=0.1, lub_min=0.1),
+                dict(aspect=0.05), dict(aspect=11.0), dict(aspect=-1.0), dict(aspect=float("nan"))):
         p = binding.make_params(**bad)
         arr = (binding.LbParams * 1)(p)
         assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_EINVAL
+    # spheres (aspect 0 or 1) and spheroids within [0.1, 10] are accepted
+    for good in (dict(aspect=0.0), dict(aspect=1.0), dict(aspect=0.1), dict(aspect=10.0), dict(aspect=1.75)):
+        arr = (binding.LbParams * 1)(binding.make_params(**good))
+        assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_OK
+    # a prolate spheroid needs a larger workspace than the sphere of its
+    # equatorial radius (bounding-radius shell lists and event buffers)
+    ws = []
+    for a in (1.0, 2.0):
+        arr = (binding.LbParams * 1)(binding.make_params(nx=64, ny=64, nz=64, n_particles=20, radius=4.0, aspect=a))
+        assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_OK
+        ws.append(n.value)
+    assert ws[1] > ws[0]
     # mixed precisions in one batch are rejected
     arr = (binding.LbParams * 2)(binding.make_params(precision="fp32"), binding.make_params(precision="fp16"))
     assert lib.lb_workspace_bytes(arr, 2, C.byref(n)) == binding.LB_EINVAL
