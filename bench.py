@@ -195,10 +195,11 @@ def gpu_id(device):
 
 def fused_bytes(sim, precision):
     """Algorithmic bytes of one launch of the fused kernel: every fluid node
-    reads and writes 2 x 19 populations (FP32: 4 B each; 16-bit deviation
-    storage: 18 x 2 B + a 4 B rest slot per component), every node reads and
-    writes 2 densities (4 B each) and reads 1 flag byte."""
-    pop = {"fp32": 2 * 19 * 4, "fp64": 2 * 19 * 8, "fp16": 2 * (18 * 2 + 4), "bf16": 2 * (18 * 2 + 4)}[precision]
+    reads and writes its 2 x 18 moving populations (FP32: 4 B each; 16-bit
+    deviation storage: 2 B; the rest population is the density minus them
+    and is not stored), every node reads and writes 2 densities (4 B each,
+    8 B in FP64) and reads 1 flag byte."""
+    pop = {"fp32": 2 * 18 * 4, "fp64": 2 * 18 * 8, "fp16": 2 * 18 * 2, "bf16": 2 * 18 * 2}[precision]
     rs = 8 if precision == "fp64" else 4
     total = 0
     for b in range(sim.nb):

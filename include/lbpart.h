@@ -59,7 +59,7 @@ extern "C" {
 /* population storage (the collision always runs in FP32, or FP64 for LB_FP64) */
 #define LB_FP64 0      /* FP64 populations and arithmetic (parity mode) */
 #define LB_FP32 1      /* FP32 populations and arithmetic */
-#define LB_FP16_DEV 2  /* f_i (i>0) stored as FP16 deviations (f_i - zeta_i rho_ref)/zeta_i, rest population FP32 */
+#define LB_FP16_DEV 2  /* f_i (i>0) stored as FP16 deviations (f_i - zeta_i rho_ref)/zeta_i, density FP32 */
 #define LB_BF16_DEV 3  /* as LB_FP16_DEV with BF16 */
 
 /* One periodic box.  Densities follow the paper's symbols. */
@@ -93,7 +93,7 @@ typedef struct {
 /* Observables of one box (lb_observables). */
 typedef struct {
     int64_t step;                /* time steps taken since init */
-    double mass[2];              /* sum of populations over fluid nodes, per component */
+    double mass[2];              /* sum of the densities rho^c over fluid nodes, per component */
     double mom_fluid[3];         /* sum over fluid nodes of sum_c sum_i f_i c_i */
     double mom_part[3];          /* sum over particles of m U (0 when particles are fixed) */
     double max_u;                /* max over fluid nodes of |j| / rho (both components) */
@@ -152,12 +152,16 @@ int lb_observables(lb_handle* h, int32_t box, lb_obs* out);
 /* Full state of one box in canonical order (host arrays, any may be NULL):
  * f[2][19][N] FP64 (0 on solid nodes), owner[N], particles[np][9],
  * meta[4] = {step, initial mass red, initial mass blue, n_particles}.
+ * The device keeps each fluid node's density rho^c and its 18 moving
+ * populations; the exported rest population is rho^c - sum_{i>0} f_i
+ * (so after lb_import_state it returns to within rounding).
  * Synchronises the stream. */
 int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double* particles,
                     double* meta);
 
 /* Replace the state of one box (same layout as lb_export_state; f, owner,
- * particles and meta are required).  An owner entry outside [-2,
+ * particles and meta are required).  Each fluid node's density becomes the
+ * sum of its 19 imported populations.  An owner entry outside [-2,
  * n_particles) returns LB_EINVAL before anything of the box changes.
  * Spheroid axes are not part of this format: a box that was stepped keeps
  * its current axes, otherwise those of the last lb_set_axes.  Host-device
@@ -166,7 +170,8 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
 int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* owner,
                     const double* particles, const double* meta);
 
-/* Densities rho[2][N] of one box (sum of populations, 0 on solid nodes). */
+/* Densities rho[2][N] of one box (rho^c = sum of the populations on fluid
+ * nodes, 0 on solid nodes). */
 int lb_export_rho(lb_handle* h, int32_t box, double* rho);
 
 /* Per-particle colour Delta rho of one box (host array of n_particles).

@@ -809,7 +809,7 @@ int lb_observables(lb_handle* h, int32_t box, lb_obs* out) {
     const BoxDev& B = h->hbox[box];
     cudaStream_t st = h->stream;
     const int par = (int)(h->t & 1);
-    CK(h->ops->obs_partial(st, h->d_boxes, box, par, h->obs_buf));
+    CK(h->ops->obs_partial(st, h->d_boxes, box, par, (int)(h->t % 3), h->obs_buf));
     double* fin = h->obs_buf + (size_t)OBS_BLOCKS * OBS_W;
     k_obs_final<<<1, 32, 0, st>>>(h->obs_buf, OBS_BLOCKS, fin);
     CK(cudaGetLastError());
@@ -852,7 +852,7 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
             const int k = d & 1;
             double* buf = h->stage + (size_t)k * B.N;
             if (d >= 2) CK(cudaStreamWaitEvent(st, h->ev_c[k], 0));
-            CK(h->ops->export_dir(st, h->d_boxes, box, d / 19, d % 19, par, buf));
+            CK(h->ops->export_dir(st, h->d_boxes, box, d / 19, d % 19, par, (int)(h->t % 3), buf));
             CK(cudaEventRecord(h->ev_k[k], st));
             CK(cudaStreamWaitEvent(h->xstream, h->ev_k[k], 0));
             CK(cudaMemcpyAsync(f + (size_t)d * B.N, buf, sizeof(double) * B.N, cudaMemcpyDeviceToHost, h->xstream));
@@ -971,7 +971,7 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
     for (int k = 0; k < 3; k++) CK(cudaMemsetAsync(B.rho[k], 0, (size_t)2 * N * h->ops->real_size, st));
     CK(cudaMemsetAsync(B.evmark, 0, sizeof(int32_t) * N, st));
     CK(cudaMemsetAsync(h->mass_tmp, 0, 2 * sizeof(double), st));
-    CK(h->ops->rho_from_pop(st, h->d_boxes, box, par, rcs, nullptr, h->mass_tmp));
+    CK(h->ops->rho_from_pop(st, h->d_boxes, box, par, -1, rcs, nullptr, h->mass_tmp));
     CK(cudaMemcpyAsync(B.mass_acc + 2 * par, h->mass_tmp, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemsetAsync(h->sh.counters + 2 * box, 0, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(h->sh.err, 0, sizeof(int), st));
@@ -983,7 +983,7 @@ int lb_export_rho(lb_handle* h, int32_t box, double* rho) {
     if (!h || !rho || box < 0 || box >= h->nb) return LB_EINVAL;
     const BoxDev& B = h->hbox[box];
     cudaStream_t st = h->stream;
-    CK(h->ops->rho_from_pop(st, h->d_boxes, box, (int)(h->t & 1), -1, h->stage, nullptr));
+    CK(h->ops->rho_from_pop(st, h->d_boxes, box, (int)(h->t & 1), (int)(h->t % 3), -1, h->stage, nullptr));
     CK(cudaMemcpyAsync(rho, h->stage, sizeof(double) * 2 * B.N, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return LB_OK;

@@ -131,8 +131,9 @@ static __global__ void k_init_pop(const BoxDev* __restrict__ boxes, int b, const
                 resid += fe - q;
                 sent += q;
             }
-            const R q0 = pop.store(c, 0, n, feq_rest<R>(r, ux, uy, uz) + resid);
-            sent += q0;
+            // the rest population: rho minus the 18 stored values, kept only
+            // as part of the density
+            sent += feq_rest<R>(r, ux, uy, uz) + resid;
             rcur[(size_t)c * B.N + n] = sent;
             if (c == 0) m0 += (double)sent;
             else m1 += (double)sent;
@@ -158,12 +159,26 @@ __device__ __forceinline__ typename P::real load_node_pop(const BoxDev& B, const
     return pop.load(c, opp(i), nbr_index(B, n, -cx(i), -cy(i), -cz(i)));
 }
 
+// f_0 of a fluid node: its density (ring slot rc) minus the 18 moving
+// populations, in double
 template <class P>
-static __global__ void k_export_dir(const BoxDev* __restrict__ boxes, int b, int c, int i, int par, double* __restrict__ out) {
+__device__ __forceinline__ double rest_of(const BoxDev& B, const Pop<P>& pop, int par, int rc, int c, int n) {
+    using R = typename P::real;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 1; i < 19; i++) s += (double)load_node_pop<P>(B, pop, par, c, i, n);
+    return (double)reinterpret_cast<const R*>(B.rho[rc])[(size_t)c * B.N + n] - s;
+}
+
+template <class P>
+static __global__ void k_export_dir(const BoxDev* __restrict__ boxes, int b, int c, int i, int par, int rc,
+                                    double* __restrict__ out) {
     const BoxDev& B = boxes[b];
     const Pop<P> pop(B);
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x)
-        out[n] = (B.flags[n] & FL_SOLID) ? 0.0 : (double)load_node_pop<P>(B, pop, par, c, i, n);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        if (B.flags[n] & FL_SOLID) out[n] = 0.0;
+        else out[n] = i == 0 ? rest_of<P>(B, pop, par, rc, c, n) : (double)load_node_pop<P>(B, pop, par, c, i, n);
+    }
 }
 
 template <class P>
@@ -179,21 +194,27 @@ static __global__ void k_import_dir(const BoxDev* __restrict__ boxes, int b, int
     }
 }
 
-// rho^c = sum_i f_i on fluid nodes (0 on solid) into ring slot rc and/or a
-// double array; fluid mass into mass_out
+// rho^c on fluid nodes (0 on solid) into ring slot rc and/or a double
+// array; fluid mass into mass_out.  With src < 0 rho^c = sum_i f_i of
+// freshly imported populations (rest slot included), else the density
+// field of ring slot src.
 template <class P>
-static __global__ void k_rho_from_pop(const BoxDev* __restrict__ boxes, int b, int par, int rc, double* __restrict__ out,
-                               double* __restrict__ mass_out) {
+static __global__ void k_rho_from_pop(const BoxDev* __restrict__ boxes, int b, int par, int src, int rc,
+                                      double* __restrict__ out, double* __restrict__ mass_out) {
     using R = typename P::real;
     const BoxDev& B = boxes[b];
     const Pop<P> pop(B);
     R* rcur = rc >= 0 ? reinterpret_cast<R*>(B.rho[rc]) : nullptr;
+    const R* rsrc = src >= 0 ? reinterpret_cast<const R*>(B.rho[src]) : nullptr;
     double m0 = 0.0, m1 = 0.0;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
         R r[2] = {R(0), R(0)};
         if (!(B.flags[n] & FL_SOLID))
-            for (int c = 0; c < 2; c++)
-                for (int i = 0; i < 19; i++) r[c] += load_node_pop<P>(B, pop, par, c, i, n);
+            for (int c = 0; c < 2; c++) {
+                if (rsrc) r[c] = rsrc[(size_t)c * B.N + n];
+                else
+                    for (int i = 0; i < 19; i++) r[c] += load_node_pop<P>(B, pop, par, c, i, n);
+            }
         if (rcur) {
             rcur[n] = r[0];
             rcur[(size_t)B.N + n] = r[1];
@@ -222,12 +243,15 @@ static __global__ void k_rho_from_pop(const BoxDev* __restrict__ boxes, int b, i
 // counts -> partials[block][8]; a second single-block pass reduces them.
 constexpr int OBS_W = 8;
 constexpr int OBS_BLOCKS = 304;
+// The mass of a fluid node is its density (ring slot rc); the momentum
+// comes from the 18 moving populations.
 template <class P>
-static __global__ void __launch_bounds__(256) k_obs_partial(const BoxDev* __restrict__ boxes, int b, int par,
-                                                     double* __restrict__ partials) {
+static __global__ void __launch_bounds__(256) k_obs_partial(const BoxDev* __restrict__ boxes, int b, int par, int rc,
+                                                            double* __restrict__ partials) {
     using R = typename P::real;
     const BoxDev& B = boxes[b];
     const Pop<P> pop(B);
+    const R* __restrict__ rho = reinterpret_cast<const R*>(B.rho[rc]);
     double v[OBS_W] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
         if (B.flags[n] & FL_SOLID) {
@@ -235,15 +259,17 @@ static __global__ void __launch_bounds__(256) k_obs_partial(const BoxDev* __rest
             continue;
         }
         double rt = 0, jt[3] = {0, 0, 0};
-        for (int c = 0; c < 2; c++)
-            for (int i = 0; i < 19; i++) {
+        for (int c = 0; c < 2; c++) {
+            const double r = (double)rho[(size_t)c * B.N + n];
+            v[c] += r;
+            rt += r;
+            for (int i = 1; i < 19; i++) {
                 const double f = (double)load_node_pop<P>(B, pop, par, c, i, n);
-                v[c] += f;
-                rt += f;
                 jt[0] += f * cx(i);
                 jt[1] += f * cy(i);
                 jt[2] += f * cz(i);
             }
+        }
         v[2] += jt[0];
         v[3] += jt[1];
         v[4] += jt[2];

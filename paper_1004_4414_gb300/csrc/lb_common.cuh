@@ -171,6 +171,9 @@ __device__ __forceinline__ R feq_rest(R rho, R ux, R uy, R uz) {
 //   FP64 / FP32: one array [2][19][N] of double / float.
 //   FP16 / BF16 deviations: [2][18][N] 16-bit values d = f/zeta_i - rho_ref^c
 //   for i = 1..18, and the rest population in a separate FP32 array [2][N].
+// The step keeps only the 18 moving populations: the density field holds
+// rho^c of every fluid node, and f_0 = rho^c - sum_{i>=1} f_i.  The rest
+// slot (i = 0) only carries an imported f_0 into the density field.
 struct P64 {
     using real = double;
     using st = double;
@@ -276,24 +279,6 @@ struct Pop {
             return dev_to_f(c, i, q);
         } else {
             *p = v;
-            return v;
-        }
-    }
-    __device__ __forceinline__ R ld_rest(int c, int n) const {
-        if constexpr (P::dev) return f0[(size_t)c * N + n];
-        else return base[(size_t)c * 19 * N + n];
-    }
-    __device__ __forceinline__ R st_rest(int c, int n, R v) const {
-        if constexpr (P::dev) f0[(size_t)c * N + n] = v;
-        else base[(size_t)c * 19 * N + n] = v;
-        return v;
-    }
-    // the value store(c, i, n, v) would leave, without storing
-    __device__ __forceinline__ R quant(int c, int i, R v) const {
-        if constexpr (P::dev) {
-            if (i == 0) return v;
-            return dev_to_f(c, i, f_to_dev(c, i, v));
-        } else {
             return v;
         }
     }

@@ -144,8 +144,8 @@ cudaError_t init_pop(cudaStream_t st, const BoxDev* boxes, int b, const double* 
     return cudaGetLastError();
 }
 
-cudaError_t export_dir(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, double* out) {
-    k_export_dir<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, c, i, par, out);
+cudaError_t export_dir(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, int rc, double* out) {
+    k_export_dir<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, c, i, par, rc, out);
     return cudaGetLastError();
 }
 
@@ -154,13 +154,14 @@ cudaError_t import_dir(cudaStream_t st, const BoxDev* boxes, int b, int c, int i
     return cudaGetLastError();
 }
 
-cudaError_t rho_from_pop(cudaStream_t st, const BoxDev* boxes, int b, int par, int rc, double* out, double* mass_out) {
-    k_rho_from_pop<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, par, rc, out, mass_out);
+cudaError_t rho_from_pop(cudaStream_t st, const BoxDev* boxes, int b, int par, int src, int rc, double* out,
+                         double* mass_out) {
+    k_rho_from_pop<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, par, src, rc, out, mass_out);
     return cudaGetLastError();
 }
 
-cudaError_t obs_partial(cudaStream_t st, const BoxDev* boxes, int b, int par, double* partials) {
-    k_obs_partial<PP><<<OBS_BLOCKS, 256, 0, st>>>(boxes, b, par, partials);
+cudaError_t obs_partial(cudaStream_t st, const BoxDev* boxes, int b, int par, int rc, double* partials) {
+    k_obs_partial<PP><<<OBS_BLOCKS, 256, 0, st>>>(boxes, b, par, rc, partials);
     return cudaGetLastError();
 }
 }  // namespace

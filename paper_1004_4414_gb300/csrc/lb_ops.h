@@ -23,11 +23,12 @@ struct LbOps {
     cudaError_t (*init_pop)(cudaStream_t st, const BoxDev* boxes, int b, const double* rho_field,
                             const double* u_field, uint64_t s_red, uint64_t s_blue, double noise, int rc,
                             double* mass_out);
-    cudaError_t (*export_dir)(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, double* out);
+    cudaError_t (*export_dir)(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, int rc,
+                              double* out);
     cudaError_t (*import_dir)(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, const double* in);
-    cudaError_t (*rho_from_pop)(cudaStream_t st, const BoxDev* boxes, int b, int par, int rc, double* out,
+    cudaError_t (*rho_from_pop)(cudaStream_t st, const BoxDev* boxes, int b, int par, int src, int rc, double* out,
                                 double* mass_out);
-    cudaError_t (*obs_partial)(cudaStream_t st, const BoxDev* boxes, int b, int par, double* partials);
+    cudaError_t (*obs_partial)(cudaStream_t st, const BoxDev* boxes, int b, int par, int rc, double* partials);
 };
 
 extern const LbOps lb_ops_fp64, lb_ops_fp32, lb_ops_fp16, lb_ops_bf16;

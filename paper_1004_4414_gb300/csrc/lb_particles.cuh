@@ -456,14 +456,12 @@ static __global__ void k_remap_apply(const BoxDev* __restrict__ boxes, Shared sh
             sh.ev_rho[(size_t)e * 2 + 0] = (double)rf.rho[0];
             sh.ev_rho[(size_t)e * 2 + 1] = (double)rf.rho[1];
             atomicAdd(&sh.counters[ev.y * 2 + 1], 1ull);
+            // the 18 moving populations; the density rho_new (set by
+            // k_remap_finish) makes the rest population rho_new minus them
             for (int c = 0; c < 2; c++) {
-                R resid = R(0);
 #pragma unroll
-                for (int i = 1; i < 19; i++) {
-                    const R fe = feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]);
-                    resid += fe - pop.store(c, slot(i), src(i), fe);
-                }
-                pop.store(c, 0, w, feq_rest<R>(rf.rho[c], rf.us[0], rf.us[1], rf.us[2]) + resid);
+                for (int i = 1; i < 19; i++)
+                    pop.store(c, slot(i), src(i), feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]));
             }
             // the particle loses the momentum of the created fluid
             // (Eq. eqn_ladd_vernichtenunderzeugen, sign from conservation)
@@ -694,12 +692,14 @@ static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* _
 //     (Eq. eqn_ladd_bewegtewand), and the particle receives
 //     (2 f*_j - 6 zeta_j rho^c(x) u_s . c_j) c_j with torque r x F
 //     (Eq. eqn_bounce-back-force).  rho(t+1) at x gets the change of the
-//     stored value (reflect = 1) or all of it (reflect = 0), and the fluid
-//     mass the step produced gets the change; in deviation storage the rest
-//     slot of x absorbs the rounding.
+//     value (reflect = 1) or all of it (reflect = 0), and the fluid mass the
+//     step produced gets the change.  In deviation storage the density
+//     field takes the exact change b - f*_j: the rounding of the re-encoded
+//     value lands in the rest population of x, which is rho^c minus the 18
+//     stored ones; an unchanged value (no wall term) moves bit for bit.
 // A link belongs to the owner of its solid end, so each slot is written
-// once; the density and rest-slot updates are atomic because several links
-// can share a fluid node.  Static walls (owner -2) reflect without a wall
+// once; the density updates are atomic because several links can share a
+// fluid node.  Static walls (owner -2) reflect without a wall
 // term and need nothing here.  rho^c(x) is the density field of the current
 // step (the fused step's moments up to rounding order).
 constexpr int COUPLE_THREADS = 256;
@@ -799,13 +799,15 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
                 const R fs = c == 0 ? fsu0[u] : fsu1[u];
                 const R wall = cu6 * (c == 0 ? rru[u] : rbu[u]);
                 if (wall != R(0) || !reflect) {
-                    const R b = fs - wall;
-                    const R q = pop.st((c == 0 ? pu0[u] : pu1[u]) + mv[u], c, i, b);
-                    R dr = q - fs;
-                    if constexpr (P::dev) {
-                        const R res = b - q;
-                        atomicAdd(&pop.f0[(size_t)c * N + m], res);
-                        dr += res;
+                    S* const at = c == 0 ? pu0[u] : pu1[u];
+                    R dr;
+                    if (P::dev && wall == R(0)) {
+                        at[mv[u]] = *at;
+                        dr = R(0);
+                    } else {
+                        const R b = fs - wall;
+                        const R q = pop.st(at + mv[u], c, i, b);
+                        dr = P::dev ? b - fs : q - fs;
                     }
                     atomicAdd(&rnext[(size_t)c * N + m], reflect ? dr : dr + fs);
                     if (c == 0) dm0 += dr;

@@ -21,6 +21,12 @@
 //     never depend on the status of a neighbour.  Each slot is read once and
 //     written once per step; neighbour offsets are wrap-aware and computed
 //     once per thread.
+//   * Only the 18 moving populations are stored.  A node's rho^c is the
+//     density field of the current step (the window fetches it for Psi
+//     anyway), and its rest population f_0 = rho^c - sum_{i>=1} f_i stays at
+//     the node: it enters only the density scatter.  So a fluid node moves
+//     2 x 18 populations per step, and the density field is the state's
+//     mass.
 //   * Reflection (template flag BB).  BB = true: the kernel reads the solid
 //     status of the 18 neighbours and selects each store's slot itself.
 //     BB = false: it stores every population as if its target were fluid
@@ -225,8 +231,19 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     // rolling slots of planes z-1, z, z+1
     int sm_ = 0, sc_ = 1, sp_ = 2;
     load_window(z0 - 1, sm_);
-    load_window(z0, sc_);
-    load_window(z0 + 1, sp_);
+    // the densities of the own node in planes z and z + 1: the window
+    // fetches them anyway, and they are the node's rho^r and rho^b
+    R rq0[2], rq1[2];
+    {
+        const WinRaw v0 = fetch_window(z0);
+        store_window(v0, sc_);
+        rq0[0] = v0.a0;
+        rq0[1] = v0.a1;
+        const WinRaw v1 = fetch_window(z0 + 1);
+        store_window(v1, sp_);
+        rq1[0] = v1.a0;
+        rq1[1] = v1.a1;
+    }
     R acc[3][2];  // own-column partial densities of planes z-1, z, z+1
 #pragma unroll
     for (int k = 0; k < 3; k++) acc[k][0] = acc[k][1] = R(0);
@@ -267,7 +284,6 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             }
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                f[c][0] = pop.ld_rest(c, n);
 #pragma unroll
                 for (int i = 1; i < 19; i++) {
                     // even steps: own slot i; odd steps: slot opp(i) of x - c_i
@@ -275,13 +291,16 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     f[c][i] = pop.ld(p, c, i);
                 }
             }
+            // rho^c is the density field (the sum of the values the previous
+            // step sent here); the rest population is rho^c minus the 18
+            // moving ones and is needed only for tau != 1
             R jx[2], jy[2], jz[2];
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 R r = 0, ax = 0, ay = 0, az = 0;
 #pragma unroll
-                for (int i = 0; i < 19; i++) {
-                    r += f[c][i];
+                for (int i = 1; i < 19; i++) {
+                    if constexpr (!T1) r += f[c][i];
                     if (cx(i) > 0) ax += f[c][i];
                     if (cx(i) < 0) ax -= f[c][i];
                     if (cy(i) > 0) ay += f[c][i];
@@ -289,7 +308,8 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     if (cz(i) > 0) az += f[c][i];
                     if (cz(i) < 0) az -= f[c][i];
                 }
-                rho[c] = r;
+                rho[c] = rq0[c];
+                f[c][0] = T1 ? R(0) : rq0[c] - r;
                 jx[c] = ax;
                 jy[c] = ay;
                 jz[c] = az;
@@ -408,11 +428,12 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                 // rest population: its equilibrium is rho minus the other 18
                 // (equal to Eq. Equil in exact arithmetic), and in deviation
                 // storage it absorbs the rounding of the 18 stored values, so
-                // node mass is kept to FP32 rounding
-                const R q0 = pop.st_rest(c, n, (T1 ? R(0) : omt * f[c][0]) + itc * (rho[c] - fe_sum) + resid);
+                // node mass is kept to FP32 rounding.  It stays at the node and
+                // enters only the density field: it is not stored.
+                const R q0 = (T1 ? R(0) : omt * f[c][0]) + itc * (rho[c] - fe_sum) + resid;
                 mid[0] += q0 + self;
-                // the 19 stored values sum to rho^c: the collision conserves
-                // mass and the rest slot absorbs the rounding of the others
+                // the 18 stored values and q0 sum to rho^c: the collision
+                // conserves mass
                 if (c == 0) msum0 += rho[0];
                 else msum1 += rho[1];
             }
@@ -506,6 +527,10 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
         }
 
         if (more) store_window(ahead, sp_);
+        rq0[0] = rq1[0];
+        rq0[1] = rq1[1];
+        rq1[0] = ahead.a0;
+        rq1[1] = ahead.a1;
 
         __syncthreads();
     }

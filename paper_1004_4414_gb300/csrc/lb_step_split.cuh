@@ -94,8 +94,6 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             return v;
         }
     };
-    auto ld_rest = [&](int n) -> R { return pop.ld_rest(c, n); };
-    auto st_rest = [&](int n, R v) -> R { return pop.st_rest(c, n, v); };
 
     const int w = T.w, h = T.h, d = T.d, x0 = T.x0, y0 = T.y0, z0 = T.z0;
     const bool active = lx < w && ly < h;
@@ -166,8 +164,17 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
 
     int sm_ = 0, sc_ = 1, sp_ = 2;
     store_window(fetch_window(z0 - 1), sm_);
-    store_window(fetch_window(z0), sc_);
-    store_window(fetch_window(z0 + 1), sp_);
+    // this component's density at the own node of planes z and z + 1: the
+    // window fetches it anyway, and it is the node's rho^c
+    R rq0, rq1;
+    {
+        const WinRaw v0 = fetch_window(z0);
+        store_window(v0, sc_);
+        rq0 = v0.a;
+        const WinRaw v1 = fetch_window(z0 + 1);
+        store_window(v1, sp_);
+        rq1 = v1.a;
+    }
     R acc[3] = {R(0), R(0), R(0)};  // own-column partial densities of planes z-1, z, z+1
     R msum = R(0);
     __syncthreads();
@@ -201,16 +208,18 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
                 for (int i = 1; i < 19; i++)
                     smask |= (unsigned)(FLG(slot_dz(cz(i)), ly + 1 + cy(i), lx + 1 + cx(i)) & FL_SOLID) << i;
             }
-            f[0] = ld_rest(n);
 #pragma unroll
             for (int i = 1; i < 19; i++) {
                 const S* p = PAR == 0 ? dirp(i) + n : dirp(opp(i)) + (n + off(opp(i)));
                 f[i] = ldv(p, i);
             }
+            // rho^c is the density field (the sum of the values the previous
+            // step sent here); the rest population is rho^c minus the 18
+            // moving ones and is needed only for tau != 1
             R r = 0, ax = 0, ay = 0, az = 0;
 #pragma unroll
-            for (int i = 0; i < 19; i++) {
-                r += f[i];
+            for (int i = 1; i < 19; i++) {
+                if constexpr (!T1) r += f[i];
                 if (cx(i) > 0) ax += f[i];
                 if (cx(i) < 0) ax -= f[i];
                 if (cy(i) > 0) ay += f[i];
@@ -218,7 +227,8 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
                 if (cz(i) > 0) az += f[i];
                 if (cz(i) < 0) az -= f[i];
             }
-            rho = r;
+            rho = rq0;
+            f[0] = T1 ? R(0) : rq0 - r;
             jx = ax;
             jy = ay;
             jz = az;
@@ -328,7 +338,8 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             pair(std::integral_constant<int, 13>{}, ux - uz);
             pair(std::integral_constant<int, 15>{}, uy + uz);
             pair(std::integral_constant<int, 17>{}, uy - uz);
-            const R q0 = st_rest(n, (T1 ? R(0) : omt * f[0]) + itc * (rho - fe_sum) + resid);
+            // the rest population stays at the node; it is not stored
+            const R q0 = (T1 ? R(0) : omt * f[0]) + itc * (rho - fe_sum) + resid;
             mid[0] += q0 + self;
             msum += rho;
         }
@@ -402,6 +413,8 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             sp_ = t;
         }
         if (more) store_window(ahead, sp_);
+        rq0 = rq1;
+        rq1 = ahead.a;
         __syncthreads();
     }
     if (active) {

@@ -92,7 +92,7 @@ def test_c512_fp16_mass_conserved_fixed_particles():
     """The largest configuration, 512^3 with 51,267 spheres (the paper's
     alpha = 0.20, R = 5) in FP16 deviation storage: with the particles held
     fixed (no cover/uncover) each component's mass is conserved to the
-    FP32 rest slot's rounding."""
+    rounding of the FP32 density field."""
     from paper_1004_4414_gb300 import Simulation
 
     box = dict(C256, nx=512, ny=512, nz=512, rho_init=(0.35, 0.35), contact_angle_deg=90.0, precision="fp16",
