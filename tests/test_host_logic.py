@@ -107,3 +107,29 @@ def test_reference_arm_times_a_bounded_sample():
     r = bench.oracle_steps("c32", steps=2, warmup=1, edge=16)
     assert r["steps"] == 2 and r["N"] == 16 ** 3 and r["value"] > 0
     assert "16x16x16" in r["sample"] and "32x32x32" in r["sample"]
+
+
+class _ObsSim:
+    """Boxes with given node and fluid-node counts (bench.fused_bytes reads
+    nb, n_nodes and observables(b)["n_fluid"])."""
+
+    def __init__(self, boxes):
+        self.nb = len(boxes)
+        self.n_nodes = [n for n, _ in boxes]
+        self._fluid = [f for _, f in boxes]
+
+    def observables(self, b):
+        return {"n_fluid": self._fluid[b]}
+
+
+@pytest.mark.parametrize("prec,per_fluid,per_node", [("fp32", 288, 17), ("fp16", 144, 17), ("bf16", 144, 17),
+                                                     ("fp64", 576, 33)])
+def test_algorithmic_bytes_count_18_stored_populations(prec, per_fluid, per_node):
+    """The roofline numerator: a fluid node reads and writes its 2 x 18 moving
+    populations (the rest population is the density minus them and is never
+    stored); every node reads one and writes one density per component and
+    reads a flag byte."""
+    import bench
+
+    sim = _ObsSim([(1000, 800), (64, 0), (27, 27)])
+    assert bench.fused_bytes(sim, prec) == (800 + 27) * per_fluid + (1000 + 64 + 27) * per_node
