@@ -65,22 +65,22 @@ extern "C" {
 /* One periodic box.  Densities follow the paper's symbols. */
 typedef struct {
     int32_t nx, ny, nz;          /* lattice size, each >= 1 */
-    int32_t n_particles;         /* exact particle count; < 0: round(volume_fraction N / (4/3 pi R^3)) */
+    int32_t n_particles;         /* exact particle count (<= N); < 0: round(volume_fraction N / (4/3 pi R^3)) */
     double tau[2];               /* BGK relaxation times tau^r, tau^b (> 1/2) */
     double g_br;                 /* Shan-Chen coupling g_br = g_rb; g_rr = g_bb = 0 */
     double rho0;                 /* reference density of Psi */
     double sc_weight[2];         /* link weights of the force stencil: axis, diagonal */
     double rho_init[2];          /* mean initial density per component */
-    double noise_amp;            /* seeded init: rho^c = rho_init^c + U(-a, a) per node */
-    double volume_fraction;      /* alpha, used when n_particles < 0 */
+    double noise_amp;            /* seeded init: rho^c = rho_init^c + U(-a, a) per node (a >= 0) */
+    double volume_fraction;      /* alpha in [0, 1), used when n_particles < 0 */
     double radius;               /* sphere radius r_par (all particles); for spheroids the equatorial semi-axis R */
     double particle_density;     /* m = rho_p 4/3 pi R^3 (spheroids: R^2 c), J = 2/5 m R^2 */
     double color;                /* particle colour Delta rho; used when contact_angle_deg is NaN */
     double contact_angle_deg;    /* if finite: Delta rho = (theta - 90) / 442 (fit of Fig. 4b) */
-    double k_hertz;              /* K_Hertz of Eq. eq:hertz */
+    double k_hertz;              /* K_Hertz of Eq. eq:hertz (>= 0) */
     double lub_cut;              /* lubrication below this gap (> lub_min) */
     double lub_min;              /* gap where lubrication is clamped (> 0) */
-    double mass_corr_c0;         /* C0 of Eq. masscorr (0 = off) */
+    double mass_corr_c0;         /* C0 of Eq. masscorr (>= 0; 0 = off) */
     double body_force[3];        /* uniform acceleration of the fluid (tests; 0 in the paper's runs) */
     int32_t vel_mode;            /* 0: Shan-Chen common velocity in f^eq, 1: each component's own velocity */
     int32_t fixed_particles;     /* 1: particles keep X, U, omega (prescribed motion; tests) */
@@ -106,7 +106,9 @@ typedef struct {
 typedef struct lb_handle lb_handle;
 
 /* Device workspace needed for n_boxes boxes: bytes out.  LB_EINVAL on bad
- * parameters.  The caller allocates it (e.g. torch.empty on the device) and
+ * parameters: a value outside the range stated in lb_params, a non-finite
+ * real (contact_angle_deg excepted; volume_fraction only when it is used),
+ * or mixed precisions.  The caller allocates it (e.g. torch.empty on the device) and
  * keeps it alive until lb_destroy; the library never allocates device
  * memory for the lattice. */
 int lb_workspace_bytes(const lb_params* boxes, int32_t n_boxes, size_t* bytes);

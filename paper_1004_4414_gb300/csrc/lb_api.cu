@@ -55,10 +55,14 @@ double particle_volume(const lb_params& p) {
     return 4.0 / 3.0 * M_PI * p.radius * p.radius * (a * p.radius);
 }
 
+// -1 for a count that is not a valid particle number: a volume fraction
+// outside [0, 1) or NaN, or more particles than nodes
 int derive_np(const lb_params& p) {
-    if (p.n_particles >= 0) return p.n_particles;
     const double N = (double)p.nx * p.ny * p.nz;
-    return (int)std::floor(p.volume_fraction * N / particle_volume(p) + 0.5);
+    if (p.n_particles >= 0) return p.n_particles <= N ? p.n_particles : -1;
+    if (!(p.volume_fraction >= 0.0 && p.volume_fraction < 1.0)) return -1;
+    const double n = std::floor(p.volume_fraction * N / particle_volume(p) + 0.5);
+    return (n >= 0.0 && n <= N) ? (int)n : -1;
 }
 
 double box_color(const lb_params& p) {
@@ -71,6 +75,16 @@ int validate(const lb_params* bx, int nb) {
     if (!bx || nb <= 0) return LB_EINVAL;
     for (int b = 0; b < nb; b++) {
         const lb_params& p = bx[b];
+        // every real parameter finite (contact_angle_deg may be NaN: use color)
+        const double reals[] = {p.tau[0], p.tau[1], p.g_br, p.rho0, p.sc_weight[0], p.sc_weight[1], p.rho_init[0],
+                                p.rho_init[1], p.noise_amp, p.radius, p.particle_density, p.color, p.k_hertz,
+                                p.lub_cut, p.lub_min, p.mass_corr_c0, p.body_force[0], p.body_force[1],
+                                p.body_force[2], p.aspect};
+        for (double v : reals)
+            if (!std::isfinite(v)) return LB_EINVAL;
+        if (p.n_particles < 0 && !std::isfinite(p.volume_fraction)) return LB_EINVAL;
+        if (p.noise_amp < 0.0 || p.k_hertz < 0.0 || p.mass_corr_c0 < 0.0) return LB_EINVAL;
+        if (p.fixed_particles != 0 && p.fixed_particles != 1) return LB_EINVAL;
         if (p.nx < 1 || p.ny < 1 || p.nz < 1) return LB_EINVAL;
         if (p.nx > 65535 || p.ny > 65535 || p.nz > 65535) return LB_EINVAL;
         if ((double)p.nx * p.ny * p.nz >= 2147483647.0) return LB_EINVAL;

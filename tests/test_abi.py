@@ -59,14 +59,31 @@ def test_invalid_parameters_rejected(lib):
     from paper_1004_4414_gb300 import binding
 
     n = C.c_size_t(0)
+    nan, inf = float("nan"), float("inf")
     for bad in (dict(nx=0), dict(tau=(0.5, 1.0)), dict(precision=7), dict(reserved=1), dict(radius=0.0),
                 dict(rho_init=(0.0, 0.7)), dict(lub_min=0.0), dict(lub_cut=0.1, lub_min=0.1),
-                dict(aspect=0.05), dict(aspect=11.0), dict(aspect=-1.0), dict(aspect=float("nan"))):
+                dict(aspect=0.05), dict(aspect=11.0), dict(aspect=-1.0), dict(aspect=nan),
+                dict(ny=0), dict(nz=-3), dict(nx=65536), dict(nx=2048, ny=2048, nz=512),
+                dict(tau=(1.0, 0.4)), dict(tau=(nan, 1.0)), dict(tau=(inf, 1.0)), dict(rho0=0.0),
+                dict(rho0=inf), dict(particle_density=-1.0), dict(rho_init=(0.7, -0.1)),
+                dict(rho_init=(inf, 0.7)), dict(vel_mode=2), dict(g_br=nan), dict(sc_weight=(1.0, inf)),
+                dict(noise_amp=-0.01), dict(noise_amp=nan), dict(k_hertz=-1.0), dict(mass_corr_c0=-1.0),
+                dict(color=nan), dict(body_force=(0.0, nan, 0.0)), dict(fixed_particles=2),
+                dict(lub_cut=nan), dict(radius=inf),
+                # a derived particle count must be a number of particles the box can hold
+                dict(n_particles=-1, volume_fraction=nan), dict(n_particles=-1, volume_fraction=-0.1),
+                dict(n_particles=-1, volume_fraction=1.0), dict(n_particles=-1, volume_fraction=1e30),
+                dict(n_particles=-1, volume_fraction=0.5, radius=1e-4),
+                dict(nx=4, ny=4, nz=4, n_particles=65)):
         p = binding.make_params(**bad)
         arr = (binding.LbParams * 1)(p)
         assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_EINVAL
-    # spheres (aspect 0 or 1) and spheroids within [0.1, 10] are accepted
-    for good in (dict(aspect=0.0), dict(aspect=1.0), dict(aspect=0.1), dict(aspect=10.0), dict(aspect=1.75)):
+    # spheres (aspect 0 or 1) and spheroids within [0.1, 10] are accepted; so
+    # are an unused NaN volume fraction, a NaN contact angle (colour given)
+    # and a box exactly full of particles by count
+    for good in (dict(aspect=0.0), dict(aspect=1.0), dict(aspect=0.1), dict(aspect=10.0), dict(aspect=1.75),
+                 dict(n_particles=3, volume_fraction=nan), dict(contact_angle_deg=nan, color=0.02),
+                 dict(nx=4, ny=4, nz=4, n_particles=64), dict(n_particles=-1, volume_fraction=0.0)):
         arr = (binding.LbParams * 1)(binding.make_params(**good))
         assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_OK
     # a prolate spheroid needs a larger workspace than the sphere of its
