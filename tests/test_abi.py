@@ -101,6 +101,15 @@ def test_invalid_parameters_rejected(lib):
     h = C.c_void_p()
     arr = (binding.LbParams * 1)(binding.make_params())
     assert lib.lb_create(arr, 1, None, 0, None, C.byref(h)) == binding.LB_EINVAL
+    # a misaligned or too small workspace and a missing handle pointer are
+    # rejected from the arguments alone (the pointer is never dereferenced)
+    assert lib.lb_workspace_bytes(arr, 1, C.byref(n)) == binding.LB_OK
+    need = n.value
+    assert lib.lb_create(arr, 1, C.c_void_p(0x100010), need, None, C.byref(h)) == binding.LB_EINVAL
+    assert lib.lb_create(arr, 1, C.c_void_p(0x100000), need - 1, None, C.byref(h)) == binding.LB_ENOMEM
+    assert lib.lb_create(arr, 1, C.c_void_p(0x100000), need, None, None) == binding.LB_EINVAL
+    assert lib.lb_create(arr, 0, C.c_void_p(0x100000), need, None, C.byref(h)) == binding.LB_EINVAL
+    assert not h.value
     assert lib.lb_step(None, 1) == binding.LB_EINVAL
 
 
