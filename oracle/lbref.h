@@ -36,7 +36,7 @@ typedef struct {
     double radius;              /* r_par, same for every particle */
     double particle_density;    /* m = rho_p 4/3 pi R^3 */
     double color;               /* particle colour Delta rho (Sec. IV) */
-    double k_hertz;             /* K_Hertz (Eq. eq:hertz) */
+    double k_hertz;             /* K_Hertz (Eq. eq:hertz); the paper gives no value: parity unpinned */
     double lub_cut;             /* lubrication acts below this gap (2/3) */
     double lub_min;             /* gap at which it is clamped (1/10) */
     double mass_corr_c0;        /* C0 of Eq. masscorr; 0 = off */
@@ -90,7 +90,11 @@ void orc_set_particle_colors(orc_state* s, const double* colors);
 void orc_get_axes(const orc_state* s, double* e);
 void orc_set_axes(orc_state* s, const double* e);
 /* test hooks for spheroids: inside test of a displacement d (minimum image)
- * for a particle with axis e; contact distance of two particles along r_hat */
+ * for a particle with axis e; contact distance of two particles along r_hat.
+ * Parity unpinned for the contact distance: the paper gives no contact law
+ * for non-spherical particles.  The sum of the two support radii along the
+ * line of centres is a reading, pinned only to its closed-form limits
+ * (spheres: 2R; aligned spheroids: sums of semi-axes). */
 int32_t orc_inside(const orc_params* p, const double d[3], const double e[3]);
 double orc_contact_distance(const orc_params* p, const double rh[3], const double ep[3], const double eq[3]);
 /* one rotational MD update of a free particle: omega (in/out), e (in/out), torque T */
