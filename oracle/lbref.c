@@ -15,7 +15,8 @@
  *   6. streaming with moving-wall bounce-back and momentum exchange
  *      (Eqs. eqn_bounce-back, eqn_ladd_bewegtewand);
  *   7. particle MD: Hertz contact (Eq. eq:hertz), lubrication
- *      (Eq. eqn_ladd_lubrikation), leap-frog for U, omega, X.
+ *      (Eq. eqn_ladd_lubrikation), leap-frog for U, omega, X (or, with
+ *      implicit_update, the implicit velocity update of reading #18).
  * Readings of places where the paper is silent or garbled are listed where
  * they are used.
  */
@@ -103,6 +104,7 @@ struct orc_state {
     double *X, *U, *W, *F, *T, *color; /* [np][3] / [np] */
     double* E;          /* [np][3] body axis of a spheroid (unit vector) */
     double Flast[1], *Fsave, *Tsave;
+    double *Z, *dV;     /* implicit update: [np][6][6] link drag tensor, [np][6] velocity change */
     double mass0[2];
     int64_t n_cover, n_uncover;
 };
@@ -251,6 +253,7 @@ static int derive_np(const orc_params* p) {
 
 orc_state* orc_create(const orc_params* p, int32_t n_particles) {
     init_tables();
+    if (p->implicit_update && !is_sphere(p)) return NULL;
     orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
     s->p = *p;
     s->nx = p->nx; s->ny = p->ny; s->nz = p->nz;
@@ -276,6 +279,8 @@ orc_state* orc_create(const orc_params* p, int32_t n_particles) {
     s->Tsave = (double*)calloc(3 * np, sizeof(double));
     s->color = (double*)calloc(np, sizeof(double));
     s->E = (double*)calloc(3 * np, sizeof(double));
+    s->Z = (double*)calloc(36 * np, sizeof(double));
+    s->dV = (double*)calloc(6 * np, sizeof(double));
     for (int q = 0; q < s->np; q++) s->color[q] = p->color;
     for (int q = 0; q < s->np; q++) s->E[3 * q + 2] = 1.0;
     for (size_t n = 0; n < N; n++) s->owner[n] = -1;
@@ -289,6 +294,7 @@ void orc_destroy(orc_state* s) {
     free(s->X); free(s->U); free(s->W); free(s->F); free(s->T); free(s->Fsave); free(s->Tsave);
     free(s->color);
     free(s->E);
+    free(s->Z); free(s->dV);
     free(s);
 }
 
@@ -380,6 +386,25 @@ static void add_force(orc_state* s, int q, const double r[3], const double dF[3]
         s->F[3 * q + a] += dF[a];
         s->T[3 * q + a] += tq[a];
     }
+}
+
+/* Implicit update (reading #18).  The wall term of a link from the fluid
+ * node x to particle q in direction j is k a.V, with k = 6 zeta_j rho^c(x),
+ * V = (U, omega) and a = (c_j, r x c_j) (u_s . c_j = c_j . U + (r x c_j) .
+ * omega).  The link's force and torque on q are (2 f* - k a.V) a, so they
+ * change by -k a a^T dV when V does: Z = sum over links of k a a^T. */
+static void link_dir(const double r[3], int j, double a[6]) {
+    const double cj[3] = {CV[j][0], CV[j][1], CV[j][2]};
+    a[0] = cj[0];
+    a[1] = cj[1];
+    a[2] = cj[2];
+    cross3(r, cj, &a[3]);
+}
+static void add_drag(orc_state* s, int q, const double r[3], int j, double k) {
+    double a[6];
+    link_dir(r, j, a);
+    for (int u = 0; u < 6; u++)
+        for (int v = 0; v < 6; v++) s->Z[36 * q + 6 * u + v] += k * a[u] * a[v];
 }
 
 /* densities rho^c = sum_i f_i^c on fluid nodes (rho0 = 1 in the density
@@ -640,6 +665,7 @@ static void stream_bounce(orc_state* s) {
                     double mag = 2.0 * fsj - wall;
                     double dF[3] = {mag * CV[j][0], mag * CV[j][1], mag * CV[j][2]};
                     add_force(s, q, r, dF);
+                    if (s->p.implicit_update) add_drag(s, q, r, j, 6.0 * WT[j] * s->rho[(int64_t)c * N + n]);
                 }
             }
         }
@@ -689,6 +715,98 @@ void orc_pair_force(const orc_params* P, const double Xp[3], const double Xq[3],
     pair_force(P, Lb, Xp, Xq, Up, Uq, ez, ez, Fp);
 }
 
+/* Solve A x = b for a 6 x 6 system (Gaussian elimination, partial
+ * pivoting); A is row-major, both are overwritten. */
+static void solve6(double A[36], double b[6], double x[6]) {
+    for (int col = 0; col < 6; col++) {
+        int piv = col;
+        for (int r = col + 1; r < 6; r++)
+            if (fabs(A[6 * r + col]) > fabs(A[6 * piv + col])) piv = r;
+        if (piv != col) {
+            for (int v = 0; v < 6; v++) {
+                const double t = A[6 * col + v];
+                A[6 * col + v] = A[6 * piv + v];
+                A[6 * piv + v] = t;
+            }
+            const double t = b[col];
+            b[col] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = col + 1; r < 6; r++) {
+            const double f = A[6 * r + col] / A[6 * col + col];
+            for (int v = col; v < 6; v++) A[6 * r + v] -= f * A[6 * col + v];
+            b[r] -= f * b[col];
+        }
+    }
+    for (int r = 5; r >= 0; r--) {
+        double t = b[r];
+        for (int v = r + 1; v < 6; v++) t -= A[6 * r + v] * x[v];
+        x[r] = t / A[6 * r + r];
+    }
+}
+
+/* Reading #18, implicit particle velocity update (the cited particle
+ * method, Ladd & Verberg 2001, discusses implicit updates for light
+ * particles).  The links' wall term is taken at the new velocity: with the
+ * force and torque (F, T) of this step, computed at the old velocity, and
+ * the drag tensor Z of add_drag,
+ *     (M + Z) dV = (F, T),  M = diag(m, m, m, J, J, J),  J = 2/5 m R^2.
+ * The fluid gets the same change of the wall term, -k a.dV on every link's
+ * bounce-back population, so fluid plus particle momentum stays exact.
+ * Then U += dU, omega += d omega, X += U.  Spheres only. */
+static void implicit_velocity_update(orc_state* s, double m, const double Lb[3]) {
+    const int np = s->np;
+    const int64_t N = s->N;
+    const double J = 0.4 * m * s->p.radius * s->p.radius;
+    const int moving = !s->p.fixed_particles;
+    for (int p = 0; p < np; p++) {
+        double A[36], b[6];
+        for (int u = 0; u < 36; u++) A[u] = s->Z[36 * p + u];
+        for (int u = 0; u < 3; u++) {
+            A[7 * u] += m;
+            A[7 * (u + 3)] += J;
+            b[u] = s->F[3 * p + u];
+            b[u + 3] = s->T[3 * p + u];
+        }
+        if (moving) solve6(A, b, &s->dV[6 * p]);
+        else
+            for (int u = 0; u < 6; u++) s->dV[6 * p + u] = 0.0;
+    }
+    if (moving) {
+        /* the fluid's share: links as in stream_bounce, with the positions
+         * the step used */
+        for (int64_t n = 0; n < N; n++) {
+            if (s->owner[n] != -1) continue;
+            int x, y, z;
+            ncoord(s, n, &x, &y, &z);
+            for (int i = 1; i < Q; i++) {
+                const int j = OPPI[i];
+                const int q = s->owner[nbr(s, n, j)];
+                if (q < 0) continue;
+                double r[3], a[6];
+                rel_pos(s, x + 0.5 * CV[j][0], y + 0.5 * CV[j][1], z + 0.5 * CV[j][2], q, r);
+                link_dir(r, j, a);
+                double ad = 0.0;
+                for (int u = 0; u < 6; u++) ad += a[u] * s->dV[6 * q + u];
+                for (int c = 0; c < 2; c++) s->f[FIDX(s, c, i, n)] -= 6.0 * WT[j] * s->rho[(int64_t)c * N + n] * ad;
+            }
+        }
+        for (int p = 0; p < np; p++)
+            for (int a = 0; a < 3; a++) {
+                s->U[3 * p + a] += s->dV[6 * p + a];
+                s->W[3 * p + a] += s->dV[6 * p + 3 + a];
+                double xn = s->X[3 * p + a] + s->U[3 * p + a];
+                xn -= Lb[a] * floor(xn / Lb[a]);
+                if (xn >= Lb[a]) xn -= Lb[a];
+                s->X[3 * p + a] = xn;
+            }
+    }
+    for (int p = 0; p < np; p++) {
+        for (int a = 0; a < 3; a++) s->F[3 * p + a] = s->T[3 * p + a] = 0.0;
+        for (int u = 0; u < 36; u++) s->Z[36 * p + u] = 0.0;
+    }
+}
+
 static void md_update(orc_state* s) {
     const int np = s->np;
     memcpy(s->Fsave, s->F, 3 * sizeof(double) * (np > 0 ? np : 1));
@@ -706,6 +824,10 @@ static void md_update(orc_state* s) {
             }
         }
     double m = particle_mass(s);
+    if (s->p.implicit_update) {
+        implicit_velocity_update(s, m, Lb);
+        return;
+    }
     for (int p = 0; p < np; p++) {
         if (!s->p.fixed_particles) {
             rotate_particle(&s->p, m, &s->W[3 * p], &s->E[3 * p], &s->T[3 * p]);

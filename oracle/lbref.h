@@ -47,6 +47,8 @@ typedef struct {
     int32_t pad_;
     uint64_t seed;
     double aspect;              /* spheroid: semi-axes R, R, aspect R about the body axis e; 1 = sphere */
+    int32_t implicit_update;    /* 1: implicit particle velocity update (reading #18; spheres only) */
+    int32_t pad2_;
 } orc_params;
 
 typedef struct orc_state orc_state;
@@ -68,6 +70,7 @@ void orc_feq(double rho, const double u[3], double out[19]);
 uint64_t orc_splitmix64(uint64_t s, uint64_t n);
 double orc_unit(uint64_t s, uint64_t n);
 
+/* NULL for implicit_update with a non-spherical particle shape */
 orc_state* orc_create(const orc_params* p, int32_t n_particles);
 void orc_destroy(orc_state* s);
 int32_t orc_n_particles(const orc_state* s);

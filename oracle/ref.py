@@ -39,6 +39,8 @@ class OrcParams(C.Structure):
         ("pad_", C.c_int32),
         ("seed", C.c_uint64),
         ("aspect", C.c_double),
+        ("implicit_update", C.c_int32),
+        ("pad2_", C.c_int32),
     ]
 
 
@@ -59,7 +61,7 @@ DEFAULTS = dict(
     sc_weight=(2.0, 1.0), rho_init=(0.7, 0.7), noise_amp=0.01, volume_fraction=0.0,
     radius=5.0, particle_density=1.0, color=0.0, k_hertz=100.0, lub_cut=2.0 / 3.0,
     lub_min=0.1, mass_corr_c0=0.0, body_force=(0.0, 0.0, 0.0), vel_mode=0,
-    virtual_fluid=1, fixed_particles=0, seed=1, aspect=1.0,
+    virtual_fluid=1, fixed_particles=0, seed=1, aspect=1.0, implicit_update=0,
 )
 
 _lib = None
@@ -198,6 +200,8 @@ class Oracle:
     def __init__(self, **params):
         self.params = make_params(**params)
         self._h = lib().orc_create(C.byref(self.params), int(self.params.n_particles))
+        if not self._h:
+            raise ValueError("oracle rejected the parameters")
         self.nx, self.ny, self.nz = self.params.nx, self.params.ny, self.params.nz
         self.N = self.nx * self.ny * self.nz
         self.np = lib().orc_n_particles(self._h)

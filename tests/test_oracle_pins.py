@@ -795,3 +795,79 @@ def test_overlapping_spheroids_claims_brute_force():
                             best, bd = q, d2
                 assert own[z, y, x] == best, (x, y, z, own[z, y, x], best)
     assert both > 20
+
+
+# ------------------------------------- implicit particle update (reading #18)
+def _link_drag(o, X, rho_tot):
+    """Z = sum over the links of the particle of 6 zeta_j rho a a^T with
+    a = (c_j, r x c_j), r from the centre X to the link midpoint: the
+    derivative of the links' force and torque with respect to (U, omega)
+    under Eq. eqn_ladd_bewegtewand, written out from the geometry."""
+    c, w, _ = ref.lattice()
+    c = c.astype(np.float64)
+    nx, ny, nz = o.nx, o.ny, o.nz
+    owner = o.get_state()["owner"].reshape(nz, ny, nx)
+    L = np.array([nx, ny, nz], np.float64)
+    Z = np.zeros((6, 6))
+    zz, yy, xx = np.nonzero(owner == -1)
+    pos = np.stack([xx, yy, zz], axis=1).astype(np.float64)
+    for j in range(1, 19):
+        t = (pos + c[j]).astype(int) % np.array([nx, ny, nz])
+        hit = owner[t[:, 2], t[:, 1], t[:, 0]] == 0
+        r = pos[hit] + 0.5 * c[j] - X
+        r -= L * np.round(r / L)
+        a = np.concatenate([np.broadcast_to(c[j], r.shape), np.cross(r, c[j])], axis=1)
+        Z += 6.0 * w[j] * rho_tot * a.T @ a
+    return Z
+
+
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_first_step_velocity_of_a_sphere_in_fluid_at_rest(implicit):
+    """A sphere centred on a node of a uniform fluid at rest (g = 0, tau = 1):
+    by the cubic symmetry of its links the populations' part of the link
+    force and torque cancels, so the only force is the wall term's -Z V0.
+    Explicit update (reading #8): V1 = V0 - M^-1 Z V0.  Implicit update
+    (reading #18): (M + Z)(V1 - V0) = -Z V0, i.e. V1 = (M + Z)^-1 M V0.
+    Z comes from the link geometry (_link_drag); a light sphere (rho_p = 0.5)
+    makes the two results differ at first order."""
+    n, R, rhop, rho_c = 16, 3.5, 0.5, 0.35
+    o = ref.Oracle(nx=n, ny=n, nz=n, n_particles=1, radius=R, g_br=0.0, particle_density=rhop,
+                   rho_init=(rho_c, rho_c), implicit_update=implicit)
+    V0 = np.array([0.01, -0.005, 0.003, 0.001, 0.002, -0.0015])
+    P = np.zeros((1, 9))
+    P[0, 0:3] = 8.0
+    P[0, 3:9] = V0
+    o.init_fields(np.full((2, n ** 3), rho_c), particles=P)
+    Z = _link_drag(o, P[0, 0:3], 2 * rho_c)
+    m = rhop * 4.0 / 3.0 * np.pi * R ** 3
+    M = np.diag([m, m, m, 0.4 * m * R * R, 0.4 * m * R * R, 0.4 * m * R * R])
+    o.step(1)
+    V1 = o.get_state()["particles"][0, 3:9]
+    want = np.linalg.solve(M + Z, M @ V0) if implicit else V0 - np.linalg.solve(M, Z @ V0)
+    assert np.max(np.abs(Z @ V0)) > 0.05 * np.max(np.abs(M @ V0))  # the wall term matters here
+    assert np.max(np.abs(V1 - want)) < 1e-13, (V1, want)
+
+
+@pytest.mark.parametrize("rhop", [1.0, 3.0])
+def test_implicit_update_conserves_momentum(rhop):
+    """With the implicit update each link's bounce-back population also gets
+    the wall term of the velocity change, so fluid plus particle momentum
+    stays exact, as in the explicit case above (moving, colliding, covering
+    and uncovering spheres, colours, mass correction)."""
+    shape = (20, 18, 16)
+    P = lbinputs.spheres(shape, 3.2, 4, seed=11, min_gap=0.3, vmax=0.04, wmax=0.02)
+    o = ref.Oracle(nx=20, ny=18, nz=16, n_particles=4, radius=3.2, g_br=0.15, color=0.04,
+                   particle_density=rhop, mass_corr_c0=5.0, implicit_update=1)
+    o.set_colors(np.array([0.04, -0.03, 0.0, 0.05]))
+    o.init_fields(lbinputs.mixture(shape, amp=0.05, seed=12), particles=P)
+    p0 = _total_momentum(o)
+    scale = o.observe()["mass"].sum() * 0.04
+    o.step(60)
+    ob = o.observe()
+    assert ob["n_cover"] > 0 and ob["n_uncover"] > 0
+    assert np.all(np.abs(_total_momentum(o) - p0) < 1e-11 * scale)
+
+
+def test_implicit_update_is_for_spheres_only():
+    with pytest.raises(ValueError):
+        ref.Oracle(nx=8, ny=8, nz=8, n_particles=0, aspect=1.5, implicit_update=1)
