@@ -448,6 +448,93 @@ def test_mass_correction_direction():
     assert np.allclose(down2 - 1.0, 2 * (down - 1.0), rtol=1e-12)
 
 
+def masscorr_factors():
+    """Refill densities of the uncovered nodes of one remap with a planted
+    total mass error Delta M^c per component, divided by the same refill
+    without the correction: (measured factors, expected factors) per
+    component.  Expected, from Eq. masscorr with N the number of all lattice
+    sites (fluid and solid) and unequal initial densities so that the ratio
+    sum_c' rho_init^c' / rho_init^c differs between the components:
+    1 - C0 (0.42 + 0.28) / rho_init^c Delta M^c / N."""
+    nx, ny, nz = 14, 13, 12
+    N = nx * ny * nz
+    rho_init = (0.42, 0.28)
+    dM = (0.9, -1.3)          # planted mass errors (current minus initial)
+    c0 = 3.0
+    P = np.zeros((1, 9))
+    P[0, 0:3] = (6.3, 6.6, 5.8)
+    P[0, 3:6] = (0.3, -0.2, 0.25)
+    rho = lbinputs.mixture((nx, ny, nz), rho_init=rho_init, amp=0.02, seed=23)
+    got = {}
+    for corr in (0.0, c0):
+        o = ref.Oracle(nx=nx, ny=ny, nz=nz, n_particles=1, radius=3.4, g_br=0.1, rho_init=rho_init,
+                       particle_density=50.0, mass_corr_c0=corr)
+        o.init_fields(rho, particles=P)
+        o.step(1)
+        st = o.get_state()
+        mass = o.observe()["mass"]
+        st["meta"][1] = mass[0] - dM[0]
+        st["meta"][2] = mass[1] - dM[1]
+        o.set_state(st)
+        unc_before = st["owner"] == 0
+        o.debug_remap()
+        after = o.get_state()
+        unc = np.nonzero(unc_before & (after["owner"] == -1))[0]
+        assert len(unc) > 0
+        got[corr] = np.stack([after["f"][c][:, unc].sum(axis=0) for c in range(2)])
+    measured = got[c0] / got[0.0]
+    expected = [1.0 - c0 * (0.42 + 0.28) / rho_init[c] * dM[c] / N for c in range(2)]
+    return measured, expected
+
+
+def test_mass_correction_magnitude():
+    """Eq. masscorr, magnitude: the refill of every uncovered node is scaled
+    by 1 - C0 (sum_c' rho_init^c' / rho_init^c) Delta M^c / N with N the
+    total number of lattice sites (Sec. IV names it so), per component.  A
+    fluid-node count in place of N, a swapped density ratio or a dropped
+    factor changes the factor by far more than rounding."""
+    measured, expected = masscorr_factors()
+    for c in range(2):
+        assert np.allclose(measured[c], expected[c], rtol=0, atol=1e-13), (c, measured[c][:4], expected[c])
+
+
+def lubrication_cases():
+    """(measured, expected) normal lubrication forces on particle p.
+
+    Expected from the leading-order Reynolds lubrication force between two
+    spheres of radii a1, a2 approaching at normal speed v with surface gap h
+    (e.g. Kim & Karrila, Microhydrodynamics, Ch. 9):
+        F = 6 pi eta (a1 a2 / (a1 + a2))^2 v / h,
+    repulsive; Eq. eqn_ladd_lubrikation adds only the part the lattice does
+    not resolve, 1/h - 1/h_c, with the gap clamped at h_min, and the LB
+    viscosity eta = rho0 c_s^2 (tau - 1/2) (rho0 = 1) at the mean tau of the
+    two components."""
+    out = []
+    hc, hmin = 2.0 / 3.0, 0.1
+    for R, tau, gap, v in ((5.0, (0.8, 1.4), 0.3, 0.01), (5.0, (0.8, 1.4), 0.05, 0.01),
+                           (3.0, (1.0, 1.0), 0.45, 0.02), (7.5, (0.6, 0.9), 0.2, 0.004)):
+        eta = CS2 * (0.5 * (tau[0] + tau[1]) - 0.5)
+        a_red = R * R / (R + R)
+        h = max(gap, hmin)
+        want = 6.0 * np.pi * eta * a_red ** 2 * v * (1.0 / h - 1.0 / hc)
+        # p on +x of q, moving towards it at speed v
+        Fp = ref.pair_force((2 * R + gap, 0, 0), (0, 0, 0), (-v, 0, 0), (0, 0, 0), nx=64, ny=64, nz=64,
+                            radius=R, tau=tau, k_hertz=0.0, lub_cut=hc, lub_min=hmin)
+        out.append((Fp[0], want))
+    return out
+
+
+def test_lubrication_magnitude():
+    """Eq. eqn_ladd_lubrikation, magnitude: the oracle's force equals the
+    Reynolds lubrication force of two equal spheres (reduced radius R / 2)
+    above the cut-off correction, at four radii / viscosities / gaps, one of
+    them clamped.  A 3 pi for 6 pi, R^2 for R^4 / (2R)^2 or a single
+    component's tau in the viscosity fails it."""
+    for got, want in lubrication_cases():
+        assert want > 0.0
+        assert abs(got - want) < 1e-12 * want, (got, want)
+
+
 # ------------------------------------------------------ colour and symmetry
 def _interface_particle(color, swap=False):
     n = 16
