@@ -93,8 +93,9 @@ static __global__ void k_flags_from_owner(const BoxDev* __restrict__ boxes, int 
 }
 
 // f = f^eq(rho, u) on fluid nodes in the even-step layout (own slots);
-// rho from a field [2][N] or from SplitMix64 noise; u from a field [3][N]
-// or zero.  The density ring slot rc gets rho on fluid nodes, 0 elsewhere.
+// rho from a field [2][N] (canonical order) or from SplitMix64 noise; u
+// from a field [3][N] or zero.  The density ring slot rc ([N][2] pairs)
+// gets rho on fluid nodes, 0 elsewhere.
 template <class P>
 static __global__ void k_init_pop(const BoxDev* __restrict__ boxes, int b, const double* __restrict__ rho_field,
                            const double* __restrict__ u_field, uint64_t s_red, uint64_t s_blue, double noise,
@@ -106,8 +107,8 @@ static __global__ void k_init_pop(const BoxDev* __restrict__ boxes, int b, const
     double m0 = 0.0, m1 = 0.0;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
         if (B.flags[n] & FL_SOLID) {
-            rcur[n] = R(0);
-            rcur[(size_t)B.N + n] = R(0);
+            rcur[2 * (size_t)n] = R(0);
+            rcur[2 * (size_t)n + 1] = R(0);
             continue;
         }
         double rho[2];
@@ -134,7 +135,7 @@ static __global__ void k_init_pop(const BoxDev* __restrict__ boxes, int b, const
             // the rest population: rho minus the 18 stored values, kept only
             // as part of the density
             sent += feq_rest<R>(r, ux, uy, uz) + resid;
-            rcur[(size_t)c * B.N + n] = sent;
+            rcur[2 * (size_t)n + c] = sent;
             if (c == 0) m0 += (double)sent;
             else m1 += (double)sent;
         }
@@ -167,7 +168,7 @@ __device__ __forceinline__ double rest_of(const BoxDev& B, const Pop<P>& pop, in
     double s = 0.0;
 #pragma unroll
     for (int i = 1; i < 19; i++) s += (double)load_node_pop<P>(B, pop, par, c, i, n);
-    return (double)reinterpret_cast<const R*>(B.rho[rc])[(size_t)c * B.N + n] - s;
+    return (double)reinterpret_cast<const R*>(B.rho[rc])[2 * (size_t)n + c] - s;
 }
 
 template <class P>
@@ -211,13 +212,13 @@ static __global__ void k_rho_from_pop(const BoxDev* __restrict__ boxes, int b, i
         R r[2] = {R(0), R(0)};
         if (!(B.flags[n] & FL_SOLID))
             for (int c = 0; c < 2; c++) {
-                if (rsrc) r[c] = rsrc[(size_t)c * B.N + n];
+                if (rsrc) r[c] = rsrc[2 * (size_t)n + c];
                 else
                     for (int i = 0; i < 19; i++) r[c] += load_node_pop<P>(B, pop, par, c, i, n);
             }
         if (rcur) {
-            rcur[n] = r[0];
-            rcur[(size_t)B.N + n] = r[1];
+            rcur[2 * (size_t)n] = r[0];
+            rcur[2 * (size_t)n + 1] = r[1];
         }
         if (out) {
             out[n] = (double)r[0];
@@ -260,7 +261,7 @@ static __global__ void __launch_bounds__(256) k_obs_partial(const BoxDev* __rest
         }
         double rt = 0, jt[3] = {0, 0, 0};
         for (int c = 0; c < 2; c++) {
-            const double r = (double)rho[(size_t)c * B.N + n];
+            const double r = (double)rho[2 * (size_t)n + c];
             v[c] += r;
             rt += r;
             for (int i = 1; i < 19; i++) {

@@ -63,9 +63,9 @@ struct PartOf<double> {
 struct BoxDev {
     int nx, ny, nz;
     int N;                      // nx*ny*nz (< 2^31)
-    void* f;                    // populations (layout: StorePolicy)
-    float* f0;                  // rest slot for 16-bit deviation storage
-    void* rho[3];               // density ring: [2][N] of real each
+    void* f;                    // populations (layout: Pop, component pairs)
+    float* f0;                  // rest slot for 16-bit deviation storage, [N][2]
+    void* rho[3];               // density ring: [N][2] of real each (rho^r, rho^b pairs)
     uint8_t* flags;             // [N]
     int32_t* owner;             // [N] global particle index, -1 fluid, -2 wall
     int32_t* evmark;            // [N] old owner + 3 while a remap is applied, else 0
@@ -167,51 +167,82 @@ __device__ __forceinline__ R feq_rest(R rho, R ux, R uy, R uz) {
 }
 
 // ----------------------------------------------------- storage policies
-// Populations of component c, direction i at node n.
-//   FP64 / FP32: one array [2][19][N] of double / float.
-//   FP16 / BF16 deviations: [2][18][N] 16-bit values d = f/zeta_i - rho_ref^c
-//   for i = 1..18, and the rest population in a separate FP32 array [2][N].
+// Populations of component c, direction i at node n.  The two components
+// of one direction and node sit side by side (a pair), so one 8-byte
+// (FP32), 16-byte (FP64) or 4-byte (16-bit) access moves both:
+//   FP64 / FP32: one array [19][N][2] of double / float.
+//   FP16 / BF16 deviations: [18][N][2] 16-bit values d = f/zeta_i - rho_ref^c
+//   for i = 1..18, and the rest population in a separate FP32 array [N][2].
 // The step keeps only the 18 moving populations: the density field holds
 // rho^c of every fluid node, and f_0 = rho^c - sum_{i>=1} f_i.  The rest
 // slot (i = 0) only carries an imported f_0 into the density field.
+// The density ring is [N][2] of the real type (FP32 for the 16-bit forms).
 struct P64 {
     using real = double;
     using st = double;
+    using st2 = double2;
+    using real2 = double2;
     static constexpr bool dev = false;
     static constexpr int id = 0;
 };
 struct P32 {
     using real = float;
     using st = float;
+    using st2 = float2;
+    using real2 = float2;
     static constexpr bool dev = false;
     static constexpr int id = 1;
 };
 struct P16 {
     using real = float;
     using st = __half;
+    using st2 = __half2;
+    using real2 = float2;
     static constexpr bool dev = true;
     static constexpr int id = 2;
 };
 struct PB16 {
     using real = float;
     using st = __nv_bfloat16;
+    using st2 = __nv_bfloat162;
+    using real2 = float2;
     static constexpr bool dev = true;
     static constexpr int id = 3;
 };
 
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
 template <class S>
 __device__ __forceinline__ S from_f(float v);
 template <>
 __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <class S2>
+__device__ __forceinline__ S2 from_f2(float a, float b);
+template <>
+__device__ __forceinline__ __half2 from_f2<__half2>(float a, float b) { return __floats2half2_rn(a, b); }
+template <>
+__device__ __forceinline__ __nv_bfloat162 from_f2<__nv_bfloat162>(float a, float b) {
+    return __floats2bfloat162_rn(a, b);
+}
+
+// (red, blue) pair of the density ring or of a population slot
+template <class V2, class R>
+__device__ __forceinline__ V2 mk2(R a, R b) {
+    V2 v;
+    v.x = a;
+    v.y = b;
+    return v;
+}
 
 template <class P>
 struct Pop {
     using R = typename P::real;
     using S = typename P::st;
+    using S2 = typename P::st2;
     S* base;
     float* f0;
     size_t N;
@@ -238,35 +269,38 @@ struct Pop {
     __device__ __forceinline__ S f_to_dev(int c, int i, float v) const {
         return from_f<S>(fmaf(v, 1.0f / wgt<float>(i), -(float)ref[c]));
     }
+    // the pair (red, blue) of direction i (>= 1 for deviation storage) at node n
+    __device__ __forceinline__ S2* pair(int i, size_t n) const {
+        return reinterpret_cast<S2*>(base) + (size_t)(P::dev ? i - 1 : i) * N + n;
+    }
+    // component c of the pair of direction i at node n
+    __device__ __forceinline__ S* at(int c, int i, size_t n) const {
+        return base + ((size_t)(P::dev ? i - 1 : i) * N + n) * 2 + c;
+    }
     __device__ __forceinline__ R load(int c, int i, int n) const {
         if constexpr (P::dev) {
-            if (i == 0) return f0[(size_t)c * N + n];
-            return dev_to_f(c, i, base[((size_t)c * 18 + (i - 1)) * N + n]);
+            if (i == 0) return f0[(size_t)n * 2 + c];
+            return dev_to_f(c, i, *at(c, i, n));
         } else {
-            return base[((size_t)c * 19 + i) * N + n];
+            return *at(c, i, n);
         }
     }
     // stores v, returns the value the next load will see
     __device__ __forceinline__ R store(int c, int i, int n, R v) const {
         if constexpr (P::dev) {
             if (i == 0) {
-                f0[(size_t)c * N + n] = v;
+                f0[(size_t)n * 2 + c] = v;
                 return v;
             }
             const S q = f_to_dev(c, i, v);
-            base[((size_t)c * 18 + (i - 1)) * N + n] = q;
+            *at(c, i, n) = q;
             return dev_to_f(c, i, q);
         } else {
-            base[((size_t)c * 19 + i) * N + n] = v;
+            *at(c, i, n) = v;
             return v;
         }
     }
-    // array of direction i (>= 1 for deviation storage) of component c
-    __device__ __forceinline__ S* dir(int c, int i) const {
-        if constexpr (P::dev) return base + ((size_t)c * 18 + (i - 1)) * N;
-        else return base + ((size_t)c * 19 + i) * N;
-    }
-    // load / store through a pointer into the array of direction i (or of
+    // load / store through a pointer to one component (direction i or
     // opp(i): opposite directions share weight and reference density)
     __device__ __forceinline__ R ld(const S* p, int c, int i) const {
         if constexpr (P::dev) return dev_to_f(c, i, *p);
@@ -282,11 +316,54 @@ struct Pop {
             return v;
         }
     }
+    // both components through a pair pointer
+    __device__ __forceinline__ void ld2(const S2* p, int i, R& a, R& b) const {
+        const S2 v = *p;
+        if constexpr (P::dev) {
+            const float2 d = to_f2(v);
+            a = fmaf(wgt<float>(i), d.x, zr[0][is_axis(i) ? 0 : 1]);
+            b = fmaf(wgt<float>(i), d.y, zr[1][is_axis(i) ? 0 : 1]);
+        } else {
+            a = v.x;
+            b = v.y;
+        }
+    }
+    // stores (a, b); qa, qb: the values the next load will see
+    __device__ __forceinline__ void st2(S2* p, int i, R a, R b, R& qa, R& qb) const {
+        if constexpr (P::dev) {
+            const S2 q = from_f2<S2>(fmaf(a, 1.0f / wgt<float>(i), -(float)ref[0]),
+                                     fmaf(b, 1.0f / wgt<float>(i), -(float)ref[1]));
+            *p = q;
+            const float2 d = to_f2(q);
+            qa = fmaf(wgt<float>(i), d.x, zr[0][is_axis(i) ? 0 : 1]);
+            qb = fmaf(wgt<float>(i), d.y, zr[1][is_axis(i) ? 0 : 1]);
+        } else {
+            *p = mk2<S2>(a, b);
+            qa = a;
+            qb = b;
+        }
+    }
 };
 
 template <class P>
 __host__ __device__ constexpr size_t pop_bytes(size_t N) {
     return P::dev ? (size_t)2 * 18 * N * 2 : (size_t)2 * 19 * N * sizeof(typename P::st);
+}
+
+// density ring access: the pair (rho^r, rho^b) of node n
+template <class R>
+struct Real2;
+template <>
+struct Real2<float> {
+    using type = float2;
+};
+template <>
+struct Real2<double> {
+    using type = double2;
+};
+template <class R>
+__device__ __forceinline__ typename Real2<R>::type* rpair(void* ring) {
+    return reinterpret_cast<typename Real2<R>::type*>(ring);
 }
 
 // ------------------------------------------------------------ helpers

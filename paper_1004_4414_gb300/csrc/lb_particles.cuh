@@ -378,7 +378,7 @@ __device__ Refill<R> refill_of(const BoxDev& B, const Shared& sh, int n, int q, 
         for (int i = 1; i < 19; i++) {
             const int m = nbr_index(B, n, cx(i), cy(i), cz(i));
             if (!old_solid(B, m)) {
-                sum += rcur[(size_t)c * B.N + m];
+                sum += rcur[2 * (size_t)m + c];
                 cnt++;
             }
         }
@@ -491,11 +491,11 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
         const int w = ev.x;
         R* rcur = reinterpret_cast<R*>(B.rho[rc]);
         if (ev.z == OWN_FLUID) {
-            rcur[w] = R(0);
-            rcur[(size_t)B.N + w] = R(0);
+            rcur[2 * (size_t)w] = R(0);
+            rcur[2 * (size_t)w + 1] = R(0);
         } else if (ev.w == OWN_FLUID) {
-            rcur[w] = (R)sh.ev_rho[(size_t)e * 2 + 0];
-            rcur[(size_t)B.N + w] = (R)sh.ev_rho[(size_t)e * 2 + 1];
+            rcur[2 * (size_t)w] = (R)sh.ev_rho[(size_t)e * 2 + 0];
+            rcur[2 * (size_t)w + 1] = (R)sh.ev_rho[(size_t)e * 2 + 1];
         }
         B.evmark[w] = 0;
         // the particles whose shell lists this event can change: the old and
@@ -515,8 +515,8 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
         auto update = [&](int n) {
             shell_update(B, n);
             if (B.flags[n] == FL_SOLID) {
-                rcur[n] = R(0);
-                rcur[(size_t)B.N + n] = R(0);
+                rcur[2 * (size_t)n] = R(0);
+                rcur[2 * (size_t)n + 1] = R(0);
             }
         };
         update(w);
@@ -581,15 +581,15 @@ static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* _
                 if (!((fmask >> i) & 1u)) continue;
                 const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) +
                               (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) + (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
-                s0 += rcur[m];
-                s1 += rcur[N + m];
+                s0 += rcur[2 * (size_t)m];
+                s1 += rcur[2 * (size_t)m + 1];
             }
             const R cnt = (R)__popc(fmask);
             R r0 = s0 / cnt, r1 = s1 / cnt;
             if (col > R(0)) r0 += col;
             else if (col < R(0)) r1 -= col;
-            rcur[n] = r0;
-            rcur[N + n] = r1;
+            rcur[2 * (size_t)n] = r0;
+            rcur[2 * (size_t)n + 1] = r1;
         }
         return;
     }
@@ -609,8 +609,8 @@ static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* _
             const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) + (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) +
                           (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
             if (!(flags[m] & FL_SOLID)) {
-                s0 += rcur[m];
-                s1 += rcur[N + m];
+                s0 += rcur[2 * (size_t)m];
+                s1 += rcur[2 * (size_t)m + 1];
                 cnt++;
                 fmask |= 1u << i;
             }
@@ -619,8 +619,8 @@ static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* _
         R r0 = s0 / (R)cnt, r1 = s1 / (R)cnt;
         if (col > R(0)) r0 += col;
         else if (col < R(0)) r1 -= col;
-        rcur[n] = r0;
-        rcur[N + n] = r1;
+        rcur[2 * (size_t)n] = r0;
+        rcur[2 * (size_t)n + 1] = r1;
     };
     // FP32 prefilter only (every shell node of p lies within R); the shell
     // flag and the owner decide.  No FP64 here: it is slow on this GPU.
@@ -717,8 +717,10 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const auto& ps = part_ptr<R>(sh)[p];
     const size_t N = (size_t)B.N;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
-    const R* __restrict__ rcur = reinterpret_cast<const R*>(B.rho[rc]);
-    R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);
+    using R2 = typename Real2<R>::type;
+    using S2 = typename P::st2;
+    const R2* __restrict__ rcur2 = rpair<R>(B.rho[rc]);
+    R2* __restrict__ rnext2 = rpair<R>(B.rho[rn]);
     double* __restrict__ mass_acc = B.mass_acc;
     const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
     const R wax = (R)B.scw_axis, wdg = (R)B.scw_diag;
@@ -739,10 +741,10 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const int nitems = 18 * ns;
     for (int k0 = threadIdx.x; k0 < nitems; k0 += U * COUPLE_THREADS) {
         int iu[U], mu[U];
-        S* pu0[U];
-        S* pu1[U];
-        ptrdiff_t mv[U];  // elements from the slot read to the slot written
-        R fsu0[U], fsu1[U], rru[U], rbu[U];
+        S2* pu[U];
+        ptrdiff_t mv[U];  // pairs from the slot read to the slot written
+        S2 rawu[U];
+        R2 rru[U];
         int4 eu[U];
         bool ok[U];
 #pragma unroll
@@ -761,24 +763,20 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
             ok[u] = ok[u] && ((eu[u].y >> i) & 1);  // s + c_i fluid: a link
             mu[u] = 0;
             mv[u] = 0;
-            pu0[u] = pu1[u] = nullptr;
-            fsu0[u] = fsu1[u] = rru[u] = rbu[u] = R(0);
+            pu[u] = nullptr;
             if (ok[u]) {
                 const int s = eu[u].x;
                 const int gx = eu[u].z & 0xffff, gy = (int)((unsigned)eu[u].z >> 16), gz = eu[u].w;
                 const int m = wrap1(gx + kC[i][0], nx) + nx * (wrap1(gy + kC[i][1], ny) + ny * wrap1(gz + kC[i][2], nz));
                 mu[u] = m;
-                // the reflected f*_j belongs after an even step in slot
+                // the reflected pair f*_j belongs after an even step in slot
                 // j = opp(i) of s, after an odd step in slot opp(j) = i of
                 // m; unreflected it sits in the other of the two
                 const bool at_s = (par == 0) == (reflect != 0);
-                pu0[u] = at_s ? pop.dir(0, opp(i)) + s : pop.dir(0, i) + m;
-                pu1[u] = at_s ? pop.dir(1, opp(i)) + s : pop.dir(1, i) + m;
-                if (!reflect) mv[u] = at_s ? (pop.dir(0, i) + m) - pu0[u] : (pop.dir(0, opp(i)) + s) - pu0[u];
-                fsu0[u] = pop.ld(pu0[u], 0, i);
-                fsu1[u] = pop.ld(pu1[u], 1, i);
-                rru[u] = __ldg(rcur + m);
-                rbu[u] = __ldg(rcur + N + m);
+                pu[u] = at_s ? pop.pair(opp(i), s) : pop.pair(i, m);
+                if (!reflect) mv[u] = at_s ? pop.pair(i, m) - pu[u] : pop.pair(opp(i), s) - pu[u];
+                rawu[u] = *pu[u];
+                rru[u] = __ldg(rcur2 + m);
             }
         }
 #pragma unroll
@@ -793,28 +791,44 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
             const R r2 = mimg_r<R>((R)gz - X2, Lz) + R(0.5) * (R)iz;
             const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
             const R cu6 = -R(6) * (i <= 6 ? wgt<R>(1) : wgt<R>(7)) * (us0 * (R)ix + us1 * (R)iy + us2 * (R)iz);
-            R mag = R(0);
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const R fs = c == 0 ? fsu0[u] : fsu1[u];
-                const R wall = cu6 * (c == 0 ? rru[u] : rbu[u]);
-                if (wall != R(0) || !reflect) {
-                    S* const at = c == 0 ? pu0[u] : pu1[u];
-                    R dr;
-                    if (P::dev && wall == R(0)) {
-                        at[mv[u]] = *at;
-                        dr = R(0);
-                    } else {
-                        const R b = fs - wall;
-                        const R q = pop.st(at + mv[u], c, i, b);
-                        dr = P::dev ? b - fs : q - fs;
-                    }
-                    atomicAdd(&rnext[(size_t)c * N + m], reflect ? dr : dr + fs);
-                    if (c == 0) dm0 += dr;
-                    else dm1 += dr;
-                }
-                mag += R(2) * fs - wall;
+            const S2 raw = rawu[u];
+            R fs[2], wall[2], dr[2] = {R(0), R(0)};
+            if constexpr (P::dev) {
+                fs[0] = pop.dev_to_f(0, i, raw.x);
+                fs[1] = pop.dev_to_f(1, i, raw.y);
+            } else {
+                fs[0] = raw.x;
+                fs[1] = raw.y;
             }
+            wall[0] = cu6 * rru[u].x;
+            wall[1] = cu6 * rru[u].y;
+            if (cu6 != R(0) || !reflect) {
+                S2 q = raw;
+                if constexpr (P::dev) {
+                    // a value without a wall term moves bit for bit; the
+                    // density field takes the exact change b - f* of a
+                    // re-encoded one (its rounding lands in the rest
+                    // population, which is rho minus the 18 stored values)
+                    if (wall[0] != R(0)) {
+                        q.x = pop.f_to_dev(0, i, fs[0] - wall[0]);
+                        dr[0] = -wall[0];
+                    }
+                    if (wall[1] != R(0)) {
+                        q.y = pop.f_to_dev(1, i, fs[1] - wall[1]);
+                        dr[1] = -wall[1];
+                    }
+                } else {
+                    q.x = fs[0] - wall[0];
+                    q.y = fs[1] - wall[1];
+                    dr[0] = q.x - fs[0];
+                    dr[1] = q.y - fs[1];
+                }
+                pu[u][mv[u]] = q;
+                red_add2<R>(rnext2 + m, reflect ? dr[0] : dr[0] + fs[0], reflect ? dr[1] : dr[1] + fs[1]);
+                dm0 += dr[0];
+                dm1 += dr[1];
+            }
+            const R mag = (R(2) * fs[0] - wall[0]) + (R(2) * fs[1] - wall[1]);
             const R F0 = -mag * (R)ix, F1 = -mag * (R)iy, F2 = -mag * (R)iz;
             acc[0] += F0;
             acc[1] += F1;
@@ -834,8 +848,9 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
         for (int i = 1; i < 19; i++) {
             const int m = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
             const R w = is_axis(i) ? wax : wdg;
-            const R pr = w * psi_of<R>(__ldg(rcur + m), rho0, irho0);
-            const R pb = w * psi_of<R>(__ldg(rcur + N + m), rho0, irho0);
+            const R2 rm = __ldg(rcur2 + m);
+            const R pr = w * psi_of<R>(rm.x, rho0, irho0);
+            const R pb = w * psi_of<R>(rm.y, rho0, irho0);
             sr0 += pr * (R)cx(i);
             sr1 += pr * (R)cy(i);
             sr2 += pr * (R)cz(i);
@@ -844,7 +859,8 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
             sb2 += pb * (R)cz(i);
         }
         const R rs0 = mimg_r<R>((R)gx - X0, Lx), rs1 = mimg_r<R>((R)gy - X1, Ly), rs2 = mimg_r<R>((R)gz - X2, Lz);
-        const R psr = psi_of<R>(__ldg(rcur + s), rho0, irho0), psb = psi_of<R>(__ldg(rcur + N + s), rho0, irho0);
+        const R2 rs = __ldg(rcur2 + s);
+        const R psr = psi_of<R>(rs.x, rho0, irho0), psb = psi_of<R>(rs.y, rho0, irho0);
         const R F0 = -g * (psr * sb0 + psb * sr0), F1 = -g * (psr * sb1 + psb * sr1), F2 = -g * (psr * sb2 + psb * sr2);
         acc[0] += F0;
         acc[1] += F1;
@@ -890,13 +906,13 @@ static __global__ void k_wall_shell(const BoxDev* __restrict__ boxes, int b, int
         for (int i = 1; i < 19; i++) {
             const int m = nbr_index(B, n, cx(i), cy(i), cz(i));
             if (!(B.flags[m] & FL_SOLID)) {
-                s0 += rcur[m];
-                s1 += rcur[(size_t)B.N + m];
+                s0 += rcur[2 * (size_t)m];
+                s1 += rcur[2 * (size_t)m + 1];
                 cnt++;
             }
         }
-        rcur[n] = s0 / (R)cnt;
-        rcur[(size_t)B.N + n] = s1 / (R)cnt;
+        rcur[2 * (size_t)n] = s0 / (R)cnt;
+        rcur[2 * (size_t)n + 1] = s1 / (R)cnt;
     }
 }
 

@@ -21,6 +21,9 @@
 //     never depend on the status of a neighbour.  Each slot is read once and
 //     written once per step; neighbour offsets are wrap-aware and computed
 //     once per thread.
+//   * The two components of a direction and node form one pair in memory
+//     (8 bytes in FP32, 4 in 16-bit storage), so one load or store moves
+//     both: a warp moves 32 consecutive pairs of one direction per access.
 //   * Only the 18 moving populations are stored.  A node's rho^c is the
 //     density field of the current step (the window fetches it for Psi
 //     anyway), and its rest population f_0 = rho^c - sum_{i>=1} f_i stays at
@@ -87,6 +90,16 @@ template <class R>
 __device__ __forceinline__ void red_add(R* p, R v) {
     atomicAdd(p, v);
 }
+// both components of a density-ring pair (one vector reduction in FP32)
+template <class R>
+__device__ __forceinline__ void red_add2(typename Real2<R>::type* p, R a, R b) {
+    if constexpr (sizeof(R) == 4) {
+        atomicAdd(p, make_float2(a, b));
+    } else {
+        atomicAdd(&p->x, a);
+        atomicAdd(&p->y, b);
+    }
+}
 
 // Destination groups of the density scatter: (dy, dz) of a direction.
 //   g: 0 (0,0) 1 (+1,0) 2 (-1,0) 3 (0,+1) 4 (0,-1) 5 (+1,+1) 6 (-1,-1)
@@ -143,9 +156,12 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
     const BoxDev& B = boxes[T.box];
     const int nx = B.nx, ny = B.ny, nz = B.nz, N = B.N;
     const int nxy = nx * ny;
-    const R* __restrict__ rcur = reinterpret_cast<const R*>(B.rho[rc]);
-    R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);
-    R* __restrict__ rzero = reinterpret_cast<R*>(B.rho[rz]);
+    using R2 = typename Real2<R>::type;
+    using S2 = typename P::st2;
+    const R2* __restrict__ rcur = rpair<R>(B.rho[rc]);
+    R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);  // component c of node m: rnext[2 m + c]
+    R2* __restrict__ rnext2 = rpair<R>(B.rho[rn]);
+    R2* __restrict__ rzero = rpair<R>(B.rho[rz]);
     const uint8_t* __restrict__ gflags = B.flags;
     const Pop<P> pop(B);
     const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
@@ -202,14 +218,16 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
         const int pb = nxy * gz;
         if (active) {
             const int n = pb + nxyc;
-            v.a0 = rcur[n];
-            v.a1 = rcur[(size_t)N + n];
+            const R2 r = rcur[n];
+            v.a0 = r.x;
+            v.a1 = r.y;
             v.af = gflags[n];
         }
         if (tid < nring) {
             const int n = pb + ring_xy;
-            v.b0 = rcur[n];
-            v.b1 = rcur[(size_t)N + n];
+            const R2 r = rcur[n];
+            v.b0 = r.x;
+            v.b1 = r.y;
             v.bf = gflags[n];
         }
         return v;
@@ -283,13 +301,10 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     smask |= (unsigned)(FLG(slot_dz(cz(i)), ly + 1 + cy(i), lx + 1 + cx(i)) & FL_SOLID) << i;
             }
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
-#pragma unroll
-                for (int i = 1; i < 19; i++) {
-                    // even steps: own slot i; odd steps: slot opp(i) of x - c_i
-                    const S* p = PAR == 0 ? pop.dir(c, i) + n : pop.dir(c, opp(i)) + (n + off(opp(i)));
-                    f[c][i] = pop.ld(p, c, i);
-                }
+            for (int i = 1; i < 19; i++) {
+                // even steps: own slot i; odd steps: slot opp(i) of x - c_i
+                const S2* p = PAR == 0 ? pop.pair(i, n) : pop.pair(opp(i), n + off(opp(i)));
+                pop.ld2(p, i, f[0][i], f[1][i]);
             }
             // rho^c is the density field (the sum of the values the previous
             // step sent here); the rest population is rho^c minus the 18
@@ -357,120 +372,140 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
         }
 
         const unsigned FULL = 0xffffffffu;
-        // Each component's density scatter is finished inside its own
-        // iteration, so its partial sums do not stay live across both.
+        // per-group partial sums of the values this node sends, per component
+        // (mid: no x move; up / dn: to x + 1 / x - 1); after the x shuffle
+        // mid[c][g] holds everything that arrives in this column
+        R mid[2][9], up[2][5], dn[2][5];
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            // per-group partial sums of the values this node sends (mid: no x
-            // move; up / dn: to x + 1 / x - 1); after the x shuffle mid[g]
-            // holds everything that arrives in this column
-            R mid[9], up[5], dn[5];
 #pragma unroll
-            for (int q = 0; q < 9; q++) mid[q] = R(0);
+            for (int q = 0; q < 9; q++) mid[c][q] = R(0);
 #pragma unroll
-            for (int q = 0; q < 5; q++) up[q] = dn[q] = R(0);
-            if (fluid) {
-                const R itc = T1 ? R(1) : (c == 0 ? itau0 : itau1);
-                const R omt = T1 ? R(0) : R(1) - itc;
-                const R uu = ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c];
-                const R a0 = R(1) - R(1.5) * uu;
-                const R rw1 = rho[c] * wgt<R>(1), rw7 = rho[c] * wgt<R>(7);
-                R resid = R(0), fe_sum = R(0), self = R(0);
-                // store f*_j where the next step reads it.  Stream target
-                // y = x + c_j fluid: even steps slot opp(j) of x, odd steps
-                // slot j of y.  Target solid (bounce-back, f_opp(j) of x at
-                // t+1): even steps slot j of y, which the odd step at x reads
-                // for direction opp(j); odd steps slot opp(j) of x.
-                auto send = [&](auto JC, R fs) {
-                    constexpr int j = decltype(JC)::value;
-                    const bool solid = BB && ((smask >> j) & 1u);
-                    S* p;
-                    if (PAR == 0) p = solid ? pop.dir(c, j) + (n + off(j)) : pop.dir(c, opp(j)) + n;
-                    else p = solid ? pop.dir(c, opp(j)) + n : pop.dir(c, j) + (n + off(j));
-                    const R q = pop.st(p, c, j, fs);
-                    if constexpr (P::dev) resid += fs - q;
-                    const R qf = solid ? R(0) : q;
-                    self += solid ? q : R(0);
-                    constexpr int gq = grp_of(j);
-                    if (cx(j) == 0) mid[gq] += qf;
-                    else if (cx(j) > 0) up[gq] += qf;
-                    else dn[gq] += qf;
-                };
-                // equilibria of opposite pairs share their even part:
-                // f^eq_(+/-) = zeta rho (E +/- O), E = 1 - 3/2 u^2 + 9/2 cu^2,
-                // O = cu (3 + 9/2 cu^2 - 9/2 u^2)
-                auto pair = [&](auto JC, R cu) {
-                    constexpr int j = decltype(JC)::value;
-                    const R rw = is_axis(j) ? rw1 : rw7;
-                    const R cu2 = cu * cu;
-                    const R E = a0 + R(4.5) * cu2;
-                    const R O = cu * (R(3) + R(4.5) * cu2 - R(4.5) * uu);
-                    const R fep = rw * (E + O), fem = rw * (E - O);
-                    fe_sum += fep + fem;
-                    if constexpr (T1) {
-                        send(std::integral_constant<int, j>{}, fep);
-                        send(std::integral_constant<int, opp(j)>{}, fem);
-                    } else {
-                        send(std::integral_constant<int, j>{}, omt * f[c][j] + itc * fep);
-                        send(std::integral_constant<int, opp(j)>{}, omt * f[c][opp(j)] + itc * fem);
-                    }
-                };
-                const R Ux = ux[c], Uy = uy[c], Uz = uz[c];
-                pair(std::integral_constant<int, 1>{}, Ux);
-                pair(std::integral_constant<int, 3>{}, Uy);
-                pair(std::integral_constant<int, 5>{}, Uz);
-                pair(std::integral_constant<int, 7>{}, Ux + Uy);
-                pair(std::integral_constant<int, 9>{}, Ux - Uy);
-                pair(std::integral_constant<int, 11>{}, Ux + Uz);
-                pair(std::integral_constant<int, 13>{}, Ux - Uz);
-                pair(std::integral_constant<int, 15>{}, Uy + Uz);
-                pair(std::integral_constant<int, 17>{}, Uy - Uz);
-                // rest population: its equilibrium is rho minus the other 18
-                // (equal to Eq. Equil in exact arithmetic), and in deviation
-                // storage it absorbs the rounding of the 18 stored values, so
-                // node mass is kept to FP32 rounding.  It stays at the node and
-                // enters only the density field: it is not stored.
-                const R q0 = (T1 ? R(0) : omt * f[c][0]) + itc * (rho[c] - fe_sum) + resid;
-                mid[0] += q0 + self;
-                // the 18 stored values and q0 sum to rho^c: the collision
-                // conserves mass
-                if (c == 0) msum0 += rho[0];
-                else msum1 += rho[1];
+            for (int q = 0; q < 5; q++) up[c][q] = dn[c][q] = R(0);
+        }
+        if (fluid) {
+            R itc[2], omt[2], uu[2], a0[2], rw1[2], rw7[2], resid[2], fe_sum[2], self[2];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                itc[c] = T1 ? R(1) : (c == 0 ? itau0 : itau1);
+                omt[c] = T1 ? R(0) : R(1) - itc[c];
+                uu[c] = ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c];
+                a0[c] = R(1) - R(1.5) * uu[c];
+                rw1[c] = rho[c] * wgt<R>(1);
+                rw7[c] = rho[c] * wgt<R>(7);
+                resid[c] = fe_sum[c] = self[c] = R(0);
             }
+            // store the pair f*_j (red, blue) where the next step reads it.
+            // Stream target y = x + c_j fluid: even steps slot opp(j) of x,
+            // odd steps slot j of y.  Target solid (bounce-back, f_opp(j) of
+            // x at t+1): even steps slot j of y, which the odd step at x
+            // reads for direction opp(j); odd steps slot opp(j) of x.
+            auto send = [&](auto JC, R fs0, R fs1) {
+                constexpr int j = decltype(JC)::value;
+                const bool solid = BB && ((smask >> j) & 1u);
+                S2* p;
+                if (PAR == 0) p = solid ? pop.pair(j, n + off(j)) : pop.pair(opp(j), n);
+                else p = solid ? pop.pair(opp(j), n) : pop.pair(j, n + off(j));
+                R q[2];
+                pop.st2(p, j, fs0, fs1, q[0], q[1]);
+                constexpr int gq = grp_of(j);
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    if constexpr (P::dev) resid[c] += (c == 0 ? fs0 : fs1) - q[c];
+                    const R qf = solid ? R(0) : q[c];
+                    self[c] += solid ? q[c] : R(0);
+                    if (cx(j) == 0) mid[c][gq] += qf;
+                    else if (cx(j) > 0) up[c][gq] += qf;
+                    else dn[c][gq] += qf;
+                }
+            };
+            // equilibria of opposite pairs share their even part:
+            // f^eq_(+/-) = zeta rho (E +/- O), E = 1 - 3/2 u^2 + 9/2 cu^2,
+            // O = cu (3 + 9/2 cu^2 - 9/2 u^2)
+            auto pair = [&](auto JC, R cu0, R cu1) {
+                constexpr int j = decltype(JC)::value;
+                R fp[2], fm[2];
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const R cu = c == 0 ? cu0 : cu1;
+                    const R rw = is_axis(j) ? rw1[c] : rw7[c];
+                    const R cu2 = cu * cu;
+                    const R E = a0[c] + R(4.5) * cu2;
+                    const R O = cu * (R(3) + R(4.5) * cu2 - R(4.5) * uu[c]);
+                    const R fep = rw * (E + O), fem = rw * (E - O);
+                    fe_sum[c] += fep + fem;
+                    if constexpr (T1) {
+                        fp[c] = fep;
+                        fm[c] = fem;
+                    } else {
+                        fp[c] = omt[c] * f[c][j] + itc[c] * fep;
+                        fm[c] = omt[c] * f[c][opp(j)] + itc[c] * fem;
+                    }
+                }
+                send(std::integral_constant<int, j>{}, fp[0], fp[1]);
+                send(std::integral_constant<int, opp(j)>{}, fm[0], fm[1]);
+            };
+            pair(std::integral_constant<int, 1>{}, ux[0], ux[1]);
+            pair(std::integral_constant<int, 3>{}, uy[0], uy[1]);
+            pair(std::integral_constant<int, 5>{}, uz[0], uz[1]);
+            pair(std::integral_constant<int, 7>{}, ux[0] + uy[0], ux[1] + uy[1]);
+            pair(std::integral_constant<int, 9>{}, ux[0] - uy[0], ux[1] - uy[1]);
+            pair(std::integral_constant<int, 11>{}, ux[0] + uz[0], ux[1] + uz[1]);
+            pair(std::integral_constant<int, 13>{}, ux[0] - uz[0], ux[1] - uz[1]);
+            pair(std::integral_constant<int, 15>{}, uy[0] + uz[0], uy[1] + uz[1]);
+            pair(std::integral_constant<int, 17>{}, uy[0] - uz[0], uy[1] - uz[1]);
+            // rest population: its equilibrium is rho minus the other 18
+            // (equal to Eq. Equil in exact arithmetic), and in deviation
+            // storage it absorbs the rounding of the 18 stored values, so
+            // node mass is kept to FP32 rounding.  It stays at the node and
+            // enters only the density field: it is not stored.
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const R q0 = (T1 ? R(0) : omt[c] * f[c][0]) + itc[c] * (rho[c] - fe_sum[c]) + resid[c];
+                mid[c][0] += q0 + self[c];
+            }
+            // the 18 stored values and q0 sum to rho^c: the collision
+            // conserves mass
+            msum0 += rho[0];
+            msum1 += rho[1];
+        }
+
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
             // x shift (all lanes take part)
 #pragma unroll
             for (int q = 0; q < 5; q++) {
-                R fromL = __shfl_up_sync(FULL, up[q], 1);
-                R fromR = __shfl_down_sync(FULL, dn[q], 1);
+                R fromL = __shfl_up_sync(FULL, up[c][q], 1);
+                R fromR = __shfl_down_sync(FULL, dn[c][q], 1);
                 if (lx == 0) fromL = R(0);
                 if (lx == 31) fromR = R(0);
-                mid[q] += fromL + fromR;
+                mid[c][q] += fromL + fromR;
             }
             // values leaving the tile through x: the first lane sends left,
             // the last active lane sends right
             if (active && (lx == 0 || lx == w - 1)) {
                 // group q arrives at n + (x offset) + yz(q)
-                R* const rx = rnext + (size_t)c * N + n + (lx == 0 ? oxm : oxp);
+                const int mx = n + (lx == 0 ? oxm : oxp);
 #pragma unroll
                 for (int q = 0; q < 5; q++) {
-                    const R v = lx == 0 ? dn[q] : up[q];
-                    if (v != R(0)) red_add(rx + yz(q), v);
+                    const R v = lx == 0 ? dn[c][q] : up[c][q];
+                    if (v != R(0)) red_add(rnext + 2 * (size_t)(mx + yz(q)) + c, v);
                 }
                 if (w == 1) {  // a one-node-wide tile also sends right
 #pragma unroll
                     for (int q = 0; q < 5; q++)
-                        if (up[q] != R(0)) red_add(rnext + (size_t)c * N + n + oxp + yz(q), up[q]);
+                        if (up[c][q] != R(0)) red_add(rnext + 2 * (size_t)(n + oxp + yz(q)) + c, up[c][q]);
                 }
             }
             // y shift: rows exchange through shared memory; values leaving
             // the tile through y are reduced into the ring rows directly
-            acc[1][c] += mid[0];
-            acc[2][c] += mid[3];
-            acc[0][c] += mid[4];
+            acc[1][c] += mid[c][0];
+            acc[2][c] += mid[c][3];
+            acc[0][c] += mid[c][4];
 #pragma unroll
             for (int q = 1; q < 9; q++) {
                 if (yb_of(q) < 0) continue;
-                YB(yb_of(q), c, ly, lx) = mid[q];
+                YB(yb_of(q), c, ly, lx) = mid[c][q];
             }
             if (active && (ly == 0 || ly == h - 1)) {
 #pragma unroll
@@ -478,7 +513,7 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
                     if (yb_of(q) < 0) continue;
                     const int dy = grp_dy(q);
                     if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
-                    if (mid[q] != R(0)) red_add(rnext + (size_t)c * N + n + yz(q), mid[q]);
+                    if (mid[c][q] != R(0)) red_add(rnext + 2 * (size_t)(n + yz(q)) + c, mid[c][q]);
                 }
             }
         }
@@ -502,15 +537,14 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             const bool interior = own_plane && pz <= z0 + d - 2 && pz >= z0 + 1 && lx >= 1 && lx <= w - 2 && ly >= 1 &&
                                   ly <= h - 2;
             const int m = n + ozm;
+            if (interior) {
+                rnext2[m] = mk2<R2>(acc[0][0], acc[0][1]);
+            } else {
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
-                if (interior) rnext[(size_t)c * N + m] = acc[0][c];
-                else if (acc[0][c] != R(0)) red_add(&rnext[(size_t)c * N + m], acc[0][c]);
+                for (int c = 0; c < 2; c++)
+                    if (acc[0][c] != R(0)) red_add(rnext + 2 * (size_t)m + c, acc[0][c]);
             }
-            if (own_plane && !interior) {
-                rzero[m] = R(0);
-                rzero[(size_t)N + m] = R(0);
-            }
+            if (own_plane && !interior) rzero[m] = mk2<R2>(R(0), R(0));
         }
 #pragma unroll
         for (int c = 0; c < 2; c++) {
@@ -543,11 +577,8 @@ static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
             const int m = nxyc + nxy * gz;
 #pragma unroll
             for (int c = 0; c < 2; c++)
-                if (acc[k][c] != R(0)) red_add(&rnext[(size_t)c * N + m], acc[k][c]);
-            if (k == 0) {
-                rzero[m] = R(0);
-                rzero[(size_t)N + m] = R(0);
-            }
+                if (acc[k][c] != R(0)) red_add(rnext + 2 * (size_t)m + c, acc[k][c]);
+            if (k == 0) rzero[m] = mk2<R2>(R(0), R(0));
         }
     }
 

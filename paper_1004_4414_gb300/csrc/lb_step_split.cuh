@@ -14,8 +14,9 @@
 // u', which needs the partner's density and momentum: four shuffles.  A
 // thread holds 19 populations instead of 38, so it needs about half the
 // registers and an SM keeps twice the warps resident to hide load and store
-// latency.  Tiles are 16 nodes wide.  Each half-warp still moves 16
-// consecutive values of one array per access (64 bytes, two full sectors).
+// latency.  Tiles are 16 nodes wide.  The two components of a direction and
+// node are one pair in memory, so a warp's access covers the 16 pairs of its
+// nodes: 128 contiguous bytes in FP32.
 #pragma once
 #include "lb_step_kernel.cuh"
 
@@ -53,6 +54,7 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
     const BoxDev& B = boxes[T.box];
     const int nx = B.nx, ny = B.ny, nz = B.nz, N = B.N;
     const int nxy = nx * ny;
+    // density ring: component c of node m at [2 m + c]
     const R* __restrict__ rcur = reinterpret_cast<const R*>(B.rho[rc]);
     R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);
     R* __restrict__ rzero = reinterpret_cast<R*>(B.rho[rz]);
@@ -60,7 +62,7 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
     const Pop<P> pop(B);
     const R rho0 = (R)B.rho0, irho0 = R(1) / (R)B.rho0, g = (R)B.g;
     const R itau0 = (R)B.inv_tau[0], itau1 = (R)B.inv_tau[1];
-    R* const rnext_c = rnext + (size_t)(threadIdx.x >> 4) * N;  // this thread's component
+    R* const rnext_c = rnext + (threadIdx.x >> 4);  // this thread's component: node m at rnext_c[2 m]
     const R wax = (R)B.scw_axis, wdg = (R)B.scw_diag;
     const R bfx = (R)B.body[0], bfy = (R)B.body[1], bfz = (R)B.body[2];
     const int velmode = B.vel_mode;
@@ -69,16 +71,16 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
     const int c = lane >> 4, lx = lane & 15;  // component, column in the tile
     const R tauc = (R)B.tau[c], itauc = (R)B.inv_tau[c];
     // this component's population arrays and deviation constants
-    S* const cbase = pop.dir(c, P::dev ? 1 : 0);
-    const size_t dstride = pop.N;  // elements between direction arrays
+    S* const cbase = pop.at(c, P::dev ? 1 : 0, 0);
+    const size_t dstride = 2 * pop.N;  // elements between direction arrays
     float zra = 0.f, zrd = 0.f, refc = 0.f;
     if constexpr (P::dev) {
         zra = c ? pop.zr[1][0] : pop.zr[0][0];
         zrd = c ? pop.zr[1][1] : pop.zr[0][1];
         refc = (float)(c ? pop.ref[1] : pop.ref[0]);
     }
-    // array of direction i >= 1 of this component
-    auto dirp = [&](int i) -> S* { return cbase + (size_t)(P::dev ? i - 1 : i) * dstride; };
+    // this component of direction i >= 1 at node m
+    auto dirp = [&](int i, int m) -> S* { return cbase + (size_t)(P::dev ? i - 1 : i) * dstride + 2 * (size_t)m; };
     auto ldv = [&](const S* p, int i) -> R {
         if constexpr (P::dev) return fmaf(wgt<float>(i), to_f(*p), is_axis(i) ? zra : zrd);
         else return *p;
@@ -139,13 +141,13 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
         const int pb = nxy * gz;
         if (active) {
             const int n = pb + nxyc;
-            v.a = rcur[(size_t)c * N + n];
+            v.a = rcur[2 * (size_t)n + c];
             if (c == 0) v.af = gflags[n];
         }
         if (tid < nring) {
             const int n = pb + ring_xy;
-            v.b0 = rcur[n];
-            v.b1 = rcur[(size_t)N + n];
+            v.b0 = rcur[2 * (size_t)n];
+            v.b1 = rcur[2 * (size_t)n + 1];
             v.bf = gflags[n];
         }
         return v;
@@ -210,7 +212,7 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             }
 #pragma unroll
             for (int i = 1; i < 19; i++) {
-                const S* p = PAR == 0 ? dirp(i) + n : dirp(opp(i)) + (n + off(opp(i)));
+                const S* p = PAR == 0 ? dirp(i, n) : dirp(opp(i), n + off(opp(i)));
                 f[i] = ldv(p, i);
             }
             // rho^c is the density field (the sum of the values the previous
@@ -302,8 +304,8 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
                 constexpr int j = decltype(JC)::value;
                 const bool solid = BB && ((smask >> j) & 1u);
                 S* p;
-                if (PAR == 0) p = solid ? dirp(j) + (n + off(j)) : dirp(opp(j)) + n;
-                else p = solid ? dirp(opp(j)) + n : dirp(j) + (n + off(j));
+                if (PAR == 0) p = solid ? dirp(j, n + off(j)) : dirp(opp(j), n);
+                else p = solid ? dirp(opp(j), n) : dirp(j, n + off(j));
                 const R q = stv(p, j, fs);
                 if constexpr (P::dev) resid += fs - q;
                 const R qf = solid ? R(0) : q;
@@ -353,16 +355,16 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             mid[q] += fromL + fromR;
         }
         if (active && (lx == 0 || lx == w - 1)) {
-            R* const rx = rnext_c + n + (lx == 0 ? oxm : oxp);
+            const int mx = n + (lx == 0 ? oxm : oxp);
 #pragma unroll
             for (int q = 0; q < 5; q++) {
                 const R v = lx == 0 ? dn[q] : up[q];
-                if (v != R(0)) red_add(rx + yz(q), v);
+                if (v != R(0)) red_add(rnext_c + 2 * (size_t)(mx + yz(q)), v);
             }
             if (w == 1) {  // a one-node-wide tile also sends right
 #pragma unroll
                 for (int q = 0; q < 5; q++)
-                    if (up[q] != R(0)) red_add(rnext_c + n + oxp + yz(q), up[q]);
+                    if (up[q] != R(0)) red_add(rnext_c + 2 * (size_t)(n + oxp + yz(q)), up[q]);
             }
         }
         acc[1] += mid[0];
@@ -379,7 +381,7 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
                 if (yb_of(q) < 0) continue;
                 const int dy = grp_dy(q);
                 if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
-                if (mid[q] != R(0)) red_add(rnext_c + n + yz(q), mid[q]);
+                if (mid[q] != R(0)) red_add(rnext_c + 2 * (size_t)(n + yz(q)), mid[q]);
             }
         }
         __syncthreads();
@@ -399,9 +401,9 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             const bool interior = own_plane && pz <= z0 + d - 2 && pz >= z0 + 1 && lx >= 1 && lx <= w - 2 && ly >= 1 &&
                                   ly <= h - 2;
             const int m = n + ozm;
-            if (interior) rnext_c[m] = acc[0];
-            else if (acc[0] != R(0)) red_add(rnext_c + m, acc[0]);
-            if (own_plane && !interior) rzero[(size_t)c * N + m] = R(0);
+            if (interior) rnext_c[2 * (size_t)m] = acc[0];
+            else if (acc[0] != R(0)) red_add(rnext_c + 2 * (size_t)m, acc[0]);
+            if (own_plane && !interior) rzero[2 * (size_t)m + c] = R(0);
         }
         acc[0] = acc[1];
         acc[1] = acc[2];
@@ -423,8 +425,8 @@ static __global__ void __launch_bounds__(32 * TY, 32 / TY)
             const int pz = z0 + d - 1 + k;
             const int gz = pz >= nz ? pz - nz : pz;
             const int m = nxyc + nxy * gz;
-            if (acc[k] != R(0)) red_add(&rnext[(size_t)c * N + m], acc[k]);
-            if (k == 0) rzero[(size_t)c * N + m] = R(0);
+            if (acc[k] != R(0)) red_add(rnext_c + 2 * (size_t)m, acc[k]);
+            if (k == 0) rzero[2 * (size_t)m + c] = R(0);
         }
     }
 
