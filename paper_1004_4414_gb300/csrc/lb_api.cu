@@ -262,6 +262,8 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     sh.shell_list = cv.take<int4>((size_t)NPa * sh.shell_cap);
     sh.shell_n = cv.take<int>(NPa);
     sh.shell_dirty = cv.take<int>(NPa);
+    sh.xref = cv.take<float>((size_t)NPa * 3);
+    sh.exact = cv.take<int>(NPa);
     sh.err = cv.take<int>(1);
     sh.counters = cv.take<unsigned long long>((size_t)nb * 2);
     BoxDev* d_boxes = cv.take<BoxDev>(nb);
@@ -318,6 +320,29 @@ void fill_params(lb_handle* h) {
         B.lub_min = p.lub_min;
         B.nu = (1.0 / 3.0) * (0.5 * (p.tau[0] + p.tau[1]) - 0.5);
         B.c0 = p.mass_corr_c0;
+        {
+            // FP32 positions near L are off by up to about L * 2^-24; the
+            // bands keep every FP32 remap decision at least twice that error
+            // away from the surface (the FP64 test decides within them)
+            const double R = B.rb, R2 = B.radius * B.radius;
+            const int nmax = p.nx > p.ny ? (p.nx > p.nz ? p.nx : p.nz) : (p.ny > p.nz ? p.ny : p.nz);
+            const double eps_pos = 1.2e-7 * (double)nmax;
+            B.det_reach2 = (float)((R + 1.5) * (R + 1.5));
+            B.det_R2 = (float)R2;
+            B.det_band = (float)(0.02 + 2e-3 * R * R + 4.0 * (R + 1.5) * eps_pos);
+            B.det_qlim = (float)(R * R) + B.det_band;
+            // spheroid form F = R^2 (d.e)^2 + c^2 (|d|^2 - (d.e)^2) against
+            // R^2 c^2: |grad F| <= 2 max(R^2, c^2) |d| within the window, so
+            // the position error moves F by at most that times eps_pos; FP32
+            // rounding of F adds a few ulps of R^2 c^2
+            const double cRd = B.aspect * B.radius;
+            const double gmax = 2.0 * (R2 > cRd * cRd ? R2 : cRd * cRd) * (R + 1.5);
+            const float cR = (float)cRd;
+            B.det_sR2 = (float)R2;
+            B.det_sc2 = cR * cR;
+            B.det_sR2c2 = B.det_sR2 * B.det_sc2;
+            B.det_sband = (float)(0.05 + 4.0 * gmax * eps_pos + 1e-6 * R2 * cRd * cRd);
+        }
     }
 }
 
@@ -372,7 +397,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         k_cell_scan<<<h->nb, 1024, 0, st>>>(h->d_boxes, h->sh);
         k_cell_fill<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
         k_nlist<<<(NP + NLIST_WARPS - 1) / NLIST_WARPS, 32 * NLIST_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
-        k_remap_detect<<<(NP + DETECT_WARPS - 1) / DETECT_WARPS, 32 * DETECT_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_remap_detect<<<NP, 32 * DETECT_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         k_remap_mark<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->sh);
         CK(cudaGetLastError());
         CK(h->ops->remap_apply(par, st, h->d_boxes, h->sh, rc, mcur));
@@ -613,6 +638,8 @@ int after_init(lb_handle* h, int64_t t) {
     // every shell list is rebuilt at the first step of a new state
     if (h->NP > 0) {
         CK(cudaMemsetAsync(h->sh.shell_dirty, 1, sizeof(int) * h->NP, h->stream));
+        // and the first remap scans every particle's whole window
+        CK(cudaMemsetAsync(h->sh.exact, 0, sizeof(int) * h->NP, h->stream));
         CK(cudaStreamSynchronize(h->stream));
     }
     // graphs bake in the per-box wall flags (the wall-shell launches and the

@@ -88,6 +88,13 @@ struct BoxDev {
     int nc[3];                  // cells per axis
     int cell_off;               // offset into the global cell arrays
     double cell_len[3];
+    // remap decisions in FP32 away from the particle surface (set on the
+    // host): squared reach of the scan window, sphere radius^2, the band
+    // of R^2 within which the FP64 test decides, the FP32 bound beyond
+    // which no node is inside a neighbour, and the spheroid form's
+    // constants R^2, c^2, R^2 c^2 and band
+    float det_reach2, det_R2, det_band, det_qlim;
+    float det_sR2, det_sc2, det_sR2c2, det_sband;
 };
 
 struct TileDev {                // one CTA work item of the fused step kernel
@@ -120,6 +127,8 @@ struct Shared {
     int* shell_n;               // [NP]
     int* shell_dirty;           // [NP] nonzero: rebuild the shell list (events nearby, or a new state)
     int shell_cap;
+    float* xref;                // [NP][3] position at the last remap (FP32 copy)
+    int* exact;                 // [NP] 1: p owns exactly the nodes inside it at xref (remap fast path)
     int* err;                   // [1] sticky error bits
     unsigned long long* counters; // [n_boxes][2] n_cover, n_uncover
 };

@@ -122,7 +122,7 @@ cudaError_t remap_finish(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc
 
 cudaError_t shell_density(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int NP) {
     if (NP <= 0) return cudaSuccess;
-    k_shell_density<RR><<<(NP + 3) / 4, 128, 0, st>>>(boxes, sh, rc, NP);
+    k_shell_density<RR><<<NP, 32 * SHELL_WARPS, 0, st>>>(boxes, sh, rc, NP);
     return cudaGetLastError();
 }
 

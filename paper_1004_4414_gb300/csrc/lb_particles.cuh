@@ -160,8 +160,8 @@ static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev*
 }
 
 // ------------------------------------------------------------- remap
-// Warp per particle p: scan the nodes around X_p and record every node whose
-// solid/fluid status or owner changes.  A node belongs to the particle whose
+// One block per particle p, its warps sharing the scan: record every node
+// around X_p whose solid/fluid status or owner changes.  A node belongs to the particle whose
 // centre is nearest among those within R (|x - X|^2 <= R^2, minimum image);
 // ties go to the lower index.  Events: covered (fluid -> p), uncovered
 // (p -> fluid), transfer (q -> p, no fluid involved).  Distances are FP32
@@ -169,14 +169,16 @@ static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev*
 // `band` of R^2, where the FP64 value, evaluated without contraction as in a
 // plain sequential evaluation, decides.  FP64 is slow on this GPU, so it is
 // kept off the common path.
-constexpr int DETECT_WARPS = 4;
-static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+constexpr int DETECT_WARPS = 4, DETECT_QUEUE = 256;
+static __global__ void __launch_bounds__(32 * DETECT_WARPS, 8) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    __shared__ int s_queue[DETECT_WARPS][DETECT_QUEUE];  // annulus candidates of the fast path
+    // the close list, built by each warp for itself
     __shared__ float s_rq[DETECT_WARPS][NL_MAX][3];  // X_q - X_p, minimum image
     __shared__ int s_nid[DETECT_WARPS][NL_MAX];
     __shared__ int s_cl[DETECT_WARPS][NL_MAX];  // entries of neighbours within 2R (+ slack)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * DETECT_WARPS + wib;
-    if (p >= NP) return;  // the whole warp leaves together
+    const int p = blockIdx.x;
+    if (p >= NP) return;  // the whole block leaves together
     const int b = sh.pbox[p];
     const BoxDev& B = boxes[b];
     const PartStateF pf = sh.partf[p];
@@ -227,92 +229,84 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
-    const float Rf2o = (float)((R + 1.5) * (R + 1.5));
-    const float R2f = (float)R2;
-    // FP32 positions near L are off by up to about L * 2^-24; the bands below
-    // keep every FP32 decision at least twice that error away from the surface
-    const double eps_pos = 1.2e-7 * (double)max(B.nx, max(B.ny, B.nz));
-    const float band = (float)(0.02 + 2e-3 * R * R + 4.0 * (R + 1.5) * eps_pos);
-    const float qlim = (float)(R * R) + band;  // no node beyond this is inside q
+    // FP32 decisions away from the surface, the FP64 test within a band of
+    // it (the box constants are set on the host; FP64 is slow on this GPU)
+    const float Rf2o = B.det_reach2, R2f = B.det_R2, band = B.det_band;
+    const float qlim = B.det_qlim;  // no node beyond this is inside q
     // spheroid prefilter: F = R^2 (d.e)^2 + c^2 (|d|^2 - (d.e)^2) against
-    // R^2 c^2 in FP32.  |grad F| <= 2 max(R^2, c^2) |d| within the window, so
-    // the position error moves F by at most that times eps_pos; FP32
-    // rounding of F adds a few ulps of R^2 c^2; FP64 decides within sband
-    const double* Ep = sh.part[p].E;
-    const float ex_ = (float)Ep[0], ey_ = (float)Ep[1], ez_ = (float)Ep[2];
-    const double cRd = B.aspect * B.radius;
-    const float cR = (float)cRd;
-    const float R2s = (float)R2, c2s = cR * cR, R2c2 = R2s * c2s;
-    const double gmax = 2.0 * fmax(R2, cRd * cRd) * (R + 1.5);
-    const float sband = (float)(0.05 + 4.0 * gmax * eps_pos + 1e-6 * R2 * cRd * cRd);
-    for (int base = 0; base < total; base += 32) {
-        const int idx = base + lane;
-        int ev_old = 0, ev_new = 0, node = 0;
-        bool have = false;
-        if (idx < total) {
-            const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-            const float fx = mimgf((float)kx - off[0], Lf[0]), fy = mimgf((float)ky - off[1], Lf[1]),
-                        fz = mimgf((float)kz - off[2], Lf[2]);
-            const float d2f = fx * fx + fy * fy + fz * fz;
-            if (d2f <= Rf2o) {
-                const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
-                // FP64 inside test of this node for particle q; d2 = squared
-                // centre distance (the claim goes to the nearest centre)
-                auto exact_in = [&](int q, double& d2) {
-                    const double* C = sh.part[q].X;
-                    const double dx = mimg((double)gx - C[0], L[0]), dy = mimg((double)gy - C[1], L[1]),
-                                 dz = mimg((double)gz - C[2], L[2]);
-                    d2 = dist2_nc(dx, dy, dz);
-                    return inside_shape(B, dx, dy, dz, sh.part[q].E);
-                };
-                const int n = gx + B.nx * (gy + B.ny * gz);
-                const int own = __ldg(B.owner + n);
-                if (own != OWN_WALL) {
-                    double d2p = -1.0;
-                    bool inside;
-                    if (sph) {
-                        if (fabsf(d2f - R2f) > band) inside = d2f < R2f;
-                        else inside = exact_in(p, d2p);
-                    } else {
-                        const float sf = fx * ex_ + fy * ey_ + fz * ez_;
-                        const float Ff = R2s * sf * sf + c2s * (d2f - sf * sf);
-                        if (fabsf(Ff - R2c2) > sband) inside = Ff < R2c2;
-                        else inside = exact_in(p, d2p);
-                    }
-                    if (inside || own == p) {
-                        bool other = false, anyone = false;
-                        const int nk = inside ? ncl : nn;
-                        for (int kk = 0; kk < nk; kk++) {
-                            const int k = inside ? s_cl[wib][kk] : kk;
-                            const float ex = mimgf(fx - s_rq[wib][k][0], Lf[0]);
-                            const float ey = mimgf(fy - s_rq[wib][k][1], Lf[1]);
-                            const float ez = mimgf(fz - s_rq[wib][k][2], Lf[2]);
-                            if (ex * ex + ey * ey + ez * ez > qlim) continue;
-                            const int q = s_nid[wib][k];
-                            double d2q;
-                            if (exact_in(q, d2q)) {
-                                anyone = true;
-                                if (inside) {
-                                    if (d2p < 0.0) exact_in(p, d2p);
-                                    if (d2q < d2p || (d2q == d2p && q < p)) other = true;
-                                }
-                            }
-                        }
-                        const bool claim = inside && !other;
-                        if (claim && own != p) {
-                            have = true;
-                            ev_old = own;
-                            ev_new = p;
-                        } else if (!claim && own == p && !anyone) {
-                            have = true;
-                            ev_old = p;
-                            ev_new = OWN_FLUID;
-                        }
-                        node = n;
-                    }
+    // R^2 c^2 in FP32; FP64 decides within sband
+    float ex_ = 0.f, ey_ = 0.f, ez_ = 0.f;
+    if (!sph) {
+        const double* Ep = sh.part[p].E;
+        ex_ = (float)Ep[0];
+        ey_ = (float)Ep[1];
+        ez_ = (float)Ep[2];
+    }
+    const float R2s = B.det_sR2, c2s = B.det_sc2, R2c2 = B.det_sR2c2, sband = B.det_sband;
+    // one candidate node (kx, ky, kz) of the window: an event if its status
+    // or owner changes (have), with its node index, old and new owner
+    auto handle = [&](int kx, int ky, int kz, bool& have, int& node, int& ev_old, int& ev_new) {
+        const float fx = mimgf((float)kx - off[0], Lf[0]), fy = mimgf((float)ky - off[1], Lf[1]),
+                    fz = mimgf((float)kz - off[2], Lf[2]);
+        const float d2f = fx * fx + fy * fy + fz * fz;
+        if (!(d2f <= Rf2o)) return;
+        const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
+        // FP64 inside test of this node for particle q; d2 = squared
+        // centre distance (the claim goes to the nearest centre)
+        auto exact_in = [&](int q, double& d2) {
+            const double* C = sh.part[q].X;
+            const double dx = mimg((double)gx - C[0], L[0]), dy = mimg((double)gy - C[1], L[1]),
+                         dz = mimg((double)gz - C[2], L[2]);
+            d2 = dist2_nc(dx, dy, dz);
+            return inside_shape(B, dx, dy, dz, sh.part[q].E);
+        };
+        const int n = gx + B.nx * (gy + B.ny * gz);
+        const int own = __ldg(B.owner + n);
+        if (own == OWN_WALL) return;
+        double d2p = -1.0;
+        bool inside;
+        if (sph) {
+            if (fabsf(d2f - R2f) > band) inside = d2f < R2f;
+            else inside = exact_in(p, d2p);
+        } else {
+            const float sf = fx * ex_ + fy * ey_ + fz * ez_;
+            const float Ff = R2s * sf * sf + c2s * (d2f - sf * sf);
+            if (fabsf(Ff - R2c2) > sband) inside = Ff < R2c2;
+            else inside = exact_in(p, d2p);
+        }
+        if (!(inside || own == p)) return;
+        bool other = false, anyone = false;
+        const int nk = inside ? ncl : nn;
+        for (int kk = 0; kk < nk; kk++) {
+            const int k = inside ? s_cl[wib][kk] : kk;
+            const float ex = mimgf(fx - s_rq[wib][k][0], Lf[0]);
+            const float ey = mimgf(fy - s_rq[wib][k][1], Lf[1]);
+            const float ez = mimgf(fz - s_rq[wib][k][2], Lf[2]);
+            if (ex * ex + ey * ey + ez * ez > qlim) continue;
+            const int q = s_nid[wib][k];
+            double d2q;
+            if (exact_in(q, d2q)) {
+                anyone = true;
+                if (inside) {
+                    if (d2p < 0.0) exact_in(p, d2p);
+                    if (d2q < d2p || (d2q == d2p && q < p)) other = true;
                 }
             }
         }
+        const bool claim = inside && !other;
+        if (claim && own != p) {
+            have = true;
+            ev_old = own;
+            ev_new = p;
+        } else if (!claim && own == p && !anyone) {
+            have = true;
+            ev_old = p;
+            ev_new = OWN_FLUID;
+        }
+        node = n;
+    };
+    // the events of 32 candidates, appended to the event list
+    auto emit = [&](bool have, int node, int ev_old, int ev_new) {
         const unsigned m = __ballot_sync(0xffffffffu, have);
         if (m) {
             int basepos = 0;
@@ -324,6 +318,113 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
                 else set_err(sh.err, ERR_OVERFLOW);
             }
         }
+    };
+    // Fast path.  If the nodes p owns are exactly those inside p at the
+    // position of the last remap X_ref (no other particle was within 2R
+    // then: flag exact), and no other particle is within 2R now (ncl = 0),
+    // then every node whose status changes through p lies in the annulus
+    // R - delta < |x - X| <= R + delta, delta = |X - X_ref|: a node inside
+    // p now but not before is farther than R - delta from X, a node inside
+    // before but not now is within R + delta.  Only that annulus is scanned
+    // (0.1 of slack covers the FP32 centre); the per-node decision is the
+    // same as in the full scan, so the events are the same.  Spheres only.
+    // delta from the FP32 copies: their error (~L 2^-24) is far inside the
+    // 0.1 of slack
+    float dref2 = 0.f;
+    {
+        const float* Xr = sh.xref + (size_t)p * 3;
+        for (int a = 0; a < 3; a++) {
+            const float v = mimgf(pf.X[a] - Xr[a], Lf[a]);
+            dref2 += v * v;
+        }
+    }
+    const float delta = sqrtf(dref2);
+    bool fits = true;  // the window covers less than half of each axis (no wrap onto itself)
+    for (int a = 0; a < 3; a++) fits = fits && 2 * span[a] < dims[a] && span[a] < 1024;
+    const bool fast = sph && fits && ncl == 0 && sh.exact[p] && delta < 0.5f;
+    if (!fast) {
+        for (int base = wib * 32; base < total; base += 32 * DETECT_WARPS) {
+            const int idx = base + lane;
+            int ev_old = 0, ev_new = 0, node = 0;
+            bool have = false;
+            if (idx < total) {
+                const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+                handle(kx, ky, kz, have, node, ev_old, ev_new);
+            }
+            emit(have, node, ev_old, ev_new);
+        }
+    } else {
+        // rows (ky, kz) of the window, one per lane; the annulus crosses a
+        // row in at most two x intervals, whose nodes go to a per-warp queue
+        const float r_out = (float)R + delta + 0.1f, r_in = fmaxf((float)R - delta - 0.1f, 0.0f);
+        int* q = s_queue[wib];
+        const int nrows = span[1] * span[2];
+        for (int rb = wib * 32; rb < nrows; rb += 32 * DETECT_WARPS) {
+            const int row = rb + lane;
+            int l0 = 0, h0 = -1, l1 = 0, h1 = -1;
+            int ky = 0, kz = 0;
+            if (row < nrows) {
+                ky = row % span[1];
+                kz = row / span[1];
+                const float fy = (float)ky - off[1], fz = (float)kz - off[2];
+                const float p2 = fy * fy + fz * fz;
+                const float o2 = r_out * r_out - p2;
+                if (o2 >= 0.0f) {
+                    const float ao = sqrtf(o2);
+                    const float i2 = r_in * r_in - p2;
+                    // kx with |kx - off0| <= ao, minus |kx - off0| < ai
+                    const int xl = max(0, (int)ceilf(off[0] - ao)), xh = min(span[0] - 1, (int)floorf(off[0] + ao));
+                    if (i2 > 0.0f) {
+                        const float ai = sqrtf(i2);
+                        l0 = xl;
+                        h0 = min(xh, (int)ceilf(off[0] - ai) - 1);
+                        l1 = max(xl, (int)floorf(off[0] + ai) + 1);
+                        h1 = xh;
+                    } else {
+                        l0 = xl;
+                        h0 = xh;
+                    }
+                }
+            }
+            const int c0 = h0 >= l0 ? h0 - l0 + 1 : 0, c1 = h1 >= l1 ? h1 - l1 + 1 : 0;
+            const int cnt = c0 + c1;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            // queue in chunks that fit: entries kx | ky << 10 | kz << 20
+            for (int done = 0; done < tot; done += DETECT_QUEUE) {
+                int pos = incl - cnt - done;
+                for (int k = 0; k < cnt; k++, pos++) {
+                    if (pos < 0 || pos >= DETECT_QUEUE) continue;
+                    const int kx = k < c0 ? l0 + k : l1 + (k - c0);
+                    q[pos] = kx | (ky << 10) | (kz << 20);
+                }
+                __syncwarp();
+                const int nq = min(DETECT_QUEUE, tot - done);
+                for (int base = 0; base < nq; base += 32) {
+                    int ev_old = 0, ev_new = 0, node = 0;
+                    bool have = false;
+                    if (base + lane < nq) {
+                        const int e = q[base + lane];
+                        handle(e & 1023, (e >> 10) & 1023, e >> 20, have, node, ev_old, ev_new);
+                    }
+                    emit(have, node, ev_old, ev_new);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    // the reference position of the next remap, and whether p then owns
+    // exactly the nodes inside it (no other particle within 2R); after every
+    // warp has read the old values
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; a++) sh.xref[(size_t)p * 3 + a] = pf.X[a];
+        sh.exact[p] = ncl == 0 ? 1 : 0;
     }
 }
 
@@ -528,26 +629,81 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
 // ------------------------------------------------------- virtual fluid
 // Shell nodes get the mean density of their fluid neighbours plus the
 // particle colour on red (Delta rho > 0) or blue (Delta rho < 0) (Sec. IV).
+// One block per particle; its warps share the work.  The per-particle shell
+// list (node, mask of fluid neighbours, x | y << 16, z) is kept across steps
+// and rebuilt only when an event touched the particle (shell_dirty).
+constexpr int SHELL_WARPS = 4;
 template <class R>
-static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh, int rc, int NP) {
-    __shared__ int s_q[4][64];
-    __shared__ int s_qc[4][64];  // x | y << 16 of the queued node
-    __shared__ int s_qz[4][64];  // z of the queued node
+static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh,
+                                                                          int rc, int NP) {
+    using R2 = typename Real2<R>::type;
+    __shared__ int s_cnt[SHELL_WARPS];
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * 4 + wib;
-    if (p >= NP) return;  // the whole warp leaves together
+    const int p = blockIdx.x;
+    if (p >= NP) return;  // the whole block leaves together
     const BoxDev& B = boxes[sh.pbox[p]];
     const PartStateF pf = sh.partf[p];
-    R* __restrict__ rcur = reinterpret_cast<R*>(B.rho[rc]);
+    R2* __restrict__ r2 = rpair<R>(B.rho[rc]);
     const uint8_t* __restrict__ flags = B.flags;
     const int32_t* __restrict__ owner = B.owner;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
-    const size_t N = (size_t)B.N;
+    const int nxy = nx * ny;
     const float R_ = (float)B.rb;  // bounding radius (the radius for spheres)
     const R col = (R)sh.color[p];
-    // window: every node within R + 0.5 of the centre (the shell nodes of p
-    // lie within R; the 0.5 of slack covers the FP32 centre)
+    const int scap = sh.shell_cap;
+    int4* __restrict__ slist = sh.shell_list + (size_t)p * scap;
+    auto finish = [&](int n, R s0, R s1, int cnt) {
+        R r0 = s0 / (R)cnt, r1 = s1 / (R)cnt;
+        if (col > R(0)) r0 += col;
+        else if (col < R(0)) r1 -= col;
+        r2[n] = mk2<R2>(r0, r1);
+    };
+    if (!sh.shell_dirty[p]) {
+        // No event near p since its list was built: the shell nodes and
+        // their fluid-neighbour masks are unchanged, only the densities are
+        // new (the whole block takes this branch together).  Two entries
+        // per thread per round: all their density loads are issued before
+        // either node is written.
+        const int ns = sh.shell_n[p];
+        constexpr int NT = 32 * SHELL_WARPS;
+        for (int k0 = threadIdx.x; k0 < ns; k0 += 2 * NT) {
+            R s0[2] = {R(0), R(0)}, s1[2] = {R(0), R(0)};
+            int nk[2] = {0, 0};
+            unsigned fm[2] = {0u, 0u};
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int k = k0 + NT * u;
+                if (k >= ns) continue;
+                const int4 e = slist[k];
+                const int n = e.x;
+                const unsigned fmask = (unsigned)e.y;
+                nk[u] = n;
+                fm[u] = fmask;
+                const int gx = e.z & 0xffff, gy = (int)((unsigned)e.z >> 16), gz = e.w;
+                const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
+                const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
+                const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
+#pragma unroll
+                for (int i = 1; i < 19; i++) {
+                    if (!((fmask >> i) & 1u)) continue;
+                    const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) +
+                                  (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) + (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
+                    const R2 v = r2[m];
+                    s0[u] += v.x;
+                    s1[u] += v.y;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; u++)
+                if (k0 + NT * u < ns) finish(nk[u], s0[u], s1[u], __popc(fm[u]));
+        }
+        return;
+    }
+    // Rebuild: every shell node of p lies within R of its centre, so the
+    // window of nodes within R + 0.5 (the slack covers the FP32 centre) is
+    // scanned; the shell flag and the owner decide.  No FP64 here: it is
+    // slow on this GPU.
     const float reach = R_ + 0.5f;
     int lo[3], span[3];
     float off[3];  // X - lo: node (lo + k) sits at k - off from the centre
@@ -559,45 +715,24 @@ static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* _
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
-    const int scap = sh.shell_cap;
-    int4* __restrict__ slist = sh.shell_list + (size_t)p * scap;
-    if (!sh.shell_dirty[p]) {
-        // No event near p since its list was built: the shell nodes and
-        // their fluid-neighbour masks are unchanged, only the densities are
-        // new (the whole warp takes this branch together).
-        const int ns = sh.shell_n[p];
-        const int nxy = nx * ny;
-        for (int k = lane; k < ns; k += 32) {
-            const int4 e = slist[k];
-            const int n = e.x;
-            const unsigned fmask = (unsigned)e.y;
-            const int gx = e.z & 0xffff, gy = (int)((unsigned)e.z >> 16), gz = e.w;
-            const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
-            const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
-            const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
-            R s0 = R(0), s1 = R(0);
-#pragma unroll
-            for (int i = 1; i < 19; i++) {
-                if (!((fmask >> i) & 1u)) continue;
-                const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) +
-                              (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) + (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
-                s0 += rcur[2 * (size_t)m];
-                s1 += rcur[2 * (size_t)m + 1];
-            }
-            const R cnt = (R)__popc(fmask);
-            R r0 = s0 / cnt, r1 = s1 / cnt;
-            if (col > R(0)) r0 += col;
-            else if (col < R(0)) r1 -= col;
-            rcur[2 * (size_t)n] = r0;
-            rcur[2 * (size_t)n + 1] = r1;
-        }
-        return;
-    }
+    const float lim = reach * reach;
+    // candidate idx of the window: a shell node of p?
+    auto test = [&](int idx, int& n, int& cxy, int& cz) -> bool {
+        if (idx >= total) return false;
+        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+        const float dx = mimgf((float)kx - off[0], (float)nx), dy = mimgf((float)ky - off[1], (float)ny),
+                    dz = mimgf((float)kz - off[2], (float)nz);
+        if (!(dx * dx + dy * dy + dz * dz <= lim)) return false;
+        const int gx = wrapi(lo[0] + kx, nx), gy = wrapi(lo[1] + ky, ny), gz = wrapi(lo[2] + kz, nz);
+        n = gx + nx * (gy + ny * gz);
+        cxy = (int)((unsigned)gx | ((unsigned)gy << 16));
+        cz = gz;
+        return (__ldg(flags + n) & FL_SHELL) && __ldg(owner + n) == p;
+    };
     // virtual density of one shell node n of p, and its entry k of p's
     // shell list (node, mask of fluid neighbours, coordinates)
-    const int nxy = nx * ny;
-    auto process = [&](int n, int gx, int gy, int gz, int k) {
-        // wrap-aware offsets to the neighbours along each axis
+    auto process = [&](int n, int cxy, int gz, int k) {
+        const int gx = cxy & 0xffff, gy = (int)((unsigned)cxy >> 16);
         const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
         const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
         const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
@@ -609,64 +744,51 @@ static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* _
             const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) + (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) +
                           (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
             if (!(flags[m] & FL_SOLID)) {
-                s0 += rcur[2 * (size_t)m];
-                s1 += rcur[2 * (size_t)m + 1];
+                const R2 v = r2[m];
+                s0 += v.x;
+                s1 += v.y;
                 cnt++;
                 fmask |= 1u << i;
             }
         }
-        if (k < scap) slist[k] = make_int4(n, (int)fmask, (int)((unsigned)gx | ((unsigned)gy << 16)), gz);
-        R r0 = s0 / (R)cnt, r1 = s1 / (R)cnt;
-        if (col > R(0)) r0 += col;
-        else if (col < R(0)) r1 -= col;
-        rcur[2 * (size_t)n] = r0;
-        rcur[2 * (size_t)n + 1] = r1;
+        if (k < scap) slist[k] = make_int4(n, (int)fmask, cxy, gz);
+        finish(n, s0, s1, cnt);
     };
-    // FP32 prefilter only (every shell node of p lies within R); the shell
-    // flag and the owner decide.  No FP64 here: it is slow on this GPU.
-    // Shell nodes are queued as they are found and handled 32 at a time;
-    // they are also listed for k_couple.
-    const float lim = (R_ + 0.5f) * (R_ + 0.5f);
-    int nq = 0, done = 0;  // warp-uniform: queue length (< 64), nodes handled
-    for (int base = 0;; base += 32) {
-        const int idx = base + lane;
-        bool take = false;
-        int n = 0, gx = 0, gy = 0, gz = 0;
-        if (idx < total) {
-            const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-            const float dx = mimgf((float)kx - off[0], (float)nx), dy = mimgf((float)ky - off[1], (float)ny),
-                        dz = mimgf((float)kz - off[2], (float)nz);
-            if (dx * dx + dy * dy + dz * dz <= lim) {
-                gx = wrapi(lo[0] + kx, nx);
-                gy = wrapi(lo[1] + ky, ny);
-                gz = wrapi(lo[2] + kz, nz);
-                n = gx + nx * (gy + ny * gz);
-                take = (__ldg(flags + n) & FL_SHELL) && __ldg(owner + n) == p;
-            }
-        }
-        const unsigned m = __ballot_sync(FULL, take);
-        if (take) {
-            const int pos = nq + __popc(m & ((1u << lane) - 1u));
-            s_q[wib][pos] = n;
-            s_qc[wib][pos] = (int)((unsigned)gx | ((unsigned)gy << 16));
-            s_qz[wib][pos] = gz;
-        }
-        nq += __popc(m);
-        __syncwarp();
-        const bool last = base + 32 >= total;  // the final round drains the queue
-        if (nq >= 32 || (last && nq > 0)) {
-            const int k = nq < 32 ? nq : 32;
-            const int item = lane < k ? s_q[wib][nq - k + lane] : -1;
-            const int ic = lane < k ? s_qc[wib][nq - k + lane] : 0;
-            const int iz = lane < k ? s_qz[wib][nq - k + lane] : 0;
-            __syncwarp();
-            nq -= k;
-            if (item >= 0) process(item, ic & 0xffff, (int)((unsigned)ic >> 16), iz, done + lane);
-            done += k;
-        }
-        if (last && nq == 0) break;
+    // Two passes over the same candidates, each warp taking chunks of 32 SU
+    // in turn: the first counts each warp's shell nodes, the second lists
+    // them after those of the lower warps, so the list order does not
+    // depend on timing.  The second pass finds the flags and owners in L1.
+    constexpr int SU = 4, CH = 32 * SU;
+    int mine = 0;
+    for (int base = wib * CH; base < total; base += CH * SHELL_WARPS) {
+        bool tk[SU];
+        int nu[SU], cu[SU], zu[SU];
+#pragma unroll
+        for (int u = 0; u < SU; u++) tk[u] = test(base + u * 32 + lane, nu[u], cu[u], zu[u]);
+#pragma unroll
+        for (int u = 0; u < SU; u++) mine += __popc(__ballot_sync(FULL, tk[u]));
     }
-    if (lane == 0) {
+    if (lane == 0) s_cnt[wib] = mine;
+    __syncthreads();
+    int pos = 0, done = 0;
+#pragma unroll
+    for (int w = 0; w < SHELL_WARPS; w++) {
+        if (w < wib) pos += s_cnt[w];
+        done += s_cnt[w];
+    }
+    for (int base = wib * CH; base < total; base += CH * SHELL_WARPS) {
+        bool tk[SU];
+        int nu[SU], cu[SU], zu[SU];
+#pragma unroll
+        for (int u = 0; u < SU; u++) tk[u] = test(base + u * 32 + lane, nu[u], cu[u], zu[u]);
+#pragma unroll
+        for (int u = 0; u < SU; u++) {
+            const unsigned m = __ballot_sync(FULL, tk[u]);
+            if (tk[u]) process(nu[u], cu[u], zu[u], pos + __popc(m & ((1u << lane) - 1u)));
+            pos += __popc(m);
+        }
+    }
+    if (threadIdx.x == 0) {
         sh.shell_n[p] = done < scap ? done : scap;
         if (done > scap) set_err(sh.err, ERR_OVERFLOW);
         else sh.shell_dirty[p] = 0;
@@ -702,12 +824,13 @@ static __global__ void __launch_bounds__(128, 8) k_shell_density(const BoxDev* _
 // fluid node.  Static walls (owner -2) reflect without a wall
 // term and need nothing here.  rho^c(x) is the density field of the current
 // step (the fused step's moments up to rounding order).
-constexpr int COUPLE_THREADS = 256;
+constexpr int COUPLE_THREADS = 128;
 template <class P>
 static __global__ void __launch_bounds__(COUPLE_THREADS)
     k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot, int par, int reflect) {
     using R = typename P::real;
-    using S = typename P::st;
+    using S2 = typename P::st2;
+    using R2 = typename Real2<R>::type;
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ R s_red[COUPLE_THREADS / 32][8];
@@ -715,10 +838,8 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const BoxDev& B = boxes[sh.pbox[p]];
     const Pop<P> pop(B);
     const auto& ps = part_ptr<R>(sh)[p];
-    const size_t N = (size_t)B.N;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
-    using R2 = typename Real2<R>::type;
-    using S2 = typename P::st2;
+    const int nxy = nx * ny;
     const R2* __restrict__ rcur2 = rpair<R>(B.rho[rc]);
     R2* __restrict__ rnext2 = rpair<R>(B.rho[rn]);
     double* __restrict__ mass_acc = B.mass_acc;
@@ -728,139 +849,116 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const R X0 = (R)ps.X[0], X1 = (R)ps.X[1], X2 = (R)ps.X[2];
     const R U0 = (R)ps.U[0], U1 = (R)ps.U[1], U2 = (R)ps.U[2];
     const R W0 = (R)ps.W[0], W1 = (R)ps.W[1], W2 = (R)ps.W[2];
+    // the reflected pair f*_j (j = opp(i)) of the link from m = s + c_i to
+    // s belongs after an even step in slot j of s, after an odd step in
+    // slot i of m; unreflected it sits in the other of the two
+    const bool at_s = (par == 0) == (reflect != 0);
     R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     R dm0 = R(0), dm1 = R(0);
-    // the shell nodes found by k_shell_density in this step
+    // the shell nodes found by k_shell_density in this step, one per thread
     const int ns = sh.shell_n[p];
     const int4* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
-    // (1) links: one item per (direction i, shell node s), direction-major,
-    // so that neighbouring threads touch neighbouring nodes of one array.
-    // Each thread takes U items at a time and issues all their loads before
-    // any store, so that U independent chains are in flight.
-    constexpr int U = 4;
-    const int nitems = 18 * ns;
-    for (int k0 = threadIdx.x; k0 < nitems; k0 += U * COUPLE_THREADS) {
-        int iu[U], mu[U];
-        S2* pu[U];
-        ptrdiff_t mv[U];  // pairs from the slot read to the slot written
-        S2 rawu[U];
-        R2 rru[U];
-        int4 eu[U];
-        bool ok[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int k = k0 + u * COUPLE_THREADS;
-            ok[u] = k < nitems;
-            iu[u] = 1;
-            if (ok[u]) {
-                iu[u] = 1 + k / ns;
-                eu[u] = list[k - (iu[u] - 1) * ns];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int i = iu[u];
-            ok[u] = ok[u] && ((eu[u].y >> i) & 1);  // s + c_i fluid: a link
-            mu[u] = 0;
-            mv[u] = 0;
-            pu[u] = nullptr;
-            if (ok[u]) {
-                const int s = eu[u].x;
-                const int gx = eu[u].z & 0xffff, gy = (int)((unsigned)eu[u].z >> 16), gz = eu[u].w;
-                const int m = wrap1(gx + kC[i][0], nx) + nx * (wrap1(gy + kC[i][1], ny) + ny * wrap1(gz + kC[i][2], nz));
-                mu[u] = m;
-                // the reflected pair f*_j belongs after an even step in slot
-                // j = opp(i) of s, after an odd step in slot opp(j) = i of
-                // m; unreflected it sits in the other of the two
-                const bool at_s = (par == 0) == (reflect != 0);
-                pu[u] = at_s ? pop.pair(opp(i), s) : pop.pair(i, m);
-                if (!reflect) mv[u] = at_s ? pop.pair(i, m) - pu[u] : pop.pair(opp(i), s) - pu[u];
-                rawu[u] = *pu[u];
-                rru[u] = __ldg(rcur2 + m);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            if (!ok[u]) continue;
-            const int i = iu[u], m = mu[u];
-            const int ix = kC[i][0], iy = kC[i][1], iz = kC[i][2];
-            const int gx = eu[u].z & 0xffff, gy = (int)((unsigned)eu[u].z >> 16), gz = eu[u].w;
-            // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
-            const R r0 = mimg_r<R>((R)gx - X0, Lx) + R(0.5) * (R)ix;
-            const R r1 = mimg_r<R>((R)gy - X1, Ly) + R(0.5) * (R)iy;
-            const R r2 = mimg_r<R>((R)gz - X2, Lz) + R(0.5) * (R)iz;
-            const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
-            const R cu6 = -R(6) * (i <= 6 ? wgt<R>(1) : wgt<R>(7)) * (us0 * (R)ix + us1 * (R)iy + us2 * (R)iz);
-            const S2 raw = rawu[u];
-            R fs[2], wall[2], dr[2] = {R(0), R(0)};
-            if constexpr (P::dev) {
-                fs[0] = pop.dev_to_f(0, i, raw.x);
-                fs[1] = pop.dev_to_f(1, i, raw.y);
-            } else {
-                fs[0] = raw.x;
-                fs[1] = raw.y;
-            }
-            wall[0] = cu6 * rru[u].x;
-            wall[1] = cu6 * rru[u].y;
-            if (cu6 != R(0) || !reflect) {
-                S2 q = raw;
-                if constexpr (P::dev) {
-                    // a value without a wall term moves bit for bit; the
-                    // density field takes the exact change b - f* of a
-                    // re-encoded one (its rounding lands in the rest
-                    // population, which is rho minus the 18 stored values)
-                    if (wall[0] != R(0)) {
-                        q.x = pop.f_to_dev(0, i, fs[0] - wall[0]);
-                        dr[0] = -wall[0];
-                    }
-                    if (wall[1] != R(0)) {
-                        q.y = pop.f_to_dev(1, i, fs[1] - wall[1]);
-                        dr[1] = -wall[1];
-                    }
-                } else {
-                    q.x = fs[0] - wall[0];
-                    q.y = fs[1] - wall[1];
-                    dr[0] = q.x - fs[0];
-                    dr[1] = q.y - fs[1];
-                }
-                pu[u][mv[u]] = q;
-                red_add2<R>(rnext2 + m, reflect ? dr[0] : dr[0] + fs[0], reflect ? dr[1] : dr[1] + fs[1]);
-                dm0 += dr[0];
-                dm1 += dr[1];
-            }
-            const R mag = (R(2) * fs[0] - wall[0]) + (R(2) * fs[1] - wall[1]);
-            const R F0 = -mag * (R)ix, F1 = -mag * (R)iy, F2 = -mag * (R)iz;
-            acc[0] += F0;
-            acc[1] += F1;
-            acc[2] += F2;
-            acc[3] += r1 * F2 - r2 * F1;
-            acc[4] += r2 * F0 - r0 * F2;
-            acc[5] += r0 * F1 - r1 * F0;
-        }
-    }
-    // (2) the Shan-Chen force of the virtual fluid at each shell node
     for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) {
         const int4 e = list[k];
         const int s = e.x;
+        const unsigned fmask = (unsigned)e.y;  // bit i: s + c_i is fluid (a link)
         const int gx = e.z & 0xffff, gy = (int)((unsigned)e.z >> 16), gz = e.w;
-        R sr0 = R(0), sr1 = R(0), sr2 = R(0), sb0 = R(0), sb1 = R(0), sb2 = R(0);
-#pragma unroll
-        for (int i = 1; i < 19; i++) {
-            const int m = wrap1(gx + cx(i), nx) + nx * (wrap1(gy + cy(i), ny) + ny * wrap1(gz + cz(i), nz));
-            const R w = is_axis(i) ? wax : wdg;
-            const R2 rm = __ldg(rcur2 + m);
-            const R pr = w * psi_of<R>(rm.x, rho0, irho0);
-            const R pb = w * psi_of<R>(rm.y, rho0, irho0);
-            sr0 += pr * (R)cx(i);
-            sr1 += pr * (R)cy(i);
-            sr2 += pr * (R)cz(i);
-            sb0 += pb * (R)cx(i);
-            sb1 += pb * (R)cy(i);
-            sb2 += pb * (R)cz(i);
-        }
+        const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
+        const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
+        const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
+        auto nb = [&](int i) -> int {
+            return s + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) + (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) +
+                   (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
+        };
+        // s relative to the centre
         const R rs0 = mimg_r<R>((R)gx - X0, Lx), rs1 = mimg_r<R>((R)gy - X1, Ly), rs2 = mimg_r<R>((R)gz - X2, Lz);
-        const R2 rs = __ldg(rcur2 + s);
-        const R psr = psi_of<R>(rs.x, rho0, irho0), psb = psi_of<R>(rs.y, rho0, irho0);
+        const R2 rss = __ldg(rcur2 + s);
+        R sr0 = R(0), sr1 = R(0), sr2 = R(0), sb0 = R(0), sb1 = R(0), sb2 = R(0);
+        // directions in three groups of six: the loads of a group (the
+        // densities of the neighbours, the populations of the links) are
+        // issued before any of its stores
+#pragma unroll
+        for (int grp = 0; grp < 3; grp++) {
+            R2 rm[6];
+            S2 raw[6];
+#pragma unroll
+            for (int t = 0; t < 6; t++) {
+                const int i = 1 + 6 * grp + t;
+                const int m = nb(i);
+                rm[t] = __ldg(rcur2 + m);
+                if ((fmask >> i) & 1u) raw[t] = *(at_s ? pop.pair(opp(i), s) : pop.pair(i, m));
+            }
+#pragma unroll
+            for (int t = 0; t < 6; t++) {
+                const int i = 1 + 6 * grp + t;
+                // Shan-Chen: Psi of every neighbour (fluid, virtual or interior)
+                const R w = is_axis(i) ? wax : wdg;
+                const R pr = w * psi_of<R>(rm[t].x, rho0, irho0);
+                const R pb = w * psi_of<R>(rm[t].y, rho0, irho0);
+                sr0 += pr * (R)cx(i);
+                sr1 += pr * (R)cy(i);
+                sr2 += pr * (R)cz(i);
+                sb0 += pb * (R)cx(i);
+                sb1 += pb * (R)cy(i);
+                sb2 += pb * (R)cz(i);
+                if (!((fmask >> i) & 1u)) continue;
+                // link from the fluid node m to s; c_j = -c_i; midpoint s + c_i / 2
+                const int m = nb(i);
+                const R r0 = rs0 + R(0.5) * (R)cx(i), r1 = rs1 + R(0.5) * (R)cy(i), r2 = rs2 + R(0.5) * (R)cz(i);
+                const R us0 = U0 + W1 * r2 - W2 * r1, us1 = U1 + W2 * r0 - W0 * r2, us2 = U2 + W0 * r1 - W1 * r0;
+                const R cu6 =
+                    -R(6) * wgt<R>(i) * (us0 * (R)cx(i) + us1 * (R)cy(i) + us2 * (R)cz(i));
+                R fs[2], wall[2], dr[2] = {R(0), R(0)};
+                if constexpr (P::dev) {
+                    fs[0] = pop.dev_to_f(0, i, raw[t].x);
+                    fs[1] = pop.dev_to_f(1, i, raw[t].y);
+                } else {
+                    fs[0] = raw[t].x;
+                    fs[1] = raw[t].y;
+                }
+                wall[0] = cu6 * rm[t].x;
+                wall[1] = cu6 * rm[t].y;
+                if (cu6 != R(0) || !reflect) {
+                    S2 q = raw[t];
+                    if constexpr (P::dev) {
+                        // a value without a wall term moves bit for bit; the
+                        // density field takes the exact change b - f* of a
+                        // re-encoded one (its rounding lands in the rest
+                        // population, which is rho minus the 18 stored values)
+                        if (wall[0] != R(0)) {
+                            q.x = pop.f_to_dev(0, i, fs[0] - wall[0]);
+                            dr[0] = -wall[0];
+                        }
+                        if (wall[1] != R(0)) {
+                            q.y = pop.f_to_dev(1, i, fs[1] - wall[1]);
+                            dr[1] = -wall[1];
+                        }
+                    } else {
+                        q.x = fs[0] - wall[0];
+                        q.y = fs[1] - wall[1];
+                        dr[0] = q.x - fs[0];
+                        dr[1] = q.y - fs[1];
+                    }
+                    // reflect = 0 moves the value to the other slot
+                    S2* const to = (at_s == (reflect != 0)) ? pop.pair(opp(i), s) : pop.pair(i, m);
+                    *to = q;
+                    red_add2<R>(rnext2 + m, reflect ? dr[0] : dr[0] + fs[0], reflect ? dr[1] : dr[1] + fs[1]);
+                    dm0 += dr[0];
+                    dm1 += dr[1];
+                }
+                const R mag = (R(2) * fs[0] - wall[0]) + (R(2) * fs[1] - wall[1]);
+                const R F0 = -mag * (R)cx(i), F1 = -mag * (R)cy(i), F2 = -mag * (R)cz(i);
+                acc[0] += F0;
+                acc[1] += F1;
+                acc[2] += F2;
+                acc[3] += r1 * F2 - r2 * F1;
+                acc[4] += r2 * F0 - r0 * F2;
+                acc[5] += r0 * F1 - r1 * F0;
+            }
+        }
+        // the Shan-Chen force of the virtual fluid at s on the particle
+        // (Eq. eqn_shan_chen_particle), torque (s - X) x F
+        const R psr = psi_of<R>(rss.x, rho0, irho0), psb = psi_of<R>(rss.y, rho0, irho0);
         const R F0 = -g * (psr * sb0 + psb * sr0), F1 = -g * (psr * sb1 + psb * sr1), F2 = -g * (psr * sb2 + psb * sr2);
         acc[0] += F0;
         acc[1] += F1;

@@ -138,8 +138,14 @@ struct StepSmem {
 
 // T1: every box has tau^r = tau^b = 1, where BGK gives f* = f^eq: the
 // loaded populations then only feed the moments and need not stay live.
+// Resident CTAs per SM: three for the FP32 / 16-bit tau = 1 kernel (80
+// registers, no spills: 24 warps hide the population loads), else two.
+template <class P, bool T1>
+constexpr int step_min_blocks(int ty) {
+    return ty <= 8 ? ((T1 && sizeof(typename P::real) == 4) ? 3 : 2) : 1;
+}
 template <class P, int PAR, int TY, bool T1, bool BB>
-static __global__ void __launch_bounds__(32 * TY, (TY <= 8 ? 2 : 1))
+static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
     k_step(const BoxDev* __restrict__ boxes, const TileDev* __restrict__ tiles, Shared sh, int rc, int rn, int rz,
            int mslot) {
     using R = typename P::real;
