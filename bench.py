@@ -1,15 +1,30 @@
 """Throughput of the particle-laden two-component Shan-Chen LB step on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload c256|c128|c512|c32|batch] [--precision fp32|fp16|bf16]
-                [--variants]
+                [--workload c256|c128|c512|c32|batch|...] [--precision fp32|fp16|bf16]
 
 One "step" is one time step of the whole hot path over the workload: particle
 remap with cover/uncover, shell virtual fluid, fused stream-collide with the
 Shan-Chen force and moving bounce-back, particle force reduction and MD.
 The metric is MLUPS (lattice node updates per second, both components,
-every node of the box counted once per step) and the fraction of the
-measured HBM roofline reached by the fused stream-collide kernel.
+every node of the box counted once per step), for FP32, for FP16 / BF16
+deviation storage and for the batched sweep, on the same GPU.
+
+With no --workload / --precision the run measures every leg of the metric
+and prints one JSON line: the 256^3 FP32 leg is the headline (value, e2e,
+roofline), and "legs" holds the 256^3 FP16-deviation, 256^3 BF16-deviation
+and 64-box batch legs with the same fields (the batch also with
+batch_vs_sequential).  Two roofline fractions are reported per leg:
+  roofline.frac       the fused stream-collide kernel alone: its algorithmic
+                      bytes per launch over its CUDA-event launch time, against
+                      the measured HBM copy bandwidth;
+  roofline.step_frac  the whole step: MLUPS over the roofline MLUPS of the
+                      ideal byte count per node (2 components x 19
+                      populations read and written: 304 B in FP32, 152 B in
+                      16-bit storage) at the measured HBM bandwidth.
+The timed steps replay the CUDA graphs exactly as lb_step does; the fused
+kernel's launch time comes from a separate pass of the same steps with
+per-launch CUDA events.
 
 Workloads (seeded, synthetic; the paper's runs are synthetic as well):
   c256  256^3, fluid ratio 60:40 of total density 0.7, alpha = 0.20, R = 5,
@@ -43,6 +58,10 @@ sys.path.insert(0, ROOT)
 
 PROFILES = os.path.join(ROOT, "profiles")
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+# ideal bytes per node and step: 2 components x 19 populations, read and written
+IDEAL_BYTES = {"fp32": 2 * 19 * 4 * 2, "fp16": 2 * 19 * 2 * 2, "bf16": 2 * 19 * 2 * 2, "fp64": 2 * 19 * 8 * 2}
+# the legs of the metric measured by a default run: (workload, precision)
+DEFAULT_LEGS = (("c256", "fp32"), ("c256", "fp16"), ("c256", "bf16"), ("batch", "fp32"))
 KERNEL_SOURCES = ("lb_step_kernel.cuh", "lb_step_split.cuh", "lb_common.cuh")
 
 
@@ -261,8 +280,8 @@ def run_ours(args, rank, world, device):
             torch.distributed.barrier()
 
     # ---- device-timed region: inputs resident in HBM (the state is larger
-    # than the 129 MB L2, so no flush is needed between steps)
-    sim.set_profiling(True)
+    # than the 129 MB L2, so no flush is needed between steps).  The steps
+    # replay the CUDA graphs exactly as lb_step does for a caller.
     barrier()
     torch.cuda.synchronize(device)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -274,11 +293,20 @@ def run_ours(args, rank, world, device):
         torch.cuda.synchronize(device)
     barrier()
     ms = e0.elapsed_time(e1)
-    fused_ms, fused_n, total_launches = sim.kernel_time()
-    sim.set_profiling(False)
     sim.sync()
     clocks = clk.summary()
     value, ms_max = job_throughput(nodes * args.steps, ms * 1e-3, world, device)
+
+    # ---- a separate pass of the same steps with per-launch CUDA events
+    # around the fused kernel (kernel-by-kernel launches instead of graph
+    # replays), for the fused kernel's launch time and the launch count
+    prof_steps = min(args.steps, 20)
+    sim.set_profiling(True)
+    sim.step(prof_steps)
+    fused_ms, fused_n, total_launches = sim.kernel_time()
+    sim.set_profiling(False)
+    sim.sync()
+    launches = int(round(total_launches / max(prof_steps, 1) * args.steps))
 
     # ---- roofline of the fused kernel
     bytes_launch = fused_bytes(sim, args.precision)
@@ -318,7 +346,7 @@ def run_ours(args, rank, world, device):
         seq = {"sequential_mlups": seq_value, "batched_mlups": value, "ratio": value / seq_value,
                "sequential_ms": seq_ms, "what": "the same boxes and states, one handle per box, run one after another"}
     return dict(value=value, ms=ms_max, fused_ms=avg_ms, fused_n=fused_n, bytes=bytes_launch, achieved=achieved,
-                peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=total_launches, nodes=nodes,
+                peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=launches, nodes=nodes,
                 n_particles=sum(sim.n_particles), error=ob["error"], n_fluid=n_fluid, tiling=tiling, seq=seq)
 
 
@@ -409,39 +437,77 @@ def oracle_steps(workload, steps, warmup, edge=64):
                        (steps, warmup, p["nx"], p["ny"], p["nz"], workload, full[0], full[1], full[2], o.np))
 
 
+NAMES = {"c256": "256^3 60:40 alpha=0.20 R=5 theta=77deg", "c128": "128^3 50:50 alpha=0.15 R=5 theta=90deg",
+         "c256p": "128^3 with the 256^3 parameters (profiling case)",
+         "c256s": "256^3 60:40 alpha=0.12 prolate spheroids 4x4x6 theta=77deg",
+         "c512": "512^3 50:50 alpha=0.20 R=5 theta=90deg", "c32": "32^3 16 spheres R=4",
+         "batch": "64 boxes {48,64,96,128}^3 theta 60-120 alpha 0.05-0.25 ratio 50:50-70:30"}
+DTYPES = {"fp32": "f32", "fp16": "f16-dev/f32", "bf16": "bf16-dev/f32"}
+
+
+def leg_fields(args, r):
+    """The fields of one measured leg (workload, precision)."""
+    traffic = ncu_traffic(args.workload, args.precision, r["tiling"][2])
+    ideal = IDEAL_BYTES[args.precision]
+    roof_mlups = r["peak"] * 1e3 / ideal  # GB/s / (B/node) -> MLUPS
+    return {
+        "value": r["value"], "unit": "MLUPS", "ms_per_step": r["ms"] / args.steps,
+        "dtype": DTYPES[args.precision],
+        "config": {"workload": NAMES[args.workload], "precision": args.precision, "nodes": r["nodes"],
+                   "fluid_nodes": r["n_fluid"], "particles": r["n_particles"],
+                   "l2": "state larger than L2 (no flush needed)",
+                   "tiling": {"ty": r["tiling"][0], "cz": r["tiling"][1], "split": r["tiling"][2]}},
+        "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
+                     "frac": r["achieved"] / r["peak"], "traffic": traffic,
+                     "peak_kind": r["peak_kind"], "kernel": fused_kernel_name(r["tiling"][2]) + " (fused stream-collide)",
+                     "bytes_per_launch": r["bytes"], "launch_ms": r["fused_ms"],
+                     "frac_nominal": r["achieved"] / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+                     "dram_gbs": traffic / (r["fused_ms"] * 1e6) if traffic else None,
+                     "step_frac": r["value"] / roof_mlups, "step_roofline_mlups": roof_mlups,
+                     "ideal_bytes_per_node": ideal},
+        "fluid_mlups": r["value"] * r["n_fluid"] / r["nodes"],
+        "e2e": r["e2e"],
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "batch_vs_sequential": r["seq"],
+        "device_error": r["error"],
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c256", choices=["c256", "c256p", "c256s", "c128", "c512", "c32", "batch"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--workload", default=None, choices=["c256", "c256p", "c256s", "c128", "c512", "c32", "batch"],
+                    help="one workload only (default: every leg of the metric)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sequential", action="store_true", help="batch: skip the one-box-at-a-time comparison")
     ap.add_argument("--tiling", default=None, metavar="TY,CZ,SPLIT",
                     help="fixed block shape of the fused kernel instead of the autotuner's (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload is None and args.precision is None and args.tiling is None:
+        legs = list(DEFAULT_LEGS)
+    else:
+        legs = [(args.workload or "c256", args.precision or "fp32")]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     metric = "MLUPS and % of HBM roofline: FP32 vs BF16/FP16-storage vs batched, same GPU"
-    names = {"c256": "256^3 60:40 alpha=0.20 R=5 theta=77deg", "c128": "128^3 50:50 alpha=0.15 R=5 theta=90deg",
-             "c256p": "128^3 with the 256^3 parameters (profiling case)",
-             "c256s": "256^3 60:40 alpha=0.12 prolate spheroids 4x4x6 theta=77deg",
-             "c512": "512^3 50:50 alpha=0.20 R=5 theta=90deg", "c32": "32^3 16 spheres R=4",
-             "batch": "64 boxes {48,64,96,128}^3 theta 60-120 alpha 0.05-0.25 ratio 50:50-70:30"}
 
     if args.impl == "reference":
         if rank != 0:
             return
-        r = oracle_steps(args.workload, args.steps, args.warmup)
+        workload = legs[0][0]
+        r = oracle_steps(workload, args.steps, args.warmup)
         line = {"impl": "reference", "metric": metric, "value": r["value"], "unit": "MLUPS", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["seconds"] / r["steps"] * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": names[args.workload], "precision": "fp64 (oracle)"},
+                "data": "synthetic", "config": {"workload": NAMES[workload], "precision": "fp64 (oracle)"},
                 "cpu_baseline": {"value": r["value"], "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
                                  "sample": r["sample"]},
                 "e2e": {"value": r["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -454,39 +520,36 @@ def main():
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl")
     device = torch.device("cuda", local)
-    r = run_ours(args, rank, world, device)
+    results = []
+    for workload, precision in legs:
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.precision = workload, precision
+        r = run_ours(a, rank, world, device)
+        results.append((a, r))
+        torch.cuda.empty_cache()
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        c = oracle_sample(args.workload)
+        c = oracle_sample(legs[0][0])
         cpu = {"value": c["value"], "unit": "MLUPS", "cores": c["cores"], "kind": "oracle", "sample": c["sample"]}
-    traffic = ncu_traffic(args.workload, args.precision, r["tiling"][2])
-    line = {
-        "metric": metric, "value": r["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-dev/f32", "bf16": "bf16-dev/f32"}[args.precision],
-        "data": "synthetic",
-        "config": {"workload": names[args.workload], "precision": args.precision, "nodes": r["nodes"],
-                   "fluid_nodes": r["n_fluid"], "particles": r["n_particles"],
-                   "l2": "state larger than L2 (no flush needed)",
-                   "tiling": {"ty": r["tiling"][0], "cz": r["tiling"][1], "split": r["tiling"][2]}},
-        "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"], "unit": "GB/s",
-                     "frac": r["achieved"] / r["peak"], "traffic": traffic,
-                     "peak_kind": r["peak_kind"], "kernel": fused_kernel_name(r["tiling"][2]) + " (fused stream-collide)",
-                     "bytes_per_launch": r["bytes"], "launch_ms": r["fused_ms"],
-                     "frac_nominal": r["achieved"] / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
-                     "dram_gbs": traffic / (r["fused_ms"] * 1e6) if traffic else None},
-        "fluid_mlups": r["value"] * r["n_fluid"] / r["nodes"],
-        "cpu_baseline": cpu,
-        "e2e": r["e2e"],
-        "clocks": r["clocks"],
-        "gpu_launches": r["launches"],
-        "batch_vs_sequential": r["seq"],
-        "device_error": r["error"],
-    }
+    head_args, head = results[0]
+    f = leg_fields(head_args, head)
+    line = {"metric": metric, "value": f["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f["dtype"], "data": "synthetic"}
+    line.update({k: v for k, v in f.items() if k not in line})
+    line["cpu_baseline"] = cpu
+    if len(results) > 1:
+        line["legs"] = {}
+        for a, r in results[1:]:
+            name = "%s_%s" % (a.workload, a.precision)
+            line["legs"][name] = leg_fields(a, r)
+        fp32 = head["value"]
+        line["legs_vs_fp32"] = {n: v["value"] / fp32 for n, v in line["legs"].items()}
+        line["gpu_launches_all_legs"] = sum(r["launches"] for _, r in results)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -886,17 +886,20 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
     const int par = (int)(h->t & 1);
     CK(cudaStreamSynchronize(st));
     if (f) {
-        // direction d is converted into staging half d % 2 on the handle's
-        // stream and copied out on xstream, so the conversion of d + 1
-        // overlaps the copy of d
-        for (int d = 0; d < 38; d++) {
+        // direction d (both components, 2N doubles) is converted into
+        // staging slot d % 2 on the handle's stream and copied out on
+        // xstream, so the conversion of d + 1 overlaps the copy of d
+        const size_t N = (size_t)B.N;
+        for (int d = 0; d < 19; d++) {
             const int k = d & 1;
-            double* buf = h->stage + (size_t)k * B.N;
+            double* buf = h->stage + (size_t)k * 2 * N;
             if (d >= 2) CK(cudaStreamWaitEvent(st, h->ev_c[k], 0));
-            CK(h->ops->export_dir(st, h->d_boxes, box, d / 19, d % 19, par, (int)(h->t % 3), buf));
+            CK(h->ops->export_dir(st, h->d_boxes, box, d, par, (int)(h->t % 3), buf));
             CK(cudaEventRecord(h->ev_k[k], st));
             CK(cudaStreamWaitEvent(h->xstream, h->ev_k[k], 0));
-            CK(cudaMemcpyAsync(f + (size_t)d * B.N, buf, sizeof(double) * B.N, cudaMemcpyDeviceToHost, h->xstream));
+            for (int c = 0; c < 2; c++)
+                CK(cudaMemcpyAsync(f + ((size_t)c * 19 + d) * N, buf + c * N, sizeof(double) * N,
+                                   cudaMemcpyDeviceToHost, h->xstream));
             CK(cudaEventRecord(h->ev_c[k], h->xstream));
         }
         CK(cudaStreamSynchronize(h->xstream));
@@ -995,18 +998,22 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
     k_shell_all<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, box);
     CK(cudaGetLastError());
     const int par = (int)(t & 1), rcs = (int)(t % 3);
-    // direction d is copied into staging half d % 2 on xstream and converted
-    // on the handle's stream, so the copy of d + 1 overlaps the conversion of d
+    // direction d (both components, 2N doubles) is copied into staging slot
+    // d % 2 on xstream and converted on the handle's stream, so the copy of
+    // d + 1 overlaps the conversion of d (the owner scratch above is free
+    // again: the map was copied into the box)
     CK(cudaEventRecord(h->ev_k[0], st));  // xstream starts after the work above
     CK(cudaStreamWaitEvent(h->xstream, h->ev_k[0], 0));
-    for (int d = 0; d < 38; d++) {
+    for (int d = 0; d < 19; d++) {
         const int k = d & 1;
-        double* buf = h->stage + (size_t)k * N;
+        double* buf = h->stage + (size_t)k * 2 * N;
         if (d >= 2) CK(cudaStreamWaitEvent(h->xstream, h->ev_k[k], 0));
-        CK(cudaMemcpyAsync(buf, f + (size_t)d * N, sizeof(double) * N, cudaMemcpyHostToDevice, h->xstream));
+        for (int c = 0; c < 2; c++)
+            CK(cudaMemcpyAsync(buf + (size_t)c * N, f + ((size_t)c * 19 + d) * N, sizeof(double) * N,
+                               cudaMemcpyHostToDevice, h->xstream));
         CK(cudaEventRecord(h->ev_c[k], h->xstream));
         CK(cudaStreamWaitEvent(st, h->ev_c[k], 0));
-        CK(h->ops->import_dir(st, h->d_boxes, box, d / 19, d % 19, par, buf));
+        CK(h->ops->import_dir(st, h->d_boxes, box, d, par, buf));
         CK(cudaEventRecord(h->ev_k[k], st));
     }
     for (int k = 0; k < 3; k++) CK(cudaMemsetAsync(B.rho[k], 0, (size_t)2 * N * h->ops->real_size, st));

@@ -171,27 +171,57 @@ __device__ __forceinline__ double rest_of(const BoxDev& B, const Pop<P>& pop, in
     return (double)reinterpret_cast<const R*>(B.rho[rc])[2 * (size_t)n + c] - s;
 }
 
+// direction i of both components of box b in canonical order: out[c * N + n]
+// (0 on solid nodes; for i = 0 the rest population rho^c - sum_{i>0} f_i)
 template <class P>
-static __global__ void k_export_dir(const BoxDev* __restrict__ boxes, int b, int c, int i, int par, int rc,
+static __global__ void k_export_dir(const BoxDev* __restrict__ boxes, int b, int i, int par, int rc,
                                     double* __restrict__ out) {
-    const BoxDev& B = boxes[b];
-    const Pop<P> pop(B);
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
-        if (B.flags[n] & FL_SOLID) out[n] = 0.0;
-        else out[n] = i == 0 ? rest_of<P>(B, pop, par, rc, c, n) : (double)load_node_pop<P>(B, pop, par, c, i, n);
-    }
-}
-
-template <class P>
-static __global__ void k_import_dir(const BoxDev* __restrict__ boxes, int b, int c, int i, int par, const double* __restrict__ in) {
     using R = typename P::real;
     const BoxDev& B = boxes[b];
     const Pop<P> pop(B);
+    const size_t N = (size_t)B.N;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        double v0 = 0.0, v1 = 0.0;
+        if (!(B.flags[n] & FL_SOLID)) {
+            if (i == 0) {
+                v0 = rest_of<P>(B, pop, par, rc, 0, n);
+                v1 = rest_of<P>(B, pop, par, rc, 1, n);
+            } else {
+                // before an even step f_i sits in slot i of n, before an odd
+                // step in slot opp(i) of n - c_i
+                const int slot = par == 0 ? i : opp(i);
+                const int m = par == 0 ? n : nbr_index(B, n, -cx(i), -cy(i), -cz(i));
+                R a, c;
+                pop.ld2(pop.pair(slot, m), i, a, c);
+                v0 = (double)a;
+                v1 = (double)c;
+            }
+        }
+        out[n] = v0;
+        out[N + n] = v1;
+    }
+}
+
+// direction i of both components from canonical order in[c * N + n]
+template <class P>
+static __global__ void k_import_dir(const BoxDev* __restrict__ boxes, int b, int i, int par,
+                                    const double* __restrict__ in) {
+    using R = typename P::real;
+    const BoxDev& B = boxes[b];
+    const Pop<P> pop(B);
+    const size_t N = (size_t)B.N;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
         if (B.flags[n] & FL_SOLID) continue;
-        const R v = (R)in[n];
-        if (par == 0 || i == 0) pop.store(c, i, n, v);
-        else pop.store(c, opp(i), nbr_index(B, n, -cx(i), -cy(i), -cz(i)), v);
+        const R v0 = (R)in[n], v1 = (R)in[N + n];
+        if (i == 0) {
+            pop.store(0, 0, n, v0);
+            pop.store(1, 0, n, v1);
+        } else {
+            const int slot = par == 0 ? i : opp(i);
+            const int m = par == 0 ? n : nbr_index(B, n, -cx(i), -cy(i), -cz(i));
+            R q0, q1;
+            pop.st2(pop.pair(slot, m), i, v0, v1, q0, q1);
+        }
     }
 }
 

@@ -144,13 +144,13 @@ cudaError_t init_pop(cudaStream_t st, const BoxDev* boxes, int b, const double* 
     return cudaGetLastError();
 }
 
-cudaError_t export_dir(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, int rc, double* out) {
-    k_export_dir<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, c, i, par, rc, out);
+cudaError_t export_dir(cudaStream_t st, const BoxDev* boxes, int b, int i, int par, int rc, double* out) {
+    k_export_dir<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, i, par, rc, out);
     return cudaGetLastError();
 }
 
-cudaError_t import_dir(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, const double* in) {
-    k_import_dir<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, c, i, par, in);
+cudaError_t import_dir(cudaStream_t st, const BoxDev* boxes, int b, int i, int par, const double* in) {
+    k_import_dir<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, i, par, in);
     return cudaGetLastError();
 }
 

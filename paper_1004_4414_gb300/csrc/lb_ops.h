@@ -23,9 +23,9 @@ struct LbOps {
     cudaError_t (*init_pop)(cudaStream_t st, const BoxDev* boxes, int b, const double* rho_field,
                             const double* u_field, uint64_t s_red, uint64_t s_blue, double noise, int rc,
                             double* mass_out);
-    cudaError_t (*export_dir)(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, int rc,
-                              double* out);
-    cudaError_t (*import_dir)(cudaStream_t st, const BoxDev* boxes, int b, int c, int i, int par, const double* in);
+    // direction i of both components, canonical order [2][N] doubles
+    cudaError_t (*export_dir)(cudaStream_t st, const BoxDev* boxes, int b, int i, int par, int rc, double* out);
+    cudaError_t (*import_dir)(cudaStream_t st, const BoxDev* boxes, int b, int i, int par, const double* in);
     cudaError_t (*rho_from_pop)(cudaStream_t st, const BoxDev* boxes, int b, int par, int src, int rc, double* out,
                                 double* mass_out);
     cudaError_t (*obs_partial)(cudaStream_t st, const BoxDev* boxes, int b, int par, int rc, double* partials);
