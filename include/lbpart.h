@@ -101,6 +101,14 @@ typedef struct {
     int64_t n_fluid, n_solid;    /* current node counts */
     int32_t error;               /* sticky device error (LB_OK or LB_E*) */
     int32_t n_particles;
+    double L[3];                 /* domain size L_i = 2 pi / sqrt(<k_i^2>) (Sec. VI, Eq. eq:domsize): <k_i^2>
+                                    the second moment along axis i of the structure function
+                                    S(k) = |phi'_k|^2 / N of phi = rho^r - rho^b (0 on solid nodes),
+                                    phi' = phi - <phi>; NaN for a uniform phi */
+    double coverage;             /* fraction of the box's particles whose fluid D3Q19 neighbours (the fluid
+                                    nodes linked to their solid nodes) include phi > 0 and phi < 0; the
+                                    paper names the interface coverage but does not define it, this is
+                                    the reading used; 0 without particles */
 } lb_obs;
 
 typedef struct lb_handle lb_handle;
@@ -148,8 +156,18 @@ int lb_step(lb_handle* h, int64_t n);
 /* Wait for the stream; return the sticky device error (LB_OK if none). */
 int lb_sync(lb_handle* h);
 
-/* Observables of one box; synchronises the stream. */
+/* Observables of one box; synchronises the stream.  The domain size and the
+ * coverage are computed on the device: one FP64 mixed-radix FFT per lattice
+ * line and axis (Parseval reduces the three-dimensional moment to line
+ * transforms; any box size, lines longer than 2048 nodes are slower), about
+ * 10 ms for a 256^3 box, so call it between steps, not every step. */
 int lb_observables(lb_handle* h, int32_t box, lb_obs* out);
+
+/* The order parameter phi = rho^r - rho^b of one box (Sec. VI; 0 on solid
+ * nodes), phi[N] in canonical node order (host array, may be NULL), with
+ * the domain size L[3] and the coverage of lb_observables (either may be
+ * NULL).  LB_EINVAL before an init.  Synchronises the stream. */
+int lb_export_phi(lb_handle* h, int32_t box, double* phi, double* L, double* coverage);
 
 /* Full state of one box in canonical order (host arrays, any may be NULL):
  * f[2][19][N] FP64 (0 on solid nodes), owner[N], particles[np][9],

@@ -61,6 +61,8 @@ class LbObs(C.Structure):
         ("n_solid", C.c_int64),
         ("error", C.c_int32),
         ("n_particles", C.c_int32),
+        ("L", C.c_double * 3),
+        ("coverage", C.c_double),
     ]
 
 
@@ -76,7 +78,8 @@ DEFAULTS = dict(
 
 ABI_FUNCTIONS = (
     "lb_workspace_bytes", "lb_create", "lb_init_from_seed", "lb_init_fields", "lb_step", "lb_sync",
-    "lb_observables", "lb_export_state", "lb_import_state", "lb_export_rho", "lb_set_particle_colors",
+    "lb_observables", "lb_export_state", "lb_import_state", "lb_export_rho", "lb_export_phi",
+    "lb_set_particle_colors",
     "lb_set_axes", "lb_get_axes",
     "lb_particle_forces", "lb_box_info", "lb_set_tiling", "lb_set_profiling", "lb_kernel_time",
     "lb_destroy", "lb_strerror", "lb_field_moments",
@@ -111,6 +114,7 @@ def load_library(path=LIB_PATH):
     L.lb_export_state.argtypes = [vp, C.c_int32, dp, ip, dp, dp]
     L.lb_import_state.argtypes = [vp, C.c_int32, dp, ip, dp, dp]
     L.lb_export_rho.argtypes = [vp, C.c_int32, dp]
+    L.lb_export_phi.argtypes = [vp, C.c_int32, dp, dp, dp]
     L.lb_set_particle_colors.argtypes = [vp, C.c_int32, dp]
     L.lb_set_axes.argtypes = [vp, C.c_int32, dp]
     L.lb_get_axes.argtypes = [vp, C.c_int32, dp]
@@ -155,10 +159,14 @@ def field_moments(f, owner, out, stream=None):
         raise TypeError("f and out must be float64, owner int32")
     if f.numel() != 2 * 19 * n or out.numel() < 8 or not (f.is_contiguous() and owner.is_contiguous()):
         raise ValueError("f must be contiguous (2, 19, N) for owner of N nodes; out needs 8 values")
-    s = stream if stream is not None else torch.cuda.current_stream(out.device)
-    _ck(load_library().lb_field_moments(C.c_void_p(f.data_ptr()), C.c_void_p(owner.data_ptr()), n,
-                                        C.c_void_p(s.cuda_stream), C.c_void_p(out.data_ptr())),
-        "lb_field_moments")
+    if not (f.device == owner.device == out.device) or out.device.type != "cuda":
+        raise ValueError("f, owner and out must be on the same CUDA device")
+    # the library checks the pointers against the current device
+    with torch.cuda.device(out.device):
+        s = stream if stream is not None else torch.cuda.current_stream(out.device)
+        _ck(load_library().lb_field_moments(C.c_void_p(f.data_ptr()), C.c_void_p(owner.data_ptr()), n,
+                                            C.c_void_p(s.cuda_stream), C.c_void_p(out.data_ptr())),
+            "lb_field_moments")
     return out
 
 
@@ -274,7 +282,7 @@ class Simulation:
         return dict(step=o.step, mass=np.array(o.mass[:]), mom_fluid=np.array(o.mom_fluid[:]),
                     mom_part=np.array(o.mom_part[:]), max_u=o.max_u, n_cover=o.n_cover,
                     n_uncover=o.n_uncover, n_fluid=o.n_fluid, n_solid=o.n_solid, error=o.error,
-                    n_particles=o.n_particles)
+                    n_particles=o.n_particles, L=np.array(o.L[:]), coverage=o.coverage)
 
     def export_state(self, box=0, f=True, f_out=None):
         """Canonical state; f_out: optional C-contiguous float64 array
@@ -309,9 +317,18 @@ class Simulation:
         return r
 
     def phi(self, box=0):
+        """Order parameter rho^r - rho^b (0 on solid nodes), shape (nz, ny, nx)."""
         nx, ny, nz = self.dims[box]
-        r = self.rho(box)
-        return (r[0] - r[1]).reshape(nz, ny, nx)
+        out = np.zeros(nx * ny * nz)
+        _ck(load_library().lb_export_phi(self._h, box, _dp(out), None, None), "lb_export_phi")
+        return out.reshape(nz, ny, nx)
+
+    def structure(self, box=0):
+        """Domain size (L_x, L_y, L_z) and interface coverage of one box."""
+        L = np.zeros(3)
+        cov = C.c_double(0)
+        _ck(load_library().lb_export_phi(self._h, box, None, _dp(L), C.byref(cov)), "lb_export_phi")
+        return L, cov.value
 
     def set_axes(self, box, e):
         """Body axes [n_particles][3] of spheroids (unit vectors)."""

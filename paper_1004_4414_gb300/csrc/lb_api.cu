@@ -10,6 +10,7 @@
 #include "lbpart.h"
 #include "lb_aux.cuh"
 #include "lb_ops.h"
+#include "lb_structure.cuh"
 
 using namespace lbp;
 
@@ -17,6 +18,12 @@ namespace {
 
 constexpr size_t ALIGN = 256;
 constexpr int SMALL_GRID = 304, SMALL_BLOCK = 256;
+// line-spectrum blocks per axis of the domain-size observable
+constexpr int SPEC_GRID = 1216;
+// staging layout of lb_observables: phi [N], the phi sums [2 OBS_BLOCKS],
+// the spectrum sums [3 SPEC_GRID], the totals [8], the coverage marks
+// [np ints], then FFT scratch for lines longer than SPEC_SMEM_POINTS
+constexpr size_t OBS_STAGE_FIXED = (size_t)2 * OBS_BLOCKS + 3 * SPEC_GRID + 8;
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -196,7 +203,7 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     const LbOps* ops = ops_for(bx[0].precision);
     const size_t rs = ops->real_size;
     const bool dev = bx[0].precision == LB_FP16_DEV || bx[0].precision == LB_BF16_DEV;
-    int NP = 0, cells = 0, maxN = 0, maxTiles = 0, evcap = 0;
+    int NP = 0, cells = 0, maxN = 0, maxTiles = 0, evcap = 0, maxEdge = 1;
     std::vector<BoxDev> hb(nb);
     for (int b = 0; b < nb; b++) {
         const lb_params& p = bx[b];
@@ -230,6 +237,8 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
         B.cell_off = cells;
         cells += cg.nc[0] * cg.nc[1] * cg.nc[2];
         maxN = N > maxN ? N : maxN;
+        const int e3 = p.nx > p.ny ? (p.nx > p.nz ? p.nx : p.nz) : (p.ny > p.nz ? p.ny : p.nz);
+        maxEdge = e3 > maxEdge ? e3 : maxEdge;
         // the most tiles any block shape makes: 32 x 4 or (split) 16 x 8 nodes, one plane each
         const int t32 = ((p.nx + 31) / 32) * ((p.ny + 3) / 4), t16 = ((p.nx + 15) / 16) * ((p.ny + 7) / 8);
         maxTiles += (t32 > t16 ? t32 : t16) * p.nz;
@@ -268,7 +277,10 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     sh.counters = cv.take<unsigned long long>((size_t)nb * 2);
     BoxDev* d_boxes = cv.take<BoxDev>(nb);
     TileDev* d_tiles = cv.take<TileDev>(maxTiles);
-    const size_t stage_doubles = (size_t)5 * maxN + (size_t)9 * NPa + 64;
+    // import/export and init need 5 N + 9 np; lb_observables N + fixed sums +
+    // np / 2 for the marks + FFT scratch of at least one line beyond
+    // SPEC_SMEM_POINTS (3 n complex values)
+    const size_t stage_doubles = (size_t)5 * maxN + (size_t)9 * NPa + OBS_STAGE_FIXED + (size_t)6 * maxEdge + 64;
     double* stage = cv.take<double>(stage_doubles);
     double* obs = cv.take<double>((size_t)OBS_BLOCKS * OBS_W + OBS_W);
     double* mtmp = cv.take<double>(2);
@@ -653,6 +665,73 @@ int after_init(lb_handle* h, int64_t t) {
     return build_graphs(h);
 }
 
+// Domain size (Eq. eq:domsize) and interface coverage of box b on the
+// device (lb_structure.cuh); phi_out (host, N doubles) receives phi if not
+// NULL.  Synchronises the stream.
+int structure_obs(lb_handle* h, int box, double L[3], double* coverage, double* phi_out) {
+    const BoxDev& B = h->hbox[box];
+    cudaStream_t st = h->stream;
+    const size_t N = (size_t)B.N;
+    const int rc = (int)(h->t % 3);
+    double* phi = h->stage;
+    double* phisum = phi + N;
+    double* specsum = phisum + 2 * OBS_BLOCKS;
+    double* tot = specsum + 3 * SPEC_GRID;
+    int* marks = reinterpret_cast<int*>(tot + 8);
+    double2* scratch = reinterpret_cast<double2*>(tot + 8 + ((size_t)B.np + 1) / 2 + 2);
+    scratch = reinterpret_cast<double2*>(((uintptr_t)scratch + 15) & ~(uintptr_t)15);
+    const size_t scratch_c2 = (h->stage_doubles - (size_t)((double*)scratch - h->stage)) / 2;  // double2 slots
+    CK(h->ops->phi_field(st, h->d_boxes, box, rc, phi, phisum));
+    k_sum_columns<<<1, 32, 0, st>>>(phisum, OBS_BLOCKS, 2, 2, tot);
+    const int dims[3] = {B.nx, B.ny, B.nz};
+    int grid[3] = {0, 0, 0};
+    for (int a = 0; a < 3; a++) {
+        const int n = dims[a];
+        const Radices rad = radices_of(n);
+        const int nlines = (int)(N / (size_t)n);
+        if (n <= SPEC_SMEM_POINTS) {
+            int W = SPEC_SMEM_POINTS / n;
+            if (W > nlines) W = nlines;
+            const int ngroups = (nlines + W - 1) / W;
+            const int G = ngroups < SPEC_GRID ? ngroups : SPEC_GRID;
+            const size_t smem = (2 * (size_t)W * n + n) * sizeof(double2);
+            k_line_spectrum<true><<<G, SPEC_THREADS, smem, st>>>(phi, B.nx, B.ny, B.nz, a, W, rad, nullptr,
+                                                                  specsum + a * SPEC_GRID);
+            grid[a] = G;
+        } else {
+            const size_t per = 3 * (size_t)n;  // double2 per block
+            size_t G = scratch_c2 / per;
+            if (G > (size_t)SPEC_GRID) G = SPEC_GRID;
+            if (G > (size_t)nlines) G = nlines;
+            if (G < 1) return LB_ENOMEM;
+            k_line_spectrum<false><<<(int)G, SPEC_THREADS, 0, st>>>(phi, B.nx, B.ny, B.nz, a, 1, rad, scratch,
+                                                                     specsum + a * SPEC_GRID);
+            grid[a] = (int)G;
+        }
+        CK(cudaGetLastError());
+        k_sum_columns<<<1, 32, 0, st>>>(specsum + a * SPEC_GRID, grid[a], 1, 1, tot + 2 + a);
+    }
+    if (B.np > 0) {
+        CK(cudaMemsetAsync(marks, 0, sizeof(int) * B.np, st));
+        CK(h->ops->coverage_marks(st, h->d_boxes, box, rc, marks));
+        k_count_both<<<1, 256, 0, st>>>(marks, B.np, tot + 5);
+    }
+    CK(cudaGetLastError());
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(v, tot, sizeof(double) * (B.np > 0 ? 6 : 5), cudaMemcpyDeviceToHost, st));
+    if (phi_out) CK(cudaMemcpyAsync(phi_out, phi, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // sum phi'^2 = sum phi^2 - N <phi>^2; <k_a^2> = spectrum_a / (n_a sum phi'^2)
+    const double mean = v[0] / (double)N;
+    const double var = v[1] - (double)N * mean * mean;
+    for (int a = 0; a < 3; a++) {
+        const double k2 = v[2 + a] / ((double)dims[a] * var);
+        L[a] = (var > 0.0 && k2 > 0.0) ? 2.0 * M_PI / std::sqrt(k2) : NAN;
+    }
+    *coverage = B.np > 0 ? v[5] / (double)B.np : 0.0;
+    return LB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -706,7 +785,10 @@ int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t
         h->axes[b].assign((size_t)3 * h->hbox[b].np, 0.0);
         for (int q = 0; q < h->hbox[b].np; q++) h->axes[b][3 * q + 2] = 1.0;
     }
-    if (h->ops->setup() != cudaSuccess || cudaHostAlloc((void**)&h->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+    if (h->ops->setup() != cudaSuccess ||
+        cudaFuncSetAttribute(k_line_spectrum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(3 * SPEC_SMEM_POINTS * sizeof(double2))) != cudaSuccess ||
+        cudaHostAlloc((void**)&h->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->xstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_k[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -875,6 +957,8 @@ int lb_observables(lb_handle* h, int32_t box, lb_obs* out) {
     out->n_cover = (int64_t)cnt[0];
     out->n_uncover = (int64_t)cnt[1];
     out->n_particles = B.np;
+    int rc = structure_obs(h, box, out->L, &out->coverage, nullptr);
+    if (rc != LB_OK) return rc;
     out->error = read_err(h);
     return LB_OK;
 }
@@ -1034,6 +1118,18 @@ int lb_export_rho(lb_handle* h, int32_t box, double* rho) {
     CK(h->ops->rho_from_pop(st, h->d_boxes, box, (int)(h->t & 1), (int)(h->t % 3), -1, h->stage, nullptr));
     CK(cudaMemcpyAsync(rho, h->stage, sizeof(double) * 2 * B.N, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    return LB_OK;
+}
+
+int lb_export_phi(lb_handle* h, int32_t box, double* phi, double L[3], double* coverage) {
+    if (!h || box < 0 || box >= h->nb) return LB_EINVAL;
+    if (!h->initialised) return LB_EINVAL;
+    double Ld[3], cov;
+    int rc = structure_obs(h, box, Ld, &cov, phi);
+    if (rc != LB_OK) return rc;
+    if (L)
+        for (int a = 0; a < 3; a++) L[a] = Ld[a];
+    if (coverage) *coverage = cov;
     return LB_OK;
 }
 

@@ -327,6 +327,72 @@ static __global__ void __launch_bounds__(256) k_obs_partial(const BoxDev* __rest
     }
 }
 
+// Order parameter phi = rho^r - rho^b on fluid nodes, 0 on solid nodes
+// (Sec. VI), into phi[N] (canonical order, may be NULL), and per-block sums
+// of phi and phi^2 into partials[block][2] (fixed order within the block).
+template <class P>
+static __global__ void __launch_bounds__(256) k_phi(const BoxDev* __restrict__ boxes, int b, int rc,
+                                                    double* __restrict__ phi, double* __restrict__ partials) {
+    using R = typename P::real;
+    using R2 = typename Real2<R>::type;
+    const BoxDev& B = boxes[b];
+    const R2* __restrict__ r2 = rpair<R>(B.rho[rc]);
+    double s0 = 0.0, s1 = 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (!(B.flags[n] & FL_SOLID)) {
+            const R2 r = r2[n];
+            v = (double)r.x - (double)r.y;
+        }
+        if (phi) phi[n] = v;
+        s0 += v;
+        s1 += v * v;
+    }
+    __shared__ double s_r[8][2];
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_r[threadIdx.x >> 5][0] = s0;
+        s_r[threadIdx.x >> 5][1] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_r[w][threadIdx.x];
+        partials[blockIdx.x * 2 + threadIdx.x] = t;
+    }
+}
+
+// Interface coverage marks (the paper names the covered interface but
+// does not define it; the reading here): for every solid node of a particle
+// q of box b, the fluid D3Q19 neighbours with phi > 0 set bit 1 and those
+// with phi < 0 bit 2 of marks[q - pstart].  A particle covers the interface
+// when both bits are set.
+template <class P>
+static __global__ void k_coverage_marks(const BoxDev* __restrict__ boxes, int b, int rc, int* __restrict__ marks) {
+    using R = typename P::real;
+    using R2 = typename Real2<R>::type;
+    const BoxDev& B = boxes[b];
+    const R2* __restrict__ r2 = rpair<R>(B.rho[rc]);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
+        const int o = B.owner[n];
+        if (o < B.pstart || o >= B.pstart + B.np) continue;
+        int bits = 0;
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            const int m = nbr_index(B, n, cx(i), cy(i), cz(i));
+            if (B.flags[m] & FL_SOLID) continue;
+            const R2 r = r2[m];
+            const double v = (double)r.x - (double)r.y;
+            if (v > 0.0) bits |= 1;
+            else if (v < 0.0) bits |= 2;
+        }
+        if (bits) atomicOr(&marks[o - B.pstart], bits);
+    }
+}
+
 static __global__ void k_obs_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
     const int k = threadIdx.x;
     if (k >= OBS_W) return;

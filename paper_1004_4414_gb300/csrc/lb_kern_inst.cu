@@ -164,10 +164,20 @@ cudaError_t obs_partial(cudaStream_t st, const BoxDev* boxes, int b, int par, in
     k_obs_partial<PP><<<OBS_BLOCKS, 256, 0, st>>>(boxes, b, par, rc, partials);
     return cudaGetLastError();
 }
+
+cudaError_t phi_field(cudaStream_t st, const BoxDev* boxes, int b, int rc, double* phi, double* partials) {
+    k_phi<PP><<<OBS_BLOCKS, 256, 0, st>>>(boxes, b, rc, phi, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t coverage_marks(cudaStream_t st, const BoxDev* boxes, int b, int rc, int* marks) {
+    k_coverage_marks<PP><<<NODE_GRID, NODE_BLOCK, 0, st>>>(boxes, b, rc, marks);
+    return cudaGetLastError();
+}
 }  // namespace
 
 const LbOps OPS_NAME = {PP::id,       sizeof(RR),   setup,         step,       remap_apply, remap_finish,
                         shell_density, couple,     wall_shell,     init_pop,   export_dir, import_dir,   rho_from_pop,
-                        obs_partial};
+                        obs_partial,   phi_field,  coverage_marks};
 
 }  // namespace lbp

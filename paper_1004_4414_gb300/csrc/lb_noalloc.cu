@@ -24,10 +24,7 @@ namespace lbp {
 namespace {
 
 constexpr int FM_W = 8;          // values per partial, in the output order
-constexpr int FM_THREADS = 256;  // threads per block
-// nodes per block; the scratch holds one partial per block
-constexpr int64_t FM_CHUNK = (int64_t)LB_FIELD_MOMENTS_MAX_NODES / LB_FIELD_MOMENTS_MAX_BLOCKS;
-static_assert(FM_CHUNK * LB_FIELD_MOMENTS_MAX_BLOCKS == LB_FIELD_MOMENTS_MAX_NODES, "chunking");
+constexpr int FM_THREADS = 256;  // threads per block; the scratch holds one partial per block
 
 // Scratch: one partial of FM_W doubles per block (256 KB in all).  Every
 // call writes the partials of the blocks it launches before its final pass
@@ -35,15 +32,16 @@ static_assert(FM_CHUNK * LB_FIELD_MOMENTS_MAX_BLOCKS == LB_FIELD_MOMENTS_MAX_NOD
 // one call are simply overwritten by the next.
 __device__ __align__(256) double g_fm_scratch[LB_FIELD_MOMENTS_MAX_BLOCKS * FM_W];
 
-// Block b sums nodes [b * chunk, min(N, (b + 1) * chunk)) of f[2][19][N]
-// (owner[n] != -1 marks a solid node, whose populations are ignored).
+// The blocks sum the nodes of f[2][19][N] grid-stride (block b takes nodes
+// b * FM_THREADS + t + k * gridDim.x * FM_THREADS), so a small field still
+// spreads over many blocks; owner[n] != -1 marks a solid node, whose
+// populations are ignored.
 __global__ void __launch_bounds__(FM_THREADS) k_fm_partial(const double* __restrict__ f,
                                                            const int32_t* __restrict__ owner, int64_t N,
-                                                           int64_t chunk, double* __restrict__ partials) {
+                                                           double* __restrict__ partials) {
     double v[FM_W] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int64_t lo = (int64_t)blockIdx.x * chunk;
-    const int64_t hi = lo + chunk < N ? lo + chunk : N;
-    for (int64_t n = lo + threadIdx.x; n < hi; n += FM_THREADS) {
+    const int64_t step = (int64_t)gridDim.x * FM_THREADS;
+    for (int64_t n = (int64_t)blockIdx.x * FM_THREADS + threadIdx.x; n < N; n += step) {
         if (owner[n] != -1) {
             v[7] += 1.0;
             continue;
@@ -142,8 +140,10 @@ extern "C" int lb_field_moments(const double* d_f, const int32_t* d_owner, int64
     const int rc = scratch_for_current_device(&scratch);
     if (rc != LB_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const int nblocks = (int)((n_nodes + FM_CHUNK - 1) / FM_CHUNK);
-    if (nblocks > 0) k_fm_partial<<<nblocks, FM_THREADS, 0, st>>>(d_f, d_owner, n_nodes, FM_CHUNK, scratch);
+    // one block per FM_THREADS nodes, at most the scratch's partials
+    const int64_t want = (n_nodes + FM_THREADS - 1) / FM_THREADS;
+    const int nblocks = (int)(want < LB_FIELD_MOMENTS_MAX_BLOCKS ? want : LB_FIELD_MOMENTS_MAX_BLOCKS);
+    if (nblocks > 0) k_fm_partial<<<nblocks, FM_THREADS, 0, st>>>(d_f, d_owner, n_nodes, scratch);
     k_fm_final<<<1, 32, 0, st>>>(scratch, nblocks, d_out);
     return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
 }

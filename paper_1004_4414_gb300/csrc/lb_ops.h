@@ -29,6 +29,10 @@ struct LbOps {
     cudaError_t (*rho_from_pop)(cudaStream_t st, const BoxDev* boxes, int b, int par, int src, int rc, double* out,
                                 double* mass_out);
     cudaError_t (*obs_partial)(cudaStream_t st, const BoxDev* boxes, int b, int par, int rc, double* partials);
+    // order parameter of box b (phi[N] may be NULL) and OBS_BLOCKS x {sum phi, sum phi^2}
+    cudaError_t (*phi_field)(cudaStream_t st, const BoxDev* boxes, int b, int rc, double* phi, double* partials);
+    // interface coverage marks of the particles of box b (marks zeroed by the caller)
+    cudaError_t (*coverage_marks)(cudaStream_t st, const BoxDev* boxes, int b, int rc, int* marks);
 };
 
 extern const LbOps lb_ops_fp64, lb_ops_fp32, lb_ops_fp16, lb_ops_bf16;

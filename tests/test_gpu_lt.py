@@ -2,7 +2,8 @@
 (Eq. eq:domsize) and interface coverage of the CUDA path against the FP64
 oracle on the 128^3 configuration (50:50 of total density 0.7,
 alpha = 0.15, R = 5, contact angle 90 deg, particle density 3, seed 2),
-every 100 steps up to 1000.  The oracle's values are stored in
+every 100 steps up to 1000, read through lb_observables.  The oracle's
+values are stored in
 tests/golden/lt_c128.json, written by tests/golden/make_lt_golden.py (which
 uses only oracle/).  Tolerance: 2 % of the oracle's value."""
 import json
@@ -10,8 +11,6 @@ import os
 
 import numpy as np
 import pytest
-
-from oracle import analysis
 
 pytestmark = pytest.mark.gpu
 
@@ -29,15 +28,12 @@ def test_domain_size_and_coverage_follow_the_oracle(precision):
     sim = Simulation(dict(p, precision=precision))
     sim.init_from_seed(g["seed"])
     assert sim.n_particles[0] == g["n_particles"]
-    shape = (p["nz"], p["ny"], p["nx"])
     step = 0
     for k, target in enumerate(g["steps"]):
         sim.step(target - step)
         step = target
-        phi = sim.phi(0)  # 0 on solid nodes
-        owner = sim.export_state(0, f=False)["owner"].reshape(shape)
-        L = np.array(analysis.domain_size(phi))
-        cov = analysis.coverage(phi, owner, sim.n_particles[0])
+        ob = sim.observables(0)  # domain size and coverage computed by the library
+        L, cov = np.array(ob["L"]), ob["coverage"]
         Lo = np.array(g["L"][k])
         assert np.all(np.abs(L - Lo) <= 0.02 * Lo), (precision, target, L, Lo)
         assert abs(cov - g["coverage"][k]) <= 0.02 * g["coverage"][k], (precision, target, cov, g["coverage"][k])

@@ -40,6 +40,17 @@ def _check(binding, sim, out):
     np.testing.assert_allclose(v[5], ob["max_u"], rtol=1e-12, atol=0)
     assert v[6] == ob["n_fluid"] and v[7] == ob["n_solid"]
     assert ob["n_fluid"] + ob["n_solid"] == owner.numel()
+    # and against plain NumPy sums of the exported populations
+    fl = st["owner"] == -1
+    ff = st["f"][:, :, fl]
+    c = np.array([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
+                  [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
+                  [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]], float)
+    np.testing.assert_allclose(v[0:2], ff.sum(axis=(1, 2)), rtol=1e-12, atol=0)
+    j = np.einsum("ai,cin->an", c, ff)
+    np.testing.assert_allclose(v[2:5], j.sum(axis=1), rtol=0, atol=1e-12 * mass.sum())
+    np.testing.assert_allclose(v[5], np.max(np.linalg.norm(j, axis=0) / ff.sum(axis=(0, 1))), rtol=1e-12)
+    assert v[6] == fl.sum() and v[7] == (~fl).sum()
     return v
 
 
@@ -51,13 +62,14 @@ def test_field_moments_matches_observables_on_two_calls_in_a_row():
     binding, _ = _lib()
     out = torch.empty(8, dtype=torch.float64, device="cuda")
     base = dict(n_particles=6, radius=4.0, rho_init=(0.42, 0.28), color=-0.03)
-    # first call: 163,840 nodes -> two blocks of the scratch, the second ragged
+    # first call: 163,840 nodes -> 640 blocks of the scratch
     big = Simulation(dict(base, nx=64, ny=64, nz=40))
     big.init_from_seed(11)
     big.step(9)
     v1 = _check(binding, big, out)
     big.close()
-    # second call: one block; a partial left by the first call must not leak in
+    # second call: 47,520 nodes -> 186 blocks, the last one ragged; the
+    # partials the first call left in blocks 186..639 must not leak in
     small = Simulation(dict(base, nx=40, ny=36, nz=33))
     small.init_from_seed(12)
     small.step(14)
