@@ -85,7 +85,12 @@ typedef struct {
     int32_t vel_mode;            /* 0: Shan-Chen common velocity in f^eq, 1: each component's own velocity */
     int32_t fixed_particles;     /* 1: particles keep X, U, omega (prescribed motion; tests) */
     int32_t precision;           /* LB_FP64 / LB_FP32 / LB_FP16_DEV / LB_BF16_DEV, same for all boxes */
-    int32_t reserved;            /* must be 0 */
+    int32_t implicit_update;     /* 0: the paper's explicit particle velocity update (Sec. III); 1: the
+                                    moving-wall term of the links taken at the new velocity, (M + Z) dV =
+                                    (F, T) with Z the links' drag tensor, and the fluid given the same
+                                    change, which keeps momentum exact (a reading; needed for light
+                                    particles in contact, e.g. density 1 in fluid of density 0.7);
+                                    spheres only */
     double aspect;               /* particle shape: 0 or 1 sphere; otherwise a spheroid with semi-axes
                                     R, R, c = aspect R about a body axis (0.1 <= aspect <= 10); see lb_set_axes */
 } lb_params;

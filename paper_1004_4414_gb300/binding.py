@@ -43,7 +43,7 @@ class LbParams(C.Structure):
         ("vel_mode", C.c_int32),
         ("fixed_particles", C.c_int32),
         ("precision", C.c_int32),
-        ("reserved", C.c_int32),
+        ("implicit_update", C.c_int32),
         ("aspect", C.c_double),
     ]
 
@@ -73,7 +73,7 @@ DEFAULTS = dict(
     sc_weight=(2.0, 1.0), rho_init=(0.7, 0.7), noise_amp=0.01, volume_fraction=0.0,
     radius=5.0, particle_density=1.0, color=0.0, contact_angle_deg=math.nan,
     k_hertz=100.0, lub_cut=2.0 / 3.0, lub_min=0.1, mass_corr_c0=0.0,
-    body_force=(0.0, 0.0, 0.0), vel_mode=0, fixed_particles=0, precision=LB_FP32, reserved=0, aspect=1.0,
+    body_force=(0.0, 0.0, 0.0), vel_mode=0, fixed_particles=0, precision=LB_FP32, implicit_update=0, aspect=1.0,
 )
 
 ABI_FUNCTIONS = (

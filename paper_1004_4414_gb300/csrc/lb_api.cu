@@ -100,7 +100,8 @@ int validate(const lb_params* bx, int nb) {
         if (!(p.rho_init[0] > 0.0) || !(p.rho_init[1] > 0.0)) return LB_EINVAL;
         if (p.precision != bx[0].precision || !ops_for(p.precision)) return LB_EINVAL;
         if (p.vel_mode != 0 && p.vel_mode != 1) return LB_EINVAL;
-        if (p.reserved != 0) return LB_EINVAL;
+        if (p.implicit_update != 0 && p.implicit_update != 1) return LB_EINVAL;
+        if (p.implicit_update && aspect_of(p) != 1.0) return LB_EINVAL;  // spheres only
         if (!(p.aspect >= 0.0 && p.aspect <= 10.0) || (p.aspect != 0.0 && !(p.aspect >= 0.1))) return LB_EINVAL;
         if (derive_np(p) < 0) return LB_EINVAL;
         if (!(p.lub_min > 0.0) || !(p.lub_cut > p.lub_min)) return LB_EINVAL;
@@ -273,6 +274,8 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     sh.shell_dirty = cv.take<int>(NPa);
     sh.xref = cv.take<float>((size_t)NPa * 3);
     sh.exact = cv.take<int>(NPa);
+    sh.zdrag = cv.take<double>((size_t)NPa * 21);
+    sh.dv = cv.take<double>((size_t)NPa * 6);
     sh.err = cv.take<int>(1);
     sh.counters = cv.take<unsigned long long>((size_t)nb * 2);
     BoxDev* d_boxes = cv.take<BoxDev>(nb);
@@ -307,6 +310,7 @@ void fill_params(lb_handle* h) {
         B.has_walls = h->has_walls[b];
         B.vel_mode = p.vel_mode;
         B.fixed = p.fixed_particles;
+        B.implicit = p.implicit_update;
         for (int c = 0; c < 2; c++) {
             B.tau[c] = p.tau[c];
             B.inv_tau[c] = 1.0 / p.tau[c];
@@ -443,10 +447,20 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     }
     if (NP > 0) {
         const int pg = (NP + 255) / 256;
-        CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, NP));
+        int impl = 0;
+        for (const auto& p : h->params) impl |= p.implicit_update;
+        CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, impl, NP));
         k_md_forces<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
-        k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
-        launches += 3;
+        if (impl) {
+            // implicit update: velocities, the fluid's share on the links, positions
+            k_md_solve<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+            CK(h->ops->couple_correct(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, NP));
+            k_md_move<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+            launches += 5;
+        } else {
+            k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+            launches += 3;
+        }
     }
     h->launches_since = launches;
     if (prof) h->prof_total += launches;

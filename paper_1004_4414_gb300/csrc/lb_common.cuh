@@ -73,7 +73,7 @@ struct BoxDev {
     int has_walls;
     int vel_mode;
     int fixed;
-    int pad0;
+    int implicit;               // 1: implicit particle velocity update (spheres)
     double tau[2], inv_tau[2];
     double g, rho0, scw_axis, scw_diag;
     double rho_ref[2];          // reference density of the deviation storage
@@ -128,6 +128,8 @@ struct Shared {
     int* shell_dirty;           // [NP] nonzero: rebuild the shell list (events nearby, or a new state)
     int shell_cap;
     float* xref;                // [NP][3] position at the last remap (FP32 copy)
+    double* zdrag;              // [NP][21] drag tensor Z of the links (upper triangle, row-major; implicit update)
+    double* dv;                 // [NP][6] velocity change dV of the implicit update
     int* exact;                 // [NP] 1: p owns exactly the nodes inside it at xref (remap fast path)
     int* err;                   // [1] sticky error bits
     unsigned long long* counters; // [n_boxes][2] n_cover, n_uncover

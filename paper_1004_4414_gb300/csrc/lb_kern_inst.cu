@@ -127,9 +127,17 @@ cudaError_t shell_density(cudaStream_t st, const BoxDev* boxes, Shared sh, int r
 }
 
 cudaError_t couple(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par, int reflect,
-                   int NP) {
+                   int impl, int NP) {
     if (NP <= 0) return cudaSuccess;
-    k_couple<PP><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot, par, reflect);
+    if (impl) k_couple<PP, true><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot, par, reflect);
+    else k_couple<PP, false><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot, par, reflect);
+    return cudaGetLastError();
+}
+
+cudaError_t couple_correct(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par,
+                           int reflect, int NP) {
+    if (NP <= 0) return cudaSuccess;
+    k_couple_correct<PP><<<NP, COUPLE_THREADS, 0, st>>>(boxes, sh, rc, rn, mslot, par, reflect);
     return cudaGetLastError();
 }
 
@@ -177,7 +185,7 @@ cudaError_t coverage_marks(cudaStream_t st, const BoxDev* boxes, int b, int rc, 
 }  // namespace
 
 const LbOps OPS_NAME = {PP::id,       sizeof(RR),   setup,         step,       remap_apply, remap_finish,
-                        shell_density, couple,     wall_shell,     init_pop,   export_dir, import_dir,   rho_from_pop,
-                        obs_partial,   phi_field,  coverage_marks};
+                        shell_density, couple,     couple_correct, wall_shell, init_pop,   export_dir,   import_dir,
+                        rho_from_pop,  obs_partial, phi_field,     coverage_marks};
 
 }  // namespace lbp

@@ -17,8 +17,11 @@ struct LbOps {
     cudaError_t (*remap_apply)(int par, cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int mslot_cur);
     cudaError_t (*remap_finish)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc);
     cudaError_t (*shell_density)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int NP);
+    // impl: some box uses the implicit velocity update (the drag tensor is summed)
     cudaError_t (*couple)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par,
-                          int reflect, int NP);
+                          int reflect, int impl, int NP);
+    cudaError_t (*couple_correct)(cudaStream_t st, const BoxDev* boxes, Shared sh, int rc, int rn, int mslot, int par,
+                                  int reflect, int NP);
     cudaError_t (*wall_shell)(cudaStream_t st, const BoxDev* boxes, int b, int rc);
     cudaError_t (*init_pop)(cudaStream_t st, const BoxDev* boxes, int b, const double* rho_field,
                             const double* u_field, uint64_t s_red, uint64_t s_blue, double noise, int rc,

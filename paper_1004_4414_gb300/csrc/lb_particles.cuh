@@ -824,8 +824,12 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
 // fluid node.  Static walls (owner -2) reflect without a wall
 // term and need nothing here.  rho^c(x) is the density field of the current
 // step (the fused step's moments up to rounding order).
+// IMPL: the box may use the implicit velocity update; its links then also
+// sum the drag tensor Z = sum_links sum_c 6 zeta_j rho^c(x) a a^T with
+// a = (c_j, r x c_j) (upper triangle into zdrag).
 constexpr int COUPLE_THREADS = 128;
-template <class P>
+constexpr int NZ = 21;  // entries of the symmetric 6 x 6 drag tensor
+template <class P, bool IMPL>
 static __global__ void __launch_bounds__(COUPLE_THREADS)
     k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot, int par, int reflect) {
     using R = typename P::real;
@@ -833,7 +837,8 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     using R2 = typename Real2<R>::type;
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ R s_red[COUPLE_THREADS / 32][8];
+    constexpr int NRED = 8 + (IMPL ? NZ : 0);
+    __shared__ R s_red[COUPLE_THREADS / 32][NRED];
     const int p = blockIdx.x;
     const BoxDev& B = boxes[sh.pbox[p]];
     const Pop<P> pop(B);
@@ -855,6 +860,10 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const bool at_s = (par == 0) == (reflect != 0);
     R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     R dm0 = R(0), dm1 = R(0);
+    R zz[IMPL ? NZ : 1];
+#pragma unroll
+    for (int e = 0; e < (IMPL ? NZ : 1); e++) zz[e] = R(0);
+    const bool impl = IMPL && B.implicit;
     // the shell nodes found by k_shell_density in this step, one per thread
     const int ns = sh.shell_n[p];
     const int4* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
@@ -954,6 +963,19 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
                 acc[3] += r1 * F2 - r2 * F1;
                 acc[4] += r2 * F0 - r0 * F2;
                 acc[5] += r0 * F1 - r1 * F0;
+                if constexpr (IMPL) {
+                    if (impl) {
+                        // a = (c_j, r x c_j), c_j = -c_i
+                        const R a[6] = {-(R)cx(i), -(R)cy(i), -(R)cz(i), -(r1 * (R)cz(i) - r2 * (R)cy(i)),
+                                        -(r2 * (R)cx(i) - r0 * (R)cz(i)), -(r0 * (R)cy(i) - r1 * (R)cx(i))};
+                        const R kz = R(6) * wgt<R>(i) * (rm[t].x + rm[t].y);
+                        int e = 0;
+#pragma unroll
+                        for (int u = 0; u < 6; u++)
+#pragma unroll
+                            for (int v = u; v < 6; v++) zz[e++] += kz * a[u] * a[v];
+                    }
+                }
             }
         }
         // the Shan-Chen force of the virtual fluid at s on the particle
@@ -973,22 +995,122 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
         for (int a = 0; a < 6; a++) acc[a] += __shfl_xor_sync(FULL, acc[a], o);
         dm0 += __shfl_xor_sync(FULL, dm0, o);
         dm1 += __shfl_xor_sync(FULL, dm1, o);
+        if constexpr (IMPL) {
+#pragma unroll
+            for (int e = 0; e < NZ; e++) zz[e] += __shfl_xor_sync(FULL, zz[e], o);
+        }
     }
     if (lane == 0) {
 #pragma unroll
         for (int a = 0; a < 6; a++) s_red[wib][a] = acc[a];
         s_red[wib][6] = dm0;
         s_red[wib][7] = dm1;
+        if constexpr (IMPL) {
+#pragma unroll
+            for (int e = 0; e < NZ; e++) s_red[wib][8 + e] = zz[e];
+        }
     }
     __syncthreads();
-    if (threadIdx.x < 8) {
+    if (threadIdx.x < NRED) {
         const int a = threadIdx.x;
         R v = s_red[0][a];
 #pragma unroll
         for (int w = 1; w < COUPLE_THREADS / 32; w++) v += s_red[w][a];
-        // the only writer of this particle's accumulator in this kernel
+        // the only writer of this particle's accumulators in this kernel
         if (a < 6) sh.force[(size_t)p * 6 + a] += (double)v;
-        else if (v != R(0)) atomicAdd(&mass_acc[mslot * 2 + (a - 6)], (double)v);
+        else if (a < 8) {
+            if (v != R(0)) atomicAdd(&mass_acc[mslot * 2 + (a - 6)], (double)v);
+        } else if (impl) {
+            sh.zdrag[(size_t)p * NZ + (a - 8)] = (double)v;
+        }
+    }
+}
+
+// Implicit update, fluid side (after k_md_solve): every link of particle p
+// gets the wall term of the velocity change, -6 zeta_j rho^c(x) a.dV, on
+// the reflected pair that the next step reads, and the same change enters
+// rho(t+1) of the fluid node and the step's fluid mass.  The links, the
+// positions and the densities are those k_couple used in this step, so the
+// fluid's momentum change is the opposite of -Z dV on the particle.
+template <class P>
+static __global__ void __launch_bounds__(COUPLE_THREADS)
+    k_couple_correct(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot, int par, int reflect) {
+    using R = typename P::real;
+    using S2 = typename P::st2;
+    using R2 = typename Real2<R>::type;
+    const unsigned FULL = 0xffffffffu;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ R s_red[COUPLE_THREADS / 32][2];
+    const int p = blockIdx.x;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    if (!B.implicit || B.fixed) return;  // the whole block leaves together
+    const Pop<P> pop(B);
+    const auto& ps = part_ptr<R>(sh)[p];
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const int nxy = nx * ny;
+    const R2* __restrict__ rcur2 = rpair<R>(B.rho[rc]);
+    R2* __restrict__ rnext2 = rpair<R>(B.rho[rn]);
+    const R Lx = (R)nx, Ly = (R)ny, Lz = (R)nz;
+    const R X0 = (R)ps.X[0], X1 = (R)ps.X[1], X2 = (R)ps.X[2];
+    R dV[6];
+#pragma unroll
+    for (int u = 0; u < 6; u++) dV[u] = (R)sh.dv[(size_t)p * 6 + u];
+    const bool at_s = (par == 0) == (reflect != 0);
+    R dm0 = R(0), dm1 = R(0);
+    const int ns = sh.shell_n[p];
+    const int4* __restrict__ list = sh.shell_list + (size_t)p * sh.shell_cap;
+    for (int k = threadIdx.x; k < ns; k += COUPLE_THREADS) {
+        const int4 e = list[k];
+        const int s = e.x;
+        const unsigned fmask = (unsigned)e.y;
+        const int gx = e.z & 0xffff, gy = (int)((unsigned)e.z >> 16), gz = e.w;
+        const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
+        const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
+        const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
+        const R rs0 = mimg_r<R>((R)gx - X0, Lx), rs1 = mimg_r<R>((R)gy - X1, Ly), rs2 = mimg_r<R>((R)gz - X2, Lz);
+#pragma unroll
+        for (int i = 1; i < 19; i++) {
+            if (!((fmask >> i) & 1u)) continue;
+            const int m = s + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) + (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) +
+                          (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
+            const R r0 = rs0 + R(0.5) * (R)cx(i), r1 = rs1 + R(0.5) * (R)cy(i), r2 = rs2 + R(0.5) * (R)cz(i);
+            // a.dV with a = (c_j, r x c_j), c_j = -c_i
+            const R ad = -((R)cx(i) * dV[0] + (R)cy(i) * dV[1] + (R)cz(i) * dV[2]) -
+                         ((r1 * (R)cz(i) - r2 * (R)cy(i)) * dV[3] + (r2 * (R)cx(i) - r0 * (R)cz(i)) * dV[4] +
+                          (r0 * (R)cy(i) - r1 * (R)cx(i)) * dV[5]);
+            const R2 rm = __ldg(rcur2 + m);
+            const R d0 = R(6) * wgt<R>(i) * rm.x * ad, d1 = R(6) * wgt<R>(i) * rm.y * ad;
+            // the slot k_couple wrote the reflected pair to
+            S2* const to = (at_s == (reflect != 0)) ? pop.pair(opp(i), s) : pop.pair(i, m);
+            S2 q = *to;
+            if constexpr (P::dev) {
+                q.x = pop.f_to_dev(0, i, pop.dev_to_f(0, i, q.x) - d0);
+                q.y = pop.f_to_dev(1, i, pop.dev_to_f(1, i, q.y) - d1);
+            } else {
+                q.x -= d0;
+                q.y -= d1;
+            }
+            *to = q;
+            red_add2<R>(rnext2 + m, -d0, -d1);
+            dm0 -= d0;
+            dm1 -= d1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dm0 += __shfl_xor_sync(FULL, dm0, o);
+        dm1 += __shfl_xor_sync(FULL, dm1, o);
+    }
+    if (lane == 0) {
+        s_red[wib][0] = dm0;
+        s_red[wib][1] = dm1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        R v = s_red[0][threadIdx.x];
+#pragma unroll
+        for (int w = 1; w < COUPLE_THREADS / 32; w++) v += s_red[w][threadIdx.x];
+        if (v != R(0)) atomicAdd(&B.mass_acc[mslot * 2 + threadIdx.x], (double)v);
     }
 }
 
@@ -1105,6 +1227,107 @@ __device__ __forceinline__ void rotate_spheroid(const BoxDev& B, double W[3], do
         for (int a = 0; a < 3; a++) e[a] = en[a] / nn;
     }
     inertia(L, W, true);
+}
+
+// Solve A x = b for a 6 x 6 system by Gaussian elimination with partial
+// pivoting; A (row-major) and b are overwritten.
+__device__ __forceinline__ void solve6(double A[36], double b[6], double x[6]) {
+    for (int col = 0; col < 6; col++) {
+        int piv = col;
+        for (int r = col + 1; r < 6; r++)
+            if (fabs(A[6 * r + col]) > fabs(A[6 * piv + col])) piv = r;
+        if (piv != col) {
+            for (int v = 0; v < 6; v++) {
+                const double t = A[6 * col + v];
+                A[6 * col + v] = A[6 * piv + v];
+                A[6 * piv + v] = t;
+            }
+            const double t = b[col];
+            b[col] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = col + 1; r < 6; r++) {
+            const double f = A[6 * r + col] / A[6 * col + col];
+            for (int v = col; v < 6; v++) A[6 * r + v] -= f * A[6 * col + v];
+            b[r] -= f * b[col];
+        }
+    }
+    for (int r = 5; r >= 0; r--) {
+        double t = b[r];
+        for (int v = r + 1; v < 6; v++) t -= A[6 * r + v] * x[v];
+        x[r] = t / A[6 * r + r];
+    }
+}
+
+// Velocity half of the MD step for handles where some box uses the implicit
+// update (k_md_move then moves the particles, after k_couple_correct has
+// given the fluid its share).  Implicit boxes: (M + Z) dV = (F, T) with
+// M = diag(m, m, m, J, J, J) and the links' drag tensor Z of k_couple, then
+// U += dU, omega += d omega (dV kept for k_couple_correct).  Other boxes: the
+// explicit update of k_md_integrate.  Accumulators zeroed.
+static __global__ void k_md_solve(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    double* fp = &sh.force[(size_t)p * 6];
+    PartState ps = sh.part[p];
+    double dv[6] = {0, 0, 0, 0, 0, 0};
+    if (!B.fixed) {
+        if (B.implicit) {
+            double A[36], b[6];
+            int e = 0;
+            for (int u = 0; u < 6; u++)
+                for (int v = u; v < 6; v++) {
+                    const double z = sh.zdrag[(size_t)p * NZ + e++];
+                    A[6 * u + v] = z;
+                    A[6 * v + u] = z;
+                }
+            for (int u = 0; u < 3; u++) {
+                A[7 * u] += B.mass;
+                A[7 * (u + 3)] += B.inertia;
+                b[u] = fp[u];
+                b[u + 3] = fp[3 + u];
+            }
+            solve6(A, b, dv);
+            for (int a = 0; a < 3; a++) {
+                ps.U[a] += dv[a];
+                ps.W[a] += dv[3 + a];
+            }
+        } else {
+            if (B.aspect != 1.0) rotate_spheroid(B, ps.W, ps.E, fp + 3);
+            for (int a = 0; a < 3; a++) {
+                ps.U[a] += fp[a] / B.mass;
+                if (B.aspect == 1.0) ps.W[a] += fp[3 + a] / B.inertia;
+            }
+        }
+        if (!(ps.U[0] * ps.U[0] + ps.U[1] * ps.U[1] + ps.U[2] * ps.U[2] < 1.0)) set_err(sh.err, ERR_FAST_PARTICLE);
+        sh.part[p] = ps;
+    }
+    for (int a = 0; a < 6; a++) {
+        sh.dv[(size_t)p * 6 + a] = dv[a];
+        fp[a] = 0.0;
+    }
+}
+
+// Position half: X += U (periodic) and the FP32 copy.
+static __global__ void k_md_move(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const BoxDev& B = boxes[sh.pbox[p]];
+    if (B.fixed) return;
+    PartState ps = sh.part[p];
+    const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
+    PartStateF pf;
+    for (int a = 0; a < 3; a++) {
+        double xn = ps.X[a] + ps.U[a];
+        xn -= L[a] * floor(xn / L[a]);
+        if (xn >= L[a]) xn -= L[a];
+        sh.part[p].X[a] = xn;
+        pf.X[a] = (float)xn;
+        pf.U[a] = (float)ps.U[a];
+        pf.W[a] = (float)ps.W[a];
+    }
+    sh.partf[p] = pf;
 }
 
 // leap-frog: U += F/m, omega += T/J (spheroids: rotate_spheroid), X += U

@@ -60,7 +60,8 @@ def test_invalid_parameters_rejected(lib):
 
     n = C.c_size_t(0)
     nan, inf = float("nan"), float("inf")
-    for bad in (dict(nx=0), dict(tau=(0.5, 1.0)), dict(precision=7), dict(reserved=1), dict(radius=0.0),
+    for bad in (dict(nx=0), dict(tau=(0.5, 1.0)), dict(precision=7), dict(radius=0.0),
+                dict(implicit_update=2), dict(implicit_update=1, aspect=1.5),
                 dict(rho_init=(0.0, 0.7)), dict(lub_min=0.0), dict(lub_cut=0.1, lub_min=0.1),
                 dict(aspect=0.05), dict(aspect=11.0), dict(aspect=-1.0), dict(aspect=nan),
                 dict(ny=0), dict(nz=-3), dict(nx=65536), dict(nx=2048, ny=2048, nz=512),
