@@ -36,6 +36,20 @@ def lamellae(shape, axis=2, rho_major=0.7, rho_minor=0.0, width=None, offset=0):
     return rho
 
 
+def layers(shape, period, rho_major=0.6, rho_minor=0.1, amp=0.01, seed=0):
+    """Alternating red and blue layers along z, each period / 2 nodes thick
+    (red first), with node noise U(-amp, amp) on both components."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    z = np.indices((nz, ny, nx))[0].reshape(-1)
+    red = (z % period) < period // 2
+    N = nx * ny * nz
+    rho = np.empty((2, N))
+    rho[0] = np.where(red, rho_major, rho_minor) + amp * (2.0 * rng.random(N) - 1.0)
+    rho[1] = np.where(red, rho_minor, rho_major) + amp * (2.0 * rng.random(N) - 1.0)
+    return rho
+
+
 def spheres(shape, radius, n, seed=0, min_gap=0.0, vmax=0.0, wmax=0.0, max_tries=100000):
     """n centres with minimum-image distance >= 2R + min_gap, uniform
     velocities in [-vmax, vmax] and angular velocities in [-wmax, wmax]."""
