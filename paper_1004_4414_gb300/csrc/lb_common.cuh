@@ -377,6 +377,25 @@ __device__ __forceinline__ typename Real2<R>::type* rpair(void* ring) {
     return reinterpret_cast<typename Real2<R>::type*>(ring);
 }
 
+// ------------------------------------------- component-pair arithmetic
+// The (red, blue) values of a node in one float2 / double2.  On sm_100 and
+// later one packed FP32 instruction (FADD2, FMUL2, FFMA2) does both
+// components; FP64 pairs take two scalar instructions.
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ double2 p2(double a) { return make_double2(a, a); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+// a b + c with one rounding
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+// a - b (exact product by -1, one rounding)
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
 // ------------------------------------------------------------ helpers
 __device__ __forceinline__ int wrapi(int a, int n) {
     a %= n;

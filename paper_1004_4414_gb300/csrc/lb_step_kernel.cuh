@@ -152,9 +152,11 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
     using S = typename P::st;
     using SM = StepSmem<R, TY>;
     constexpr int W2 = SM::W2, H2 = SM::H2;
+    using R2 = typename Real2<R>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* s_psi = reinterpret_cast<R*>(smem_raw);                         // [3 slots][2][H2][W2]
-    R* s_yb = s_psi + SM::psi_elems;                                   // [6][2][TY][32]
+    // Psi window: (Psi^r, Psi^b) pairs, [3 slots][H2][W2]
+    R2* s_psi2 = reinterpret_cast<R2*>(smem_raw);
+    R* s_yb = reinterpret_cast<R*>(smem_raw) + SM::psi_elems;          // [6][2][TY][32]
     uint8_t* s_flg = reinterpret_cast<uint8_t*>(s_yb + SM::yb_elems);  // [3 slots][H2][W2]
     __shared__ double s_red[2][TY];
 
@@ -162,7 +164,6 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
     const BoxDev& B = boxes[T.box];
     const int nx = B.nx, ny = B.ny, nz = B.nz, N = B.N;
     const int nxy = nx * ny;
-    using R2 = typename Real2<R>::type;
     using S2 = typename P::st2;
     const R2* __restrict__ rcur = rpair<R>(B.rho[rc]);
     R* __restrict__ rnext = reinterpret_cast<R*>(B.rho[rn]);  // component c of node m: rnext[2 m + c]
@@ -185,9 +186,12 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
     const int oym = (y == 0) ? (ny - 1) * nx : -nx, oyp = (y == ny - 1) ? -(ny - 1) * nx : nx;
     const int nxyc = x + nx * y;  // in-plane index
 
-    auto PSI = [&](int s, int c, int r, int k) -> R& { return s_psi[((s * 2 + c) * H2 + r) * W2 + k]; };
+    auto PSI2 = [&](int s, int r, int k) -> R2& { return s_psi2[(s * H2 + r) * W2 + k]; };
     auto FLG = [&](int s, int r, int k) -> uint8_t& { return s_flg[(s * H2 + r) * W2 + k]; };
-    auto YB = [&](int q, int c, int r, int k) -> R& { return s_yb[((q * 2 + c) * TY + r) * 32 + k]; };
+    // this thread's node in a window plane; neighbours at constant offsets
+    const int tofs = (ly + 1) * W2 + lx + 1;
+    R2* const s_yb2 = reinterpret_cast<R2*>(s_yb);  // row exchange: [6][TY][32] pairs
+    auto YB2 = [&](int q, int r, int k) -> R2& { return s_yb2[(q * TY + r) * 32 + k]; };
 
     // The window of a plane: Psi and flags of the tile (one node per
     // thread) and of its one-node ring (thread tid < nring takes ring node
@@ -240,13 +244,11 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
     };
     auto store_window = [&](const WinRaw& v, int s) {
         if (active) {
-            PSI(s, 0, ly + 1, lx + 1) = psi_of<R>(v.a0, rho0, irho0);
-            PSI(s, 1, ly + 1, lx + 1) = psi_of<R>(v.a1, rho0, irho0);
+            PSI2(s, ly + 1, lx + 1) = mk2<R2>(psi_of<R>(v.a0, rho0, irho0), psi_of<R>(v.a1, rho0, irho0));
             FLG(s, ly + 1, lx + 1) = v.af;
         }
         if (tid < nring) {
-            PSI(s, 0, ring_r, ring_k) = psi_of<R>(v.b0, rho0, irho0);
-            PSI(s, 1, ring_r, ring_k) = psi_of<R>(v.b1, rho0, irho0);
+            PSI2(s, ring_r, ring_k) = mk2<R2>(psi_of<R>(v.b0, rho0, irho0), psi_of<R>(v.b1, rho0, irho0));
             FLG(s, ring_r, ring_k) = v.bf;
         }
     };
@@ -268,10 +270,10 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
         rq1[0] = v1.a0;
         rq1[1] = v1.a1;
     }
-    R acc[3][2];  // own-column partial densities of planes z-1, z, z+1
+    R2 acc[3];  // own-column partial densities of planes z-1, z, z+1
 #pragma unroll
-    for (int k = 0; k < 3; k++) acc[k][0] = acc[k][1] = R(0);
-    R msum0 = R(0), msum1 = R(0);  // fluid mass sent (own precision: Eq. masscorr uses small differences)
+    for (int k = 0; k < 3; k++) acc[k] = p2(R(0));
+    R2 msum = p2(R(0));  // fluid mass sent (own precision: Eq. masscorr uses small differences)
     __syncthreads();
 
     for (int z = z0; z < z0 + d; z++) {
@@ -287,255 +289,227 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
             return (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) + (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) +
                    (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
         };
-        auto slot_dz = [&](int dz) { return dz < 0 ? sm_ : (dz > 0 ? sp_ : sc_); };
         // offset of the node (x, y + dy, z + dz) of scatter group q
         auto yz = [&](int q) -> int {
             const int dy = grp_dy(q), dz = grp_dz(q);
             return (dy < 0 ? oym : (dy > 0 ? oyp : 0)) + (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
         };
 
-        const uint8_t fl = active ? FLG(sc_, ly + 1, lx + 1) : FL_SOLID;
+        // window planes z - 1, z, z + 1 at this thread's node
+        const R2* const wp[3] = {s_psi2 + sm_ * SM::PLANE + tofs, s_psi2 + sc_ * SM::PLANE + tofs,
+                                 s_psi2 + sp_ * SM::PLANE + tofs};
+        const uint8_t* const wf[3] = {s_flg + sm_ * SM::PLANE + tofs, s_flg + sc_ * SM::PLANE + tofs,
+                                      s_flg + sp_ * SM::PLANE + tofs};
+        const uint8_t fl = active ? wf[1][0] : FL_SOLID;
         const bool fluid = active && !(fl & FL_SOLID);
         unsigned smask = 0;  // bit i: x + c_i is solid
-        R f[2][19];
-        R rho[2] = {R(1), R(1)}, ux[2] = {R(0), R(0)}, uy[2] = {R(0), R(0)}, uz[2] = {R(0), R(0)};
+        // component pairs (red, blue) throughout: one packed instruction
+        // per operation for both components
+        R2 f[19];
+        R2 rho = p2(R(1)), ux = p2(R(0)), uy = p2(R(0)), uz = p2(R(0));
         if (fluid) {
             // ------------------------------------------------- fluid node
             if constexpr (BB) {
 #pragma unroll
                 for (int i = 1; i < 19; i++)
-                    smask |= (unsigned)(FLG(slot_dz(cz(i)), ly + 1 + cy(i), lx + 1 + cx(i)) & FL_SOLID) << i;
+                    smask |= (unsigned)(wf[cz(i) + 1][cy(i) * W2 + cx(i)] & FL_SOLID) << i;
             }
 #pragma unroll
             for (int i = 1; i < 19; i++) {
                 // even steps: own slot i; odd steps: slot opp(i) of x - c_i
                 const S2* p = PAR == 0 ? pop.pair(i, n) : pop.pair(opp(i), n + off(opp(i)));
-                pop.ld2(p, i, f[0][i], f[1][i]);
+                pop.ld2(p, i, f[i].x, f[i].y);
             }
             // rho^c is the density field (the sum of the values the previous
             // step sent here); the rest population is rho^c minus the 18
             // moving ones and is needed only for tau != 1
-            R jx[2], jy[2], jz[2];
+            R2 rs = p2(R(0)), jx = p2(R(0)), jy = p2(R(0)), jz = p2(R(0));
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
-                R r = 0, ax = 0, ay = 0, az = 0;
+            for (int i = 1; i < 19; i++) {
+                if constexpr (!T1) rs = padd(rs, f[i]);
+                if (cx(i) > 0) jx = padd(jx, f[i]);
+                if (cx(i) < 0) jx = psub(jx, f[i]);
+                if (cy(i) > 0) jy = padd(jy, f[i]);
+                if (cy(i) < 0) jy = psub(jy, f[i]);
+                if (cz(i) > 0) jz = padd(jz, f[i]);
+                if (cz(i) < 0) jz = psub(jz, f[i]);
+            }
+            rho = mk2<R2>(rq0[0], rq0[1]);
+            f[0] = T1 ? p2(R(0)) : psub(rho, rs);
+            // Shan-Chen force F^c = -g Psi^c(x) sum_i W_i Psi^cbar(x + c_i) c_i:
+            // one pair load per neighbour, swapped so that each component
+            // meets the other one's Psi
+            R2 Fx, Fy, Fz;
+            {
+                R2 sx = p2(R(0)), sy = p2(R(0)), sz = p2(R(0));
 #pragma unroll
                 for (int i = 1; i < 19; i++) {
-                    if constexpr (!T1) r += f[c][i];
-                    if (cx(i) > 0) ax += f[c][i];
-                    if (cx(i) < 0) ax -= f[c][i];
-                    if (cy(i) > 0) ay += f[c][i];
-                    if (cy(i) < 0) ay -= f[c][i];
-                    if (cz(i) > 0) az += f[c][i];
-                    if (cz(i) < 0) az -= f[c][i];
+                    const R2 pp = wp[cz(i) + 1][cy(i) * W2 + cx(i)];
+                    const R2 q = mk2<R2>(pp.y, pp.x);
+                    const R w = is_axis(i) ? wax : wdg;
+                    if (cx(i)) sx = pfma(q, p2(cx(i) > 0 ? w : -w), sx);
+                    if (cy(i)) sy = pfma(q, p2(cy(i) > 0 ? w : -w), sy);
+                    if (cz(i)) sz = pfma(q, p2(cz(i) > 0 ? w : -w), sz);
                 }
-                rho[c] = rq0[c];
-                f[c][0] = T1 ? R(0) : rq0[c] - r;
-                jx[c] = ax;
-                jy[c] = ay;
-                jz[c] = az;
+                const R2 pc = pmul(p2(-g), wp[1][0]);
+                Fx = pfma(pc, sx, pmul(rho, p2(bfx)));
+                Fy = pfma(pc, sy, pmul(rho, p2(bfy)));
+                Fz = pfma(pc, sz, pmul(rho, p2(bfz)));
             }
-            // Shan-Chen force F^c = -g Psi^c(x) sum_i W_i Psi^cbar(x + c_i) c_i
-            R Fx[2], Fy[2], Fz[2];
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const int cb = 1 - c;
-                R sx = 0, sy = 0, sz = 0;
-#pragma unroll
-                for (int i = 1; i < 19; i++) {
-                    const R p = (is_axis(i) ? wax : wdg) * PSI(slot_dz(cz(i)), cb, ly + 1 + cy(i), lx + 1 + cx(i));
-                    if (cx(i) > 0) sx += p;
-                    if (cx(i) < 0) sx -= p;
-                    if (cy(i) > 0) sy += p;
-                    if (cy(i) < 0) sy -= p;
-                    if (cz(i) > 0) sz += p;
-                    if (cz(i) < 0) sz -= p;
-                }
-                const R pc = -g * PSI(sc_, c, ly + 1, lx + 1);
-                Fx[c] = pc * sx + rho[c] * bfx;
-                Fy[c] = pc * sy + rho[c] * bfy;
-                Fz[c] = pc * sz + rho[c] * bfz;
-            }
-            const R iden = R(1) / (rho[0] * itau0 + rho[1] * itau1);
-            const R upx = (jx[0] * itau0 + jx[1] * itau1) * iden;
-            const R upy = (jy[0] * itau0 + jy[1] * itau1) * iden;
-            const R upz = (jz[0] * itau0 + jz[1] * itau1) * iden;
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const R tc = c == 0 ? tau0 : tau1;
-                const R ir = R(1) / rho[c];
-                const R bx_ = velmode ? jx[c] * ir : upx;
-                const R by_ = velmode ? jy[c] * ir : upy;
-                const R bz_ = velmode ? jz[c] * ir : upz;
-                ux[c] = bx_ + tc * Fx[c] * ir;
-                uy[c] = by_ + tc * Fy[c] * ir;
-                uz[c] = bz_ + tc * Fz[c] * ir;
-            }
-            const R rt = rho[0] + rho[1];
-            const R vx = jx[0] + jx[1], vy = jy[0] + jy[1], vz = jz[0] + jz[1];
-            if (!(rho[0] > R(0)) || !(rho[1] > R(0)) || !(vx * vx + vy * vy + vz * vz < R(0.25) * rt * rt))
+            const R2 it2 = mk2<R2>(itau0, itau1);
+            const R2 rt = pmul(rho, it2);
+            const R iden = R(1) / (rt.x + rt.y);
+            const R2 qx = pmul(jx, it2), qy = pmul(jy, it2), qz = pmul(jz, it2);
+            const R2 ir = mk2<R2>(R(1) / rho.x, R(1) / rho.y);
+            const R2 bx_ = velmode ? pmul(jx, ir) : p2((qx.x + qx.y) * iden);
+            const R2 by_ = velmode ? pmul(jy, ir) : p2((qy.x + qy.y) * iden);
+            const R2 bz_ = velmode ? pmul(jz, ir) : p2((qz.x + qz.y) * iden);
+            const R2 tir = pmul(mk2<R2>(tau0, tau1), ir);
+            ux = pfma(Fx, tir, bx_);
+            uy = pfma(Fy, tir, by_);
+            uz = pfma(Fz, tir, bz_);
+            const R rtot = rho.x + rho.y;
+            const R vx = jx.x + jx.y, vy = jy.x + jy.y, vz = jz.x + jz.y;
+            if (!(rho.x > R(0)) || !(rho.y > R(0)) || !(vx * vx + vy * vy + vz * vz < R(0.25) * rtot * rtot))
                 set_err(sh.err, ERR_UNSTABLE);
         }
 
         const unsigned FULL = 0xffffffffu;
-        // per-group partial sums of the values this node sends, per component
-        // (mid: no x move; up / dn: to x + 1 / x - 1); after the x shuffle
-        // mid[c][g] holds everything that arrives in this column
-        R mid[2][9], up[2][5], dn[2][5];
+        // per-group partial sums of the pairs this node sends (mid: no x
+        // move; up / dn: to x + 1 / x - 1); after the x shuffle mid[g] holds
+        // everything that arrives in this column
+        R2 mid[9], up[5], dn[5];
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
+        for (int q = 0; q < 9; q++) mid[q] = p2(R(0));
 #pragma unroll
-            for (int q = 0; q < 9; q++) mid[c][q] = R(0);
-#pragma unroll
-            for (int q = 0; q < 5; q++) up[c][q] = dn[c][q] = R(0);
-        }
+        for (int q = 0; q < 5; q++) up[q] = dn[q] = p2(R(0));
         if (fluid) {
-            R itc[2], omt[2], uu[2], a0[2], rw1[2], rw7[2], resid[2], fe_sum[2], self[2];
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                itc[c] = T1 ? R(1) : (c == 0 ? itau0 : itau1);
-                omt[c] = T1 ? R(0) : R(1) - itc[c];
-                uu[c] = ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c];
-                a0[c] = R(1) - R(1.5) * uu[c];
-                rw1[c] = rho[c] * wgt<R>(1);
-                rw7[c] = rho[c] * wgt<R>(7);
-                resid[c] = fe_sum[c] = self[c] = R(0);
-            }
-            // store the pair f*_j (red, blue) where the next step reads it.
-            // Stream target y = x + c_j fluid: even steps slot opp(j) of x,
-            // odd steps slot j of y.  Target solid (bounce-back, f_opp(j) of
-            // x at t+1): even steps slot j of y, which the odd step at x
-            // reads for direction opp(j); odd steps slot opp(j) of x.
-            auto send = [&](auto JC, R fs0, R fs1) {
+            const R2 itc = T1 ? p2(R(1)) : mk2<R2>(itau0, itau1);
+            const R2 omt = T1 ? p2(R(0)) : psub(p2(R(1)), itc);
+            const R2 uu = pfma(ux, ux, pfma(uy, uy, pmul(uz, uz)));
+            const R2 a0 = pfma(p2(R(-1.5)), uu, p2(R(1)));
+            const R2 rw1 = pmul(rho, p2(wgt<R>(1))), rw7 = pmul(rho, p2(wgt<R>(7)));
+            R2 resid = p2(R(0)), fe_sum = p2(R(0)), self = p2(R(0));
+            // store the pair f*_j where the next step reads it.  Stream target
+            // y = x + c_j fluid: even steps slot opp(j) of x, odd steps slot j
+            // of y.  Target solid (bounce-back, f_opp(j) of x at t+1): even
+            // steps slot j of y, which the odd step at x reads for direction
+            // opp(j); odd steps slot opp(j) of x.
+            auto send = [&](auto JC, R2 fs) {
                 constexpr int j = decltype(JC)::value;
                 const bool solid = BB && ((smask >> j) & 1u);
                 S2* p;
                 if (PAR == 0) p = solid ? pop.pair(j, n + off(j)) : pop.pair(opp(j), n);
                 else p = solid ? pop.pair(opp(j), n) : pop.pair(j, n + off(j));
-                R q[2];
-                pop.st2(p, j, fs0, fs1, q[0], q[1]);
+                R2 q;
+                pop.st2(p, j, fs.x, fs.y, q.x, q.y);
+                if constexpr (P::dev) resid = padd(resid, psub(fs, q));
+                const R2 qf = solid ? p2(R(0)) : q;
+                if constexpr (BB) self = padd(self, solid ? q : p2(R(0)));
                 constexpr int gq = grp_of(j);
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    if constexpr (P::dev) resid[c] += (c == 0 ? fs0 : fs1) - q[c];
-                    const R qf = solid ? R(0) : q[c];
-                    self[c] += solid ? q[c] : R(0);
-                    if (cx(j) == 0) mid[c][gq] += qf;
-                    else if (cx(j) > 0) up[c][gq] += qf;
-                    else dn[c][gq] += qf;
-                }
+                if (cx(j) == 0) mid[gq] = padd(mid[gq], qf);
+                else if (cx(j) > 0) up[gq] = padd(up[gq], qf);
+                else dn[gq] = padd(dn[gq], qf);
             };
             // equilibria of opposite pairs share their even part:
             // f^eq_(+/-) = zeta rho (E +/- O), E = 1 - 3/2 u^2 + 9/2 cu^2,
-            // O = cu (3 + 9/2 cu^2 - 9/2 u^2)
-            auto pair = [&](auto JC, R cu0, R cu1) {
+            // O = cu (3 + 9/2 (cu^2 - u^2))
+            auto pair = [&](auto JC, R2 cu) {
                 constexpr int j = decltype(JC)::value;
-                R fp[2], fm[2];
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const R cu = c == 0 ? cu0 : cu1;
-                    const R rw = is_axis(j) ? rw1[c] : rw7[c];
-                    const R cu2 = cu * cu;
-                    const R E = a0[c] + R(4.5) * cu2;
-                    const R O = cu * (R(3) + R(4.5) * cu2 - R(4.5) * uu[c]);
-                    const R fep = rw * (E + O), fem = rw * (E - O);
-                    fe_sum[c] += fep + fem;
-                    if constexpr (T1) {
-                        fp[c] = fep;
-                        fm[c] = fem;
-                    } else {
-                        fp[c] = omt[c] * f[c][j] + itc[c] * fep;
-                        fm[c] = omt[c] * f[c][opp(j)] + itc[c] * fem;
-                    }
+                const R2 rw = is_axis(j) ? rw1 : rw7;
+                const R2 cu2 = pmul(cu, cu);
+                const R2 E = pfma(p2(R(4.5)), cu2, a0);
+                const R2 O = pmul(cu, pfma(p2(R(4.5)), psub(cu2, uu), p2(R(3))));
+                const R2 fep = pmul(rw, padd(E, O)), fem = pmul(rw, psub(E, O));
+                fe_sum = padd(fe_sum, padd(fep, fem));
+                if constexpr (T1) {
+                    send(std::integral_constant<int, j>{}, fep);
+                    send(std::integral_constant<int, opp(j)>{}, fem);
+                } else {
+                    send(std::integral_constant<int, j>{}, pfma(omt, f[j], pmul(itc, fep)));
+                    send(std::integral_constant<int, opp(j)>{}, pfma(omt, f[opp(j)], pmul(itc, fem)));
                 }
-                send(std::integral_constant<int, j>{}, fp[0], fp[1]);
-                send(std::integral_constant<int, opp(j)>{}, fm[0], fm[1]);
             };
-            pair(std::integral_constant<int, 1>{}, ux[0], ux[1]);
-            pair(std::integral_constant<int, 3>{}, uy[0], uy[1]);
-            pair(std::integral_constant<int, 5>{}, uz[0], uz[1]);
-            pair(std::integral_constant<int, 7>{}, ux[0] + uy[0], ux[1] + uy[1]);
-            pair(std::integral_constant<int, 9>{}, ux[0] - uy[0], ux[1] - uy[1]);
-            pair(std::integral_constant<int, 11>{}, ux[0] + uz[0], ux[1] + uz[1]);
-            pair(std::integral_constant<int, 13>{}, ux[0] - uz[0], ux[1] - uz[1]);
-            pair(std::integral_constant<int, 15>{}, uy[0] + uz[0], uy[1] + uz[1]);
-            pair(std::integral_constant<int, 17>{}, uy[0] - uz[0], uy[1] - uz[1]);
+            pair(std::integral_constant<int, 1>{}, ux);
+            pair(std::integral_constant<int, 3>{}, uy);
+            pair(std::integral_constant<int, 5>{}, uz);
+            pair(std::integral_constant<int, 7>{}, padd(ux, uy));
+            pair(std::integral_constant<int, 9>{}, psub(ux, uy));
+            pair(std::integral_constant<int, 11>{}, padd(ux, uz));
+            pair(std::integral_constant<int, 13>{}, psub(ux, uz));
+            pair(std::integral_constant<int, 15>{}, padd(uy, uz));
+            pair(std::integral_constant<int, 17>{}, psub(uy, uz));
             // rest population: its equilibrium is rho minus the other 18
             // (equal to Eq. Equil in exact arithmetic), and in deviation
             // storage it absorbs the rounding of the 18 stored values, so
             // node mass is kept to FP32 rounding.  It stays at the node and
             // enters only the density field: it is not stored.
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const R q0 = (T1 ? R(0) : omt[c] * f[c][0]) + itc[c] * (rho[c] - fe_sum[c]) + resid[c];
-                mid[c][0] += q0 + self[c];
-            }
+            const R2 q0 = padd(pfma(itc, psub(rho, fe_sum), T1 ? p2(R(0)) : pmul(omt, f[0])), resid);
+            mid[0] = padd(mid[0], padd(q0, self));
             // the 18 stored values and q0 sum to rho^c: the collision
             // conserves mass
-            msum0 += rho[0];
-            msum1 += rho[1];
+            msum = padd(msum, rho);
         }
 
+        // x shift (all lanes take part)
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
-            // x shift (all lanes take part)
+        for (int q = 0; q < 5; q++) {
+            R2 fromL, fromR;
+            fromL.x = __shfl_up_sync(FULL, up[q].x, 1);
+            fromL.y = __shfl_up_sync(FULL, up[q].y, 1);
+            fromR.x = __shfl_down_sync(FULL, dn[q].x, 1);
+            fromR.y = __shfl_down_sync(FULL, dn[q].y, 1);
+            if (lx == 0) fromL = p2(R(0));
+            if (lx == 31) fromR = p2(R(0));
+            mid[q] = padd(mid[q], padd(fromL, fromR));
+        }
+        // values leaving the tile through x: the first lane sends left, the
+        // last active lane sends right (both components at one address)
+        if (active && (lx == 0 || lx == w - 1)) {
+            // group q arrives at n + (x offset) + yz(q)
+            const int mx = n + (lx == 0 ? oxm : oxp);
 #pragma unroll
             for (int q = 0; q < 5; q++) {
-                R fromL = __shfl_up_sync(FULL, up[c][q], 1);
-                R fromR = __shfl_down_sync(FULL, dn[c][q], 1);
-                if (lx == 0) fromL = R(0);
-                if (lx == 31) fromR = R(0);
-                mid[c][q] += fromL + fromR;
+                const R2 v = lx == 0 ? dn[q] : up[q];
+                if (v.x != R(0) || v.y != R(0)) red_add2<R>(rnext2 + (mx + yz(q)), v.x, v.y);
             }
-            // values leaving the tile through x: the first lane sends left,
-            // the last active lane sends right
-            if (active && (lx == 0 || lx == w - 1)) {
-                // group q arrives at n + (x offset) + yz(q)
-                const int mx = n + (lx == 0 ? oxm : oxp);
+            if (w == 1) {  // a one-node-wide tile also sends right
 #pragma unroll
-                for (int q = 0; q < 5; q++) {
-                    const R v = lx == 0 ? dn[c][q] : up[c][q];
-                    if (v != R(0)) red_add(rnext + 2 * (size_t)(mx + yz(q)) + c, v);
-                }
-                if (w == 1) {  // a one-node-wide tile also sends right
-#pragma unroll
-                    for (int q = 0; q < 5; q++)
-                        if (up[c][q] != R(0)) red_add(rnext + 2 * (size_t)(n + oxp + yz(q)) + c, up[c][q]);
-                }
+                for (int q = 0; q < 5; q++)
+                    if (up[q].x != R(0) || up[q].y != R(0))
+                        red_add2<R>(rnext2 + (n + oxp + yz(q)), up[q].x, up[q].y);
             }
-            // y shift: rows exchange through shared memory; values leaving
-            // the tile through y are reduced into the ring rows directly
-            acc[1][c] += mid[c][0];
-            acc[2][c] += mid[c][3];
-            acc[0][c] += mid[c][4];
+        }
+        // y shift: rows exchange through shared memory; values leaving the
+        // tile through y are reduced into the ring rows directly
+        acc[1] = padd(acc[1], mid[0]);
+        acc[2] = padd(acc[2], mid[3]);
+        acc[0] = padd(acc[0], mid[4]);
+#pragma unroll
+        for (int q = 1; q < 9; q++) {
+            if (yb_of(q) < 0) continue;
+            YB2(yb_of(q), ly, lx) = mid[q];
+        }
+        if (active && (ly == 0 || ly == h - 1)) {
 #pragma unroll
             for (int q = 1; q < 9; q++) {
                 if (yb_of(q) < 0) continue;
-                YB(yb_of(q), c, ly, lx) = mid[c][q];
-            }
-            if (active && (ly == 0 || ly == h - 1)) {
-#pragma unroll
-                for (int q = 1; q < 9; q++) {
-                    if (yb_of(q) < 0) continue;
-                    const int dy = grp_dy(q);
-                    if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
-                    if (mid[c][q] != R(0)) red_add(rnext + 2 * (size_t)(n + yz(q)) + c, mid[c][q]);
-                }
+                const int dy = grp_dy(q);
+                if (!((ly == 0 && dy < 0) || (ly == h - 1 && dy > 0))) continue;
+                if (mid[q].x != R(0) || mid[q].y != R(0)) red_add2<R>(rnext2 + (n + yz(q)), mid[q].x, mid[q].y);
             }
         }
         __syncthreads();
 
         if (active) {
 #pragma unroll
-            for (int c = 0; c < 2; c++)
-#pragma unroll
-                for (int q = 1; q < 9; q++) {
-                    if (yb_of(q) < 0) continue;
-                    const int dy = grp_dy(q), dz = grp_dz(q);
-                    const int src = ly - dy;
-                    if (src < 0 || src >= h) continue;
-                    acc[1 + dz][c] += YB(yb_of(q), c, src, lx);
-                }
+            for (int q = 1; q < 9; q++) {
+                if (yb_of(q) < 0) continue;
+                const int dy = grp_dy(q), dz = grp_dz(q);
+                const int src = ly - dy;
+                if (src < 0 || src >= h) continue;
+                acc[1 + dz] = padd(acc[1 + dz], YB2(yb_of(q), src, lx));
+            }
             // plane z - 1 is complete: interior nodes are stored, edge and
             // ring nodes reduced
             const int pz = z - 1;
@@ -543,21 +517,13 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
             const bool interior = own_plane && pz <= z0 + d - 2 && pz >= z0 + 1 && lx >= 1 && lx <= w - 2 && ly >= 1 &&
                                   ly <= h - 2;
             const int m = n + ozm;
-            if (interior) {
-                rnext2[m] = mk2<R2>(acc[0][0], acc[0][1]);
-            } else {
-#pragma unroll
-                for (int c = 0; c < 2; c++)
-                    if (acc[0][c] != R(0)) red_add(rnext + 2 * (size_t)m + c, acc[0][c]);
-            }
-            if (own_plane && !interior) rzero[m] = mk2<R2>(R(0), R(0));
+            if (interior) rnext2[m] = acc[0];
+            else if (acc[0].x != R(0) || acc[0].y != R(0)) red_add2<R>(rnext2 + m, acc[0].x, acc[0].y);
+            if (own_plane && !interior) rzero[m] = p2(R(0));
         }
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            acc[0][c] = acc[1][c];
-            acc[1][c] = acc[2][c];
-            acc[2][c] = R(0);
-        }
+        acc[0] = acc[1];
+        acc[1] = acc[2];
+        acc[2] = p2(R(0));
         // plane z + 2 replaces plane z - 1 in the window
         {
             const int t = sm_;
@@ -581,9 +547,7 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
             const int pz = z0 + d - 1 + k;
             const int gz = pz >= nz ? pz - nz : pz;
             const int m = nxyc + nxy * gz;
-#pragma unroll
-            for (int c = 0; c < 2; c++)
-                if (acc[k][c] != R(0)) red_add(rnext + 2 * (size_t)m + c, acc[k][c]);
+            if (acc[k].x != R(0) || acc[k].y != R(0)) red_add2<R>(rnext2 + m, acc[k].x, acc[k].y);
             if (k == 0) rzero[m] = mk2<R2>(R(0), R(0));
         }
     }
@@ -593,12 +557,12 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
         const unsigned FULL = 0xffffffffu;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            msum0 += __shfl_xor_sync(FULL, msum0, off);
-            msum1 += __shfl_xor_sync(FULL, msum1, off);
+            msum.x += __shfl_xor_sync(FULL, msum.x, off);
+            msum.y += __shfl_xor_sync(FULL, msum.y, off);
         }
         if (lx == 0) {
-            s_red[0][ly] = (double)msum0;
-            s_red[1][ly] = (double)msum1;
+            s_red[0][ly] = (double)msum.x;
+            s_red[1][ly] = (double)msum.y;
         }
         __syncthreads();
         if (tid == 0) {
