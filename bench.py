@@ -304,6 +304,7 @@ def run_ours(args, rank, world, device):
     sim.set_profiling(True)
     sim.step(prof_steps)
     fused_ms, fused_n, total_launches = sim.kernel_time()
+    phases = {k: v / prof_steps for k, v in sim.phase_times().items()}
     sim.set_profiling(False)
     sim.sync()
     launches = int(round(total_launches / max(prof_steps, 1) * args.steps))
@@ -346,7 +347,7 @@ def run_ours(args, rank, world, device):
         seq = {"sequential_mlups": seq_value, "batched_mlups": value, "ratio": value / seq_value,
                "sequential_ms": seq_ms, "what": "the same boxes and states, one handle per box, run one after another"}
     return dict(value=value, ms=ms_max, fused_ms=avg_ms, fused_n=fused_n, bytes=bytes_launch, achieved=achieved,
-                peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=launches, nodes=nodes,
+                peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=launches, nodes=nodes, phases=phases,
                 n_particles=sum(sim.n_particles), error=ob["error"], n_fluid=n_fluid, tiling=tiling, seq=seq)
 
 
@@ -466,6 +467,7 @@ def leg_fields(args, r):
                      "step_frac": r["value"] / roof_mlups, "step_roofline_mlups": roof_mlups,
                      "ideal_bytes_per_node": ideal},
         "fluid_mlups": r["value"] * r["n_fluid"] / r["nodes"],
+        "phases_ms_per_step": r["phases"],
         "e2e": r["e2e"],
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],

@@ -241,6 +241,17 @@ int lb_set_tiling(lb_handle* h, int32_t ty, int32_t cz, int32_t split);
 int lb_set_profiling(lb_handle* h, int32_t on);
 int lb_kernel_time(lb_handle* h, double* ms_fused, int64_t* launches_fused, int64_t* launches_total);
 
+/* Phase times of the steps measured by the last lb_kernel_time (profiling
+ * mode: CUDA events at every phase boundary, kernels launched one by one):
+ * ms[k] for the first n of the LB_NPHASES phases of a step, in order
+ *   0 cell and neighbour lists, 1 remap detection, 2 cover / uncover
+ *   (marks, refills, shell flags), 3 shell virtual densities, 4 fused
+ *   stream-collide kernel, 5 coupling pass (links, momentum exchange,
+ *   Shan-Chen force on the particles), 6 MD.
+ * Each phase also carries its share of launch gaps. */
+#define LB_NPHASES 7
+int lb_phase_times(lb_handle* h, double* ms, int32_t n);
+
 /* Destroy the handle (does not free the caller's workspace). */
 void lb_destroy(lb_handle* h);
 

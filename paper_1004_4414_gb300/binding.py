@@ -81,7 +81,7 @@ ABI_FUNCTIONS = (
     "lb_observables", "lb_export_state", "lb_import_state", "lb_export_rho", "lb_export_phi",
     "lb_set_particle_colors",
     "lb_set_axes", "lb_get_axes",
-    "lb_particle_forces", "lb_box_info", "lb_set_tiling", "lb_set_profiling", "lb_kernel_time",
+    "lb_particle_forces", "lb_box_info", "lb_set_tiling", "lb_set_profiling", "lb_kernel_time", "lb_phase_times",
     "lb_destroy", "lb_strerror", "lb_field_moments",
 )
 
@@ -123,6 +123,7 @@ def load_library(path=LIB_PATH):
     L.lb_set_tiling.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
     L.lb_set_profiling.argtypes = [vp, C.c_int32]
     L.lb_kernel_time.argtypes = [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.lb_phase_times.argtypes = [vp, dp, C.c_int32]
     L.lb_destroy.argtypes = [vp]
     L.lb_destroy.restype = None
     L.lb_strerror.argtypes = [C.c_int]
@@ -357,6 +358,14 @@ class Simulation:
 
     def set_profiling(self, on):
         _ck(load_library().lb_set_profiling(self._h, 1 if on else 0), "lb_set_profiling")
+
+    PHASES = ("lists", "remap_detect", "cover_uncover", "shell", "fused", "couple", "md")
+
+    def phase_times(self):
+        """Milliseconds per phase of the steps the last kernel_time() covered."""
+        ms = np.zeros(len(self.PHASES))
+        _ck(load_library().lb_phase_times(self._h, _dp(ms), len(ms)), "lb_phase_times")
+        return dict(zip(self.PHASES, ms))
 
     def kernel_time(self):
         ms = C.c_double(0)

@@ -175,6 +175,10 @@ struct lb_handle {
     std::vector<cudaEvent_t> evpool;
     int ev_used = 0;
     double prof_ms = 0.0;
+    // profiling mode: an event at every phase boundary of a step, (phase,
+    // event index) of each phase start; summed per phase by lb_kernel_time
+    std::vector<std::pair<int, int>> phase_marks;
+    double phase_ms[LB_NPHASES] = {};
     int64_t prof_fused = 0, prof_total = 0, launches_since = 0;
 
     int* h_err = nullptr;  // pinned mirror of the device error word
@@ -396,8 +400,31 @@ int build_tiles(lb_handle* h) {
 }
 
 // all kernels of one time step t
+// profiling: an event on the stream (from the handle's pool)
+int prof_event(lb_handle* h, int* idx) {
+    if (h->ev_used + 1 > (int)h->evpool.size()) {
+        for (int k = 0; k < 64; k++) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            h->evpool.push_back(e);
+        }
+    }
+    *idx = h->ev_used++;
+    CK(cudaEventRecord(h->evpool[*idx], h->stream));
+    return LB_OK;
+}
+
 int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     cudaStream_t st = h->stream;
+    // phase boundaries (profiling only): phase k runs between marks k and k + 1
+    int evi = 0;
+    auto mark = [&](int phase) -> int {
+        if (!prof) return LB_OK;
+        int rc = prof_event(h, &evi);
+        if (rc == LB_OK) h->phase_marks.push_back({phase, evi});
+        return rc;
+    };
+    if (mark(0) != LB_OK) return LB_ECUDA;
     const int par = (int)(t & 1), rc = (int)(t % 3), rn = (int)((t + 1) % 3), rz = (int)((t + 2) % 3);
     const int mcur = (int)(t & 1), mnext = (int)((t + 1) & 1);
     const int NP = h->NP;
@@ -413,11 +440,14 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         k_cell_scan<<<h->nb, 1024, 0, st>>>(h->d_boxes, h->sh);
         k_cell_fill<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
         k_nlist<<<(NP + NLIST_WARPS - 1) / NLIST_WARPS, 32 * NLIST_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
+        if (mark(1) != LB_OK) return LB_ECUDA;
         k_remap_detect<<<NP, 32 * DETECT_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
+        if (mark(2) != LB_OK) return LB_ECUDA;
         k_remap_mark<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->sh);
         CK(cudaGetLastError());
         CK(h->ops->remap_apply(par, st, h->d_boxes, h->sh, rc, mcur));
         CK(h->ops->remap_finish(st, h->d_boxes, h->sh, rc));
+        if (mark(3) != LB_OK) return LB_ECUDA;
         CK(h->ops->shell_density(st, h->d_boxes, h->sh, rc, NP));
         launches += 9;
     }
@@ -426,30 +456,17 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
             CK(h->ops->wall_shell(st, h->d_boxes, b, rc));
             launches++;
         }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (prof) {
-        if (h->ev_used + 2 > (int)h->evpool.size()) {
-            for (int k = 0; k < 64; k++) {
-                cudaEvent_t e;
-                CK(cudaEventCreate(&e));
-                h->evpool.push_back(e);
-            }
-        }
-        e0 = h->evpool[h->ev_used++];
-        e1 = h->evpool[h->ev_used++];
-        CK(cudaEventRecord(e0, st));
-    }
+    if (mark(4) != LB_OK) return LB_ECUDA;
     CK(h->ops->step(par, h->ty, h->split, h->tau1, h->reflect, h->ntiles, st, h->d_boxes, h->d_tiles, h->sh, rc, rn, rz, mnext));
     launches++;
-    if (prof) {
-        CK(cudaEventRecord(e1, st));
-        h->prof_fused++;
-    }
+    if (prof) h->prof_fused++;
+    if (mark(5) != LB_OK) return LB_ECUDA;
     if (NP > 0) {
         const int pg = (NP + 255) / 256;
         int impl = 0;
         for (const auto& p : h->params) impl |= p.implicit_update;
         CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, impl, NP));
+        if (mark(6) != LB_OK) return LB_ECUDA;
         k_md_forces<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         if (impl) {
             // implicit update: velocities, the fluid's share on the links, positions
@@ -462,6 +479,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
             launches += 3;
         }
     }
+    if (mark(LB_NPHASES) != LB_OK) return LB_ECUDA;  // end of the step
     h->launches_since = launches;
     if (prof) h->prof_total += launches;
     CK(cudaGetLastError());
@@ -1234,6 +1252,7 @@ int lb_set_profiling(lb_handle* h, int32_t on) {
     CK(cudaStreamSynchronize(h->stream));
     h->prof = on != 0;
     h->ev_used = 0;
+    h->phase_marks.clear();
     h->prof_ms = 0.0;
     h->prof_fused = 0;
     h->prof_total = 0;
@@ -1243,18 +1262,28 @@ int lb_set_profiling(lb_handle* h, int32_t on) {
 int lb_kernel_time(lb_handle* h, double* ms_fused, int64_t* launches_fused, int64_t* launches_total) {
     if (!h) return LB_EINVAL;
     CK(cudaStreamSynchronize(h->stream));
-    double ms = 0.0;
-    for (int k = 0; k + 1 < h->ev_used; k += 2) {
+    // phase k of a step lasts from its mark to the next mark of the step
+    for (int k = 0; k < LB_NPHASES; k++) h->phase_ms[k] = 0.0;
+    for (size_t k = 0; k + 1 < h->phase_marks.size(); k++) {
+        const int ph = h->phase_marks[k].first;
+        if (ph >= LB_NPHASES) continue;  // end-of-step mark
         float v = 0.f;
-        CK(cudaEventElapsedTime(&v, h->evpool[k], h->evpool[k + 1]));
-        ms += v;
+        CK(cudaEventElapsedTime(&v, h->evpool[h->phase_marks[k].second], h->evpool[h->phase_marks[k + 1].second]));
+        h->phase_ms[ph] += v;
     }
-    if (ms_fused) *ms_fused = ms;
+    h->phase_marks.clear();
+    if (ms_fused) *ms_fused = h->phase_ms[4];
     if (launches_fused) *launches_fused = h->prof_fused;
     if (launches_total) *launches_total = h->prof_total;
     h->ev_used = 0;
     h->prof_fused = 0;
     h->prof_total = 0;
+    return LB_OK;
+}
+
+int lb_phase_times(lb_handle* h, double* ms, int32_t n) {
+    if (!h || !ms || n < 0) return LB_EINVAL;
+    for (int k = 0; k < n && k < LB_NPHASES; k++) ms[k] = h->phase_ms[k];
     return LB_OK;
 }
 

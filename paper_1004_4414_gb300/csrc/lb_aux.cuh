@@ -379,10 +379,11 @@ static __global__ void k_coverage_marks(const BoxDev* __restrict__ boxes, int b,
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B.N; n += gridDim.x * blockDim.x) {
         const int o = B.owner[n];
         if (o < B.pstart || o >= B.pstart + B.np) continue;
-        int bits = 0;
+        int bits = 0, x, y, z;
+        node_xyz(B, n, x, y, z);
 #pragma unroll
         for (int i = 1; i < 19; i++) {
-            const int m = nbr_index(B, n, cx(i), cy(i), cz(i));
+            const int m = node_off(B, x, y, z, cx(i), cy(i), cz(i));
             if (B.flags[m] & FL_SOLID) continue;
             const R2 r = r2[m];
             const double v = (double)r.x - (double)r.y;

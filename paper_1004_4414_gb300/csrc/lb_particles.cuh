@@ -170,7 +170,7 @@ static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev*
 // plain sequential evaluation, decides.  FP64 is slow on this GPU, so it is
 // kept off the common path.
 constexpr int DETECT_WARPS = 4, DETECT_QUEUE = 256;
-static __global__ void __launch_bounds__(32 * DETECT_WARPS, 8) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     __shared__ int s_queue[DETECT_WARPS][DETECT_QUEUE];  // annulus candidates of the fast path
     // the close list, built by each warp for itself
     __shared__ float s_rq[DETECT_WARPS][NL_MAX][3];  // X_q - X_p, minimum image
@@ -243,14 +243,34 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 8) k_remap_detect(co
         ez_ = (float)Ep[2];
     }
     const float R2s = B.det_sR2, c2s = B.det_sc2, R2c2 = B.det_sR2c2, sband = B.det_sband;
-    // one candidate node (kx, ky, kz) of the window: an event if its status
-    // or owner changes (have), with its node index, old and new owner
-    auto handle = [&](int kx, int ky, int kz, bool& have, int& node, int& ev_old, int& ev_new) {
-        const float fx = mimgf((float)kx - off[0], Lf[0]), fy = mimgf((float)ky - off[1], Lf[1]),
-                    fz = mimgf((float)kz - off[2], Lf[2]);
-        const float d2f = fx * fx + fy * fy + fz * fz;
-        if (!(d2f <= Rf2o)) return;
-        const int gx = wrapi(lo[0] + kx, B.nx), gy = wrapi(lo[1] + ky, B.ny), gz = wrapi(lo[2] + kz, B.nz);
+    // one candidate node (kx, ky, kz) of the window: probe computes its
+    // offsets from the centre and loads its owner (the only global load),
+    // decide finds whether its status or owner changes (have), with its node
+    // index, old and new owner; full scans probe several candidates before
+    // deciding any, so that their loads are in flight together
+    struct Cand {
+        float fx, fy, fz, d2f;
+        int n, own, gx, gy, gz;
+        bool ok;
+    };
+    auto probe = [&](int kx, int ky, int kz) -> Cand {
+        Cand c;
+        c.fx = mimgf((float)kx - off[0], Lf[0]);
+        c.fy = mimgf((float)ky - off[1], Lf[1]);
+        c.fz = mimgf((float)kz - off[2], Lf[2]);
+        c.d2f = c.fx * c.fx + c.fy * c.fy + c.fz * c.fz;
+        c.ok = c.d2f <= Rf2o;
+        c.gx = wrapi(lo[0] + kx, B.nx);
+        c.gy = wrapi(lo[1] + ky, B.ny);
+        c.gz = wrapi(lo[2] + kz, B.nz);
+        c.n = c.gx + B.nx * (c.gy + B.ny * c.gz);
+        c.own = c.ok ? __ldg(B.owner + c.n) : OWN_WALL;
+        return c;
+    };
+    auto decide = [&](const Cand& c, bool& have, int& node, int& ev_old, int& ev_new) {
+        if (!c.ok || c.own == OWN_WALL) return;
+        const float fx = c.fx, fy = c.fy, fz = c.fz, d2f = c.d2f;
+        const int gx = c.gx, gy = c.gy, gz = c.gz, own = c.own;
         // FP64 inside test of this node for particle q; d2 = squared
         // centre distance (the claim goes to the nearest centre)
         auto exact_in = [&](int q, double& d2) {
@@ -260,9 +280,6 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 8) k_remap_detect(co
             d2 = dist2_nc(dx, dy, dz);
             return inside_shape(B, dx, dy, dz, sh.part[q].E);
         };
-        const int n = gx + B.nx * (gy + B.ny * gz);
-        const int own = __ldg(B.owner + n);
-        if (own == OWN_WALL) return;
         double d2p = -1.0;
         bool inside;
         if (sph) {
@@ -303,7 +320,10 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 8) k_remap_detect(co
             ev_old = p;
             ev_new = OWN_FLUID;
         }
-        node = n;
+        node = c.n;
+    };
+    auto handle = [&](int kx, int ky, int kz, bool& have, int& node, int& ev_old, int& ev_new) {
+        decide(probe(kx, ky, kz), have, node, ev_old, ev_new);
     };
     // the events of 32 candidates, appended to the event list
     auto emit = [&](bool have, int node, int ev_old, int ev_new) {
@@ -343,15 +363,27 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 8) k_remap_detect(co
     for (int a = 0; a < 3; a++) fits = fits && 2 * span[a] < dims[a] && span[a] < 1024;
     const bool fast = sph && fits && ncl == 0 && sh.exact[p] && delta < 0.5f;
     if (!fast) {
-        for (int base = wib * 32; base < total; base += 32 * DETECT_WARPS) {
-            const int idx = base + lane;
-            int ev_old = 0, ev_new = 0, node = 0;
-            bool have = false;
-            if (idx < total) {
-                const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-                handle(kx, ky, kz, have, node, ev_old, ev_new);
+        // two candidates per lane per round, probed before either is decided
+        constexpr int SU = 2;
+        for (int base = wib * 32 * SU; base < total; base += 32 * SU * DETECT_WARPS) {
+            Cand c[SU];
+#pragma unroll
+            for (int u = 0; u < SU; u++) {
+                const int idx = base + u * 32 + lane;
+                if (idx < total) {
+                    const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+                    c[u] = probe(kx, ky, kz);
+                } else {
+                    c[u].ok = false;
+                }
             }
-            emit(have, node, ev_old, ev_new);
+#pragma unroll
+            for (int u = 0; u < SU; u++) {
+                int ev_old = 0, ev_new = 0, node = 0;
+                bool have = false;
+                decide(c[u], have, node, ev_old, ev_new);
+                emit(have, node, ev_old, ev_new);
+            }
         }
     } else {
         // rows (ky, kz) of the window, one per lane; the annulus crosses a
@@ -454,49 +486,6 @@ __device__ __forceinline__ bool old_solid(const BoxDev& B, int n) {
     if (m) return (m - 3) != OWN_FLUID;
     return B.flags[n] & FL_SOLID;
 }
-// refill of an uncovered node (Eqs. eqn_rho_neu and masscorr): mean density
-// of the neighbours that were fluid, times the mass-correction factor; the
-// surface velocity of the particle that left it.
-template <class R>
-struct Refill {
-    R rho[2];
-    R us[3];
-    double r[3];
-};
-template <class R>
-__device__ Refill<R> refill_of(const BoxDev& B, const Shared& sh, int n, int q, const R* rcur, int mslot_cur) {
-    Refill<R> o;
-    double corr[2] = {1.0, 1.0};
-    if (B.c0 != 0.0) {
-        const double rsum = B.rho_init[0] + B.rho_init[1];
-        for (int c = 0; c < 2; c++)
-            corr[c] = 1.0 - B.c0 * (rsum / B.rho_init[c]) * (B.mass_acc[mslot_cur * 2 + c] - B.mass0[c]) / (double)B.N;
-    }
-    for (int c = 0; c < 2; c++) {
-        R sum = R(0);
-        int cnt = 0;
-#pragma unroll
-        for (int i = 1; i < 19; i++) {
-            const int m = nbr_index(B, n, cx(i), cy(i), cz(i));
-            if (!old_solid(B, m)) {
-                sum += rcur[2 * (size_t)m + c];
-                cnt++;
-            }
-        }
-        const R rbar = cnt ? sum / (R)cnt : (R)B.rho_init[c];
-        o.rho[c] = (R)((double)rbar * corr[c]);
-    }
-    const int x = n % B.nx, y = (n / B.nx) % B.ny, z = n / (B.nx * B.ny);
-    const PartState ps = sh.part[q];
-    o.r[0] = mimg((double)x - ps.X[0], B.nx);
-    o.r[1] = mimg((double)y - ps.X[1], B.ny);
-    o.r[2] = mimg((double)z - ps.X[2], B.nz);
-    o.us[0] = (R)(ps.U[0] + ps.W[1] * o.r[2] - ps.W[2] * o.r[1]);
-    o.us[1] = (R)(ps.U[1] + ps.W[2] * o.r[0] - ps.W[0] * o.r[2]);
-    o.us[2] = (R)(ps.U[2] + ps.W[0] * o.r[1] - ps.W[1] * o.r[0]);
-    return o;
-}
-
 __device__ __forceinline__ void add_force_torque(const Shared& sh, int p, const double r[3], const double F[3]) {
     double t[3];
     cross3(r, F, t);
@@ -514,6 +503,29 @@ __device__ __forceinline__ void node_rel(const BoxDev& B, const Shared& sh, int 
     r[2] = mimg((double)z - ps.X[2], B.nz);
 }
 
+// D3Q19 vectors as bit fields (2 bits per direction, value + 1), for a
+// direction known only at run time (one per lane) without a memory lookup
+__host__ __device__ constexpr uint64_t dir_bits(int a) {
+    uint64_t v = 0;
+    for (int i = 0; i < 19; i++) v |= (uint64_t)((a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i))) + 1) << (2 * i);
+    return v;
+}
+__device__ __forceinline__ int dvec(int a, int i) {
+    constexpr uint64_t B0 = dir_bits(0), B1 = dir_bits(1), B2 = dir_bits(2);
+    const uint64_t b = a == 0 ? B0 : (a == 1 ? B1 : B2);
+    return (int)((b >> (2 * i)) & 3u) - 1;
+}
+__device__ __forceinline__ void node_xyz(const BoxDev& B, int n, int& x, int& y, int& z) {
+    x = n % B.nx;
+    const int r = n / B.nx;
+    y = r % B.ny;
+    z = r / B.ny;
+}
+// node at (x + dx, y + dy, z + dz), |d| <= 1 per axis, periodic
+__device__ __forceinline__ int node_off(const BoxDev& B, int x, int y, int z, int dx, int dy, int dz) {
+    return wrap1(x + dx, B.nx) + B.nx * (wrap1(y + dy, B.ny) + B.ny * wrap1(z + dz, B.nz));
+}
+
 // Cover / uncover.  PAR is the parity of the coming fused step.  Before an
 // even step f_i of a node sits in its own slot i; before an odd step it sits
 // in slot opp(i) of the neighbour x - c_i, whatever that neighbour's status
@@ -521,108 +533,178 @@ __device__ __forceinline__ void node_rel(const BoxDev& B, const Shared& sh, int 
 // node's slot).  So a status change moves nothing: a covered node gives the
 // momentum of its populations to the particle, an uncovered node gets
 // f^eq(rho_new, u_s) in the same places, and the particle loses the
-// momentum of the created fluid.
+// momentum of the created fluid.  One warp per event, lane i takes
+// direction i (1..18).
 template <class P, int PAR>
 static __global__ void k_remap_apply(const BoxDev* __restrict__ boxes, Shared sh, int rc, int mslot_cur) {
     using R = typename P::real;
+    using R2 = typename Real2<R>::type;
+    using S2 = typename P::st2;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int cnt = ev_total(sh);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const int i = lane;
+    const bool act = i >= 1 && i <= 18;
+    const int ix = act ? dvec(0, i) : 0, iy = act ? dvec(1, i) : 0, iz = act ? dvec(2, i) : 0;
+    const int io = act ? opp(i) : 0;
+    for (int e = warp; e < cnt; e += nwarps) {
         const int4 ev = sh.events[e];
         const int w = ev.x, old = ev.z, nw = ev.w;
-        if (old != OWN_FLUID && nw != OWN_FLUID) continue;  // transfer between particles
+        if (old != OWN_FLUID && nw != OWN_FLUID) continue;  // transfer between particles (warp-uniform)
         const BoxDev& B = boxes[ev.y];
         const Pop<P> pop(B);
-        const R* rcur = reinterpret_cast<const R*>(B.rho[rc]);
-        const bool covered = (old == OWN_FLUID);
-        // node holding f_i of w before the coming step
-        auto src = [&](int i) { return PAR == 0 ? w : nbr_index(B, w, -cx(i), -cy(i), -cz(i)); };
-        auto slot = [&](int i) { return PAR == 0 ? i : opp(i); };
-        if (covered) {
-            atomicAdd(&sh.counters[ev.y * 2 + 0], 1ull);
-            double mom_w[3] = {0, 0, 0};
-            for (int c = 0; c < 2; c++) {
+        int x, y, z;
+        node_xyz(B, w, x, y, z);
+        // the pair of f_i of w before the coming step
+        S2* const at = act ? (PAR == 0 ? pop.pair(i, w) : pop.pair(io, node_off(B, x, y, z, -ix, -iy, -iz))) : nullptr;
+        if (old == OWN_FLUID) {
+            // covered: the particle gains the momentum of the node's fluid
+            double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+            if (act) {
+                R a, b;
+                pop.ld2(at, i, a, b);
+                const double v = (double)a + (double)b;
+                m0 = v * ix;
+                m1 = v * iy;
+                m2 = v * iz;
+            }
 #pragma unroll
-                for (int i = 1; i < 19; i++) {
-                    const R v = pop.load(c, slot(i), src(i));
-                    mom_w[0] += (double)v * cx(i);
-                    mom_w[1] += (double)v * cy(i);
-                    mom_w[2] += (double)v * cz(i);
+            for (int o = 16; o > 0; o >>= 1) {
+                m0 += __shfl_xor_sync(FULL, m0, o);
+                m1 += __shfl_xor_sync(FULL, m1, o);
+                m2 += __shfl_xor_sync(FULL, m2, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&sh.counters[ev.y * 2 + 0], 1ull);
+                double r[3];
+                node_rel(B, sh, w, nw, r);
+                const double mom[3] = {m0, m1, m2};
+                add_force_torque(sh, nw, r, mom);
+            }
+        } else {
+            // uncovered (Eqs. eqn_rho_neu and masscorr): the mean density of
+            // the neighbours that were fluid, times the mass-correction
+            // factor; f = f^eq(rho_new, u_s) of the particle that left it
+            const R2* __restrict__ rcur2 = rpair<R>(B.rho[rc]);
+            R s0 = R(0), s1 = R(0);
+            int c = 0;
+            if (act) {
+                const int m = node_off(B, x, y, z, ix, iy, iz);
+                if (!old_solid(B, m)) {
+                    const R2 v = rcur2[m];
+                    s0 = v.x;
+                    s1 = v.y;
+                    c = 1;
                 }
             }
-            double r[3];
-            node_rel(B, sh, w, nw, r);
-            add_force_torque(sh, nw, r, mom_w);
-        } else {
-            const Refill<R> rf = refill_of<R>(B, sh, w, old, rcur, mslot_cur);
-            sh.ev_rho[(size_t)e * 2 + 0] = (double)rf.rho[0];
-            sh.ev_rho[(size_t)e * 2 + 1] = (double)rf.rho[1];
-            atomicAdd(&sh.counters[ev.y * 2 + 1], 1ull);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s0 += __shfl_xor_sync(FULL, s0, o);
+                s1 += __shfl_xor_sync(FULL, s1, o);
+                c += __shfl_xor_sync(FULL, c, o);
+            }
+            double corr[2] = {1.0, 1.0};
+            if (B.c0 != 0.0) {
+                const double rsum = B.rho_init[0] + B.rho_init[1];
+                for (int k = 0; k < 2; k++)
+                    corr[k] = 1.0 - B.c0 * (rsum / B.rho_init[k]) * (B.mass_acc[mslot_cur * 2 + k] - B.mass0[k]) /
+                                        (double)B.N;
+            }
+            const R rb0 = c ? s0 / (R)c : (R)B.rho_init[0], rb1 = c ? s1 / (R)c : (R)B.rho_init[1];
+            const R rn0 = (R)((double)rb0 * corr[0]), rn1 = (R)((double)rb1 * corr[1]);
+            const PartState ps = sh.part[old];
+            const double r[3] = {mimg((double)x - ps.X[0], B.nx), mimg((double)y - ps.X[1], B.ny),
+                                 mimg((double)z - ps.X[2], B.nz)};
+            const R us[3] = {(R)(ps.U[0] + ps.W[1] * r[2] - ps.W[2] * r[1]),
+                             (R)(ps.U[1] + ps.W[2] * r[0] - ps.W[0] * r[2]),
+                             (R)(ps.U[2] + ps.W[0] * r[1] - ps.W[1] * r[0])};
             // the 18 moving populations; the density rho_new (set by
             // k_remap_finish) makes the rest population rho_new minus them
-            for (int c = 0; c < 2; c++) {
-#pragma unroll
-                for (int i = 1; i < 19; i++)
-                    pop.store(c, slot(i), src(i), feq_rt<R>(i, rf.rho[c], rf.us[0], rf.us[1], rf.us[2]));
+            if (act) {
+                R q0, q1;
+                pop.st2(at, i, feq_rt<R>(i, rn0, us[0], us[1], us[2]), feq_rt<R>(i, rn1, us[0], us[1], us[2]), q0, q1);
             }
-            // the particle loses the momentum of the created fluid
-            // (Eq. eqn_ladd_vernichtenunderzeugen, sign from conservation)
-            const double rs = (double)rf.rho[0] + (double)rf.rho[1];
-            const double F[3] = {-rs * (double)rf.us[0], -rs * (double)rf.us[1], -rs * (double)rf.us[2]};
-            add_force_torque(sh, old, rf.r, F);
+            if (lane == 0) {
+                sh.ev_rho[(size_t)e * 2 + 0] = (double)rn0;
+                sh.ev_rho[(size_t)e * 2 + 1] = (double)rn1;
+                atomicAdd(&sh.counters[ev.y * 2 + 1], 1ull);
+                // the particle loses the momentum of the created fluid
+                // (Eq. eqn_ladd_vernichtenunderzeugen, sign from conservation)
+                const double rs = (double)rn0 + (double)rn1;
+                const double F[3] = {-rs * (double)us[0], -rs * (double)us[1], -rs * (double)us[2]};
+                add_force_torque(sh, old, r, F);
+            }
         }
     }
 }
 
-__device__ __forceinline__ void shell_update(const BoxDev& B, int n) {
+// shell flag of node (x, y, z): solid with a fluid D3Q19 neighbour
+__device__ __forceinline__ void shell_update_at(const BoxDev& B, int x, int y, int z) {
+    const int n = x + B.nx * (y + B.ny * z);
     const uint8_t f = B.flags[n];
     if (!(f & FL_SOLID)) return;
     bool shl = false;
 #pragma unroll
     for (int i = 1; i < 19; i++)
-        if (!(B.flags[nbr_index(B, n, cx(i), cy(i), cz(i))] & FL_SOLID)) shl = true;
+        if (!(B.flags[node_off(B, x, y, z, cx(i), cy(i), cz(i))] & FL_SOLID)) shl = true;
     B.flags[n] = FL_SOLID | (shl ? FL_SHELL : 0);
 }
+__device__ __forceinline__ void shell_update(const BoxDev& B, int n) {
+    int x, y, z;
+    node_xyz(B, n, x, y, z);
+    shell_update_at(B, x, y, z);
+}
 
+// After the events: densities of the event nodes, shell flags around them,
+// and the particles whose shell lists must be rebuilt.  One warp per event:
+// lane 0 takes the event node, lane i (1..18) its neighbour w + c_i.
 template <class R>
 static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared sh, int rc) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int cnt = ev_total(sh);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const int i = lane;
+    const int ix = i <= 18 ? dvec(0, i) : 0, iy = i <= 18 ? dvec(1, i) : 0, iz = i <= 18 ? dvec(2, i) : 0;
+    for (int e = warp; e < cnt; e += nwarps) {
         const int4 ev = sh.events[e];
         const BoxDev& B = boxes[ev.y];
         const int w = ev.x;
         R* rcur = reinterpret_cast<R*>(B.rho[rc]);
-        if (ev.z == OWN_FLUID) {
-            rcur[2 * (size_t)w] = R(0);
-            rcur[2 * (size_t)w + 1] = R(0);
-        } else if (ev.w == OWN_FLUID) {
-            rcur[2 * (size_t)w] = (R)sh.ev_rho[(size_t)e * 2 + 0];
-            rcur[2 * (size_t)w + 1] = (R)sh.ev_rho[(size_t)e * 2 + 1];
+        int x, y, z;
+        node_xyz(B, w, x, y, z);
+        if (lane == 0) {
+            if (ev.z == OWN_FLUID) {
+                rcur[2 * (size_t)w] = R(0);
+                rcur[2 * (size_t)w + 1] = R(0);
+            } else if (ev.w == OWN_FLUID) {
+                rcur[2 * (size_t)w] = (R)sh.ev_rho[(size_t)e * 2 + 0];
+                rcur[2 * (size_t)w + 1] = (R)sh.ev_rho[(size_t)e * 2 + 1];
+            }
+            B.evmark[w] = 0;
+            // the particles whose shell lists this event can change: the old
+            // and new owner of w and the owners of its solid neighbours
+            // (their fluid-neighbour masks)
+            if (ev.z >= 0) sh.shell_dirty[ev.z] = 1;
+            if (ev.w >= 0) sh.shell_dirty[ev.w] = 1;
         }
-        B.evmark[w] = 0;
-        // the particles whose shell lists this event can change: the old and
-        // new owner of w and the owners of its solid neighbours (their
-        // fluid-neighbour masks)
-        if (ev.z >= 0) sh.shell_dirty[ev.z] = 1;
-        if (ev.w >= 0) sh.shell_dirty[ev.w] = 1;
-#pragma unroll
-        for (int i = 1; i < 19; i++) {
-            const int o = B.owner[nbr_index(B, w, cx(i), cy(i), cz(i))];
-            if (o >= 0) sh.shell_dirty[o] = 1;
-        }
-        // A solid node left without fluid neighbours takes density 0: the
-        // fused step may have counted reflected populations in it while it
-        // was a shell node, and no later pass rewrites it (the particle's
-        // Shan-Chen force reads it through its shell neighbours).
-        auto update = [&](int n) {
-            shell_update(B, n);
+        if (i <= 18) {
+            const int nx_ = wrap1(x + ix, B.nx), ny_ = wrap1(y + iy, B.ny), nz_ = wrap1(z + iz, B.nz);
+            const int n = nx_ + B.nx * (ny_ + B.ny * nz_);
+            if (i >= 1) {
+                const int o = B.owner[n];
+                if (o >= 0) sh.shell_dirty[o] = 1;
+            }
+            // A solid node left without fluid neighbours takes density 0: the
+            // fused step may have counted reflected populations in it while it
+            // was a shell node, and no later pass rewrites it (the particle's
+            // Shan-Chen force reads it through its shell neighbours).
+            shell_update_at(B, nx_, ny_, nz_);
             if (B.flags[n] == FL_SOLID) {
                 rcur[2 * (size_t)n] = R(0);
                 rcur[2 * (size_t)n + 1] = R(0);
             }
-        };
-        update(w);
-#pragma unroll
-        for (int i = 1; i < 19; i++) update(nbr_index(B, w, cx(i), cy(i), cz(i)));
+        }
     }
 }
 
