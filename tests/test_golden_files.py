@@ -9,9 +9,9 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def test_layers_golden_coverage_is_informative():
-    """On the layered 80^3 case the interface coverage stays well inside
+    """On the layered 112^3 case the interface coverage stays well inside
     (0, 1) and changes over the run, so comparing it tests something."""
-    g = json.load(open(os.path.join(GOLDEN, "lt_layers80.json")))
+    g = json.load(open(os.path.join(GOLDEN, "lt_layers112.json")))
     cov = np.array(g["coverage"])
     assert len(cov) == len(g["steps"]) == len(g["L"])
     assert np.all(cov < 0.95) and np.all(cov > 0.05)
