@@ -114,10 +114,10 @@ struct CellGeom {
     double len[3];
 };
 CellGeom cell_geom(const lb_params& p) {
-    // cells at least 2R + 2 wide: neighbour list for node claims (centre
-    // distance <= 2R + 2) and lubrication (gap < lub_cut <= 2) fit in +-1 cell
+    // cells at least as wide as the neighbour-list reach, so that the list
+    // of a particle comes from the 27 cells around its own
     CellGeom g;
-    const double cmin = 2.0 * bound_radius(p) + 2.0 + (p.lub_cut > 2.0 ? p.lub_cut - 2.0 : 0.0);
+    const double cmin = nl_reach(bound_radius(p), p.lub_cut);
     const int L[3] = {p.nx, p.ny, p.nz};
     for (int a = 0; a < 3; a++) {
         int n = (int)std::floor(L[a] / cmin);
@@ -278,6 +278,8 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     sh.shell_dirty = cv.take<int>(NPa);
     sh.xref = cv.take<float>((size_t)NPa * 3);
     sh.exact = cv.take<int>(NPa);
+    sh.xnl = cv.take<float>((size_t)NPa * 3);
+    sh.nl_flag = cv.take<int>(2);
     sh.zdrag = cv.take<double>((size_t)NPa * 21);
     sh.dv = cv.take<double>((size_t)NPa * 6);
     sh.err = cv.take<int>(1);
@@ -432,14 +434,14 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
     h->reflect = 0;
     for (int b = 0; b < h->nb; b++)
         if (h->has_walls[b]) h->reflect = 1;
-    k_step_begin<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->nb, h->sh, h->total_cells, mnext);
+    k_step_begin<<<SMALL_GRID, SMALL_BLOCK, 0, st>>>(h->d_boxes, h->nb, h->sh, h->total_cells, mnext, par);
     launches++;
     if (NP > 0) {
         const int pg = (NP + 255) / 256;
-        k_cell_count<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
-        k_cell_scan<<<h->nb, 1024, 0, st>>>(h->d_boxes, h->sh);
-        k_cell_fill<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
-        k_nlist<<<(NP + NLIST_WARPS - 1) / NLIST_WARPS, 32 * NLIST_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
+        k_cell_count<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP, par);
+        k_cell_scan<<<h->nb, 1024, 0, st>>>(h->d_boxes, h->sh, par);
+        k_cell_fill<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP, par);
+        k_nlist<<<(NP + NLIST_WARPS - 1) / NLIST_WARPS, 32 * NLIST_WARPS, 0, st>>>(h->d_boxes, h->sh, NP, par);
         if (mark(1) != LB_OK) return LB_ECUDA;
         k_remap_detect<<<NP, 32 * DETECT_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         if (mark(2) != LB_OK) return LB_ECUDA;
@@ -472,10 +474,10 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
             // implicit update: velocities, the fluid's share on the links, positions
             k_md_solve<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
             CK(h->ops->couple_correct(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, NP));
-            k_md_move<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+            k_md_move<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP, par);
             launches += 5;
         } else {
-            k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
+            k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP, par);
             launches += 3;
         }
     }
@@ -682,8 +684,10 @@ int after_init(lb_handle* h, int64_t t) {
     // every shell list is rebuilt at the first step of a new state
     if (h->NP > 0) {
         CK(cudaMemsetAsync(h->sh.shell_dirty, 1, sizeof(int) * h->NP, h->stream));
-        // and the first remap scans every particle's whole window
+        // and the first remap scans every particle's whole window, and the
+        // first step builds the cell and neighbour lists
         CK(cudaMemsetAsync(h->sh.exact, 0, sizeof(int) * h->NP, h->stream));
+        CK(cudaMemsetAsync(h->sh.nl_flag, 1, 2 * sizeof(int), h->stream));
         CK(cudaStreamSynchronize(h->stream));
     }
     // graphs bake in the per-box wall flags (the wall-shell launches and the

@@ -128,6 +128,8 @@ struct Shared {
     int* shell_dirty;           // [NP] nonzero: rebuild the shell list (events nearby, or a new state)
     int shell_cap;
     float* xref;                // [NP][3] position at the last remap (FP32 copy)
+    float* xnl;                 // [NP][3] positions at the last neighbour-list build (FP32 copy)
+    int* nl_flag;               // [2] by step parity: 1 = rebuild the cell and neighbour lists in that step
     double* zdrag;              // [NP][21] drag tensor Z of the links (upper triangle, row-major; implicit update)
     double* dv;                 // [NP][6] velocity change dV of the implicit update
     int* exact;                 // [NP] 1: p owns exactly the nodes inside it at xref (remap fast path)
@@ -136,6 +138,14 @@ struct Shared {
 };
 
 constexpr int NL_MAX = 32;
+// The neighbour list holds every particle within the reach its users need
+// (claims within 2R, the remap's scan of nodes left behind within 2R + 1.5,
+// lubrication within 2R + lub_cut) plus NL_SKIN; it is rebuilt when some
+// particle has moved more than NL_SKIN / 2 since the last build.
+constexpr float NL_SKIN = 1.0f;
+__host__ __device__ inline double nl_reach(double rb, double lub_cut) {
+    return 2.0 * rb + (lub_cut > 1.55 ? lub_cut : 1.55) + (double)NL_SKIN;
+}
 
 // ------------------------------------------------------------ SplitMix64
 // Steele, Lea & Flood (OOPSLA 2014): output n of a generator seeded with s

@@ -22,26 +22,35 @@ __device__ __forceinline__ int cell_of(const BoxDev& B, const double X[3]) {
     return B.cell_off + c[0] + B.nc[0] * (c[1] + B.nc[1] * c[2]);
 }
 
-static __global__ void k_step_begin(const BoxDev* __restrict__ boxes, int nb, Shared sh, int total_cells, int mslot_next) {
+// par: parity of this step.  The lists are rebuilt in this step when
+// nl_flag[par] is set (by the MD of the previous step, or an init); the
+// flag of the next step is cleared here, before this step's MD can set it.
+static __global__ void k_step_begin(const BoxDev* __restrict__ boxes, int nb, Shared sh, int total_cells, int mslot_next,
+                                    int par) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int i = tid; i < total_cells; i += gridDim.x * blockDim.x) sh.cell_count[i] = 0;
-    if (tid == 0) *sh.ev_count = 0;
+    if (sh.nl_flag[par])
+        for (int i = tid; i < total_cells; i += gridDim.x * blockDim.x) sh.cell_count[i] = 0;
+    if (tid == 0) {
+        *sh.ev_count = 0;
+        sh.nl_flag[par ^ 1] = 0;
+    }
     if (tid < nb) {
         boxes[tid].mass_acc[mslot_next * 2 + 0] = 0.0;
         boxes[tid].mass_acc[mslot_next * 2 + 1] = 0.0;
     }
 }
 
-static __global__ void k_cell_count(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+static __global__ void k_cell_count(const BoxDev* __restrict__ boxes, Shared sh, int NP, int par) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
+    if (p >= NP || !sh.nl_flag[par]) return;
     const BoxDev& B = boxes[sh.pbox[p]];
     atomicAdd(&sh.cell_count[cell_of(B, sh.part[p].X)], 1);
 }
 
 // one block per box: exclusive scan of the cell counts (offset by the box's
 // first particle), cursors = starts
-static __global__ void k_cell_scan(const BoxDev* __restrict__ boxes, Shared sh) {
+static __global__ void k_cell_scan(const BoxDev* __restrict__ boxes, Shared sh, int par) {
+    if (!sh.nl_flag[par]) return;  // the whole block leaves together
     const BoxDev& B = boxes[blockIdx.x];
     const int ncell = B.nc[0] * B.nc[1] * B.nc[2];
     __shared__ int s_tmp[1024];
@@ -71,32 +80,36 @@ static __global__ void k_cell_scan(const BoxDev* __restrict__ boxes, Shared sh) 
     }
 }
 
-static __global__ void k_cell_fill(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+static __global__ void k_cell_fill(const BoxDev* __restrict__ boxes, Shared sh, int NP, int par) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
+    if (p >= NP || !sh.nl_flag[par]) return;
     const BoxDev& B = boxes[sh.pbox[p]];
     const int pos = atomicAdd(&sh.cell_cursor[cell_of(B, sh.part[p].X)], 1);
     sh.cell_list[pos] = p;
 }
 
-// Neighbour list of p: every particle whose centre lies within
-// 2R + max(2, lub_cut) (a node owned before the move lies within R + |U| <=
-// R + 1 of the new centre, and lubrication acts below a gap of lub_cut).
+// Neighbour list of p: every particle whose centre lies within nl_reach (a
+// node owned before the move lies within R + |U| <= R + 1 of the new
+// centre, lubrication acts below a gap of lub_cut, NL_SKIN of slack for the
+// steps until the next build).  Built only in steps that rebuild the lists;
+// the positions of the build are kept in xnl.
 // One warp per particle; lane k scans cell k of the 3x3x3 block around p.
 // FP32 distances against a slightly larger radius give a superset of the
 // exact list, which is harmless for both users (claims and pair forces).
 // The list is sorted by particle index, so the pair-force sums do not
 // depend on the order in which the cells were filled.
 constexpr int NLIST_WARPS = 4;
-static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev* __restrict__ boxes, Shared sh, int NP,
+                                                                     int par) {
     __shared__ int s_ids[NLIST_WARPS][NL_MAX];
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * NLIST_WARPS + wib;
-    if (p >= NP) return;  // the whole warp leaves together
+    if (p >= NP || !sh.nl_flag[par]) return;  // the whole warp leaves together
     const BoxDev& B = boxes[sh.pbox[p]];
     const PartStateF pf = sh.partf[p];
-    const float reach = 2.0f * (float)B.rb + fmaxf(2.0f, (float)B.lub_cut);
+    if (lane < 3) sh.xnl[(size_t)p * 3 + lane] = pf.X[lane];
+    const float reach = (float)nl_reach(B.rb, B.lub_cut);
     const float lim2 = reach * reach * 1.0001f + 1e-3f;
     const float Lf[3] = {(float)B.nx, (float)B.ny, (float)B.nz};
     // the block of cells around the cell of p (from its FP64 position)
@@ -1276,7 +1289,17 @@ static __global__ void __launch_bounds__(32 * MD_WARPS) k_md_forces(const BoxDev
     if (lane < 6) sh.force_last[(size_t)p * 6 + lane] = mine;
     double F[3] = {0.0, 0.0, 0.0};
     const int nn = sh.nlist_n[p];
-    if (lane < nn) pair_force(B, sh.part[p], sh.part[sh.nlist[(size_t)p * NL_MAX + lane]], F);
+    if (lane < nn) {
+        // FP32 prefilter: only pairs within contact or lubrication range
+        // (centre distance below 2 R_b + lub_cut, with slack for the FP32
+        // positions) take the FP64 force
+        const int q = sh.nlist[(size_t)p * NL_MAX + lane];
+        const PartStateF a = sh.partf[p], b = sh.partf[q];
+        const float dx = mimgf(a.X[0] - b.X[0], (float)B.nx), dy = mimgf(a.X[1] - b.X[1], (float)B.ny),
+                    dz = mimgf(a.X[2] - b.X[2], (float)B.nz);
+        const float lim = 2.0f * (float)B.rb + (float)B.lub_cut + 0.01f;
+        if (dx * dx + dy * dy + dz * dz < lim * lim) pair_force(B, sh.part[p], sh.part[q], F);
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -1309,6 +1332,15 @@ __device__ __forceinline__ void rotate_spheroid(const BoxDev& B, double W[3], do
         for (int a = 0; a < 3; a++) e[a] = en[a] / nn;
     }
     inertia(L, W, true);
+}
+
+// the lists of the next step (parity par ^ 1) are rebuilt when p has moved
+// more than NL_SKIN / 2 since the last build
+__device__ __forceinline__ void nl_check(const BoxDev& B, const Shared& sh, int p, const PartStateF& pf, int par) {
+    const float* xb = sh.xnl + (size_t)p * 3;
+    const float dx = mimgf(pf.X[0] - xb[0], (float)B.nx), dy = mimgf(pf.X[1] - xb[1], (float)B.ny),
+                dz = mimgf(pf.X[2] - xb[2], (float)B.nz);
+    if (!(dx * dx + dy * dy + dz * dz <= 0.25f * NL_SKIN * NL_SKIN)) sh.nl_flag[par ^ 1] = 1;
 }
 
 // Solve A x = b for a 6 x 6 system by Gaussian elimination with partial
@@ -1391,8 +1423,8 @@ static __global__ void k_md_solve(const BoxDev* __restrict__ boxes, Shared sh, i
     }
 }
 
-// Position half: X += U (periodic) and the FP32 copy.
-static __global__ void k_md_move(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+// Position half: X += U (periodic) and the FP32 copy.  par: parity of this step.
+static __global__ void k_md_move(const BoxDev* __restrict__ boxes, Shared sh, int NP, int par) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NP) return;
     const BoxDev& B = boxes[sh.pbox[p]];
@@ -1410,11 +1442,12 @@ static __global__ void k_md_move(const BoxDev* __restrict__ boxes, Shared sh, in
         pf.W[a] = (float)ps.W[a];
     }
     sh.partf[p] = pf;
+    nl_check(B, sh, p, pf, par);
 }
 
 // leap-frog: U += F/m, omega += T/J (spheroids: rotate_spheroid), X += U
-// (periodic); accumulators zeroed
-static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+// (periodic); accumulators zeroed.  par: parity of this step.
+static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared sh, int NP, int par) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NP) return;
     const BoxDev& B = boxes[sh.pbox[p]];
@@ -1440,6 +1473,7 @@ static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared s
             pf.W[a] = (float)ps.W[a];
         }
         sh.partf[p] = pf;
+        nl_check(B, sh, p, pf, par);
     }
     for (int a = 0; a < 6; a++) fp[a] = 0.0;
 }
