@@ -350,6 +350,7 @@ void fill_params(lb_handle* h) {
             const int nmax = p.nx > p.ny ? (p.nx > p.nz ? p.nx : p.nz) : (p.ny > p.nz ? p.ny : p.nz);
             const double eps_pos = 1.2e-7 * (double)nmax;
             B.det_reach2 = (float)((R + 1.5) * (R + 1.5));
+            B.det_rb = (float)R;
             B.det_R2 = (float)R2;
             B.det_band = (float)(0.02 + 2e-3 * R * R + 4.0 * (R + 1.5) * eps_pos);
             B.det_qlim = (float)(R * R) + B.det_band;

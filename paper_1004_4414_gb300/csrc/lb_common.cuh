@@ -92,8 +92,9 @@ struct BoxDev {
     // host): squared reach of the scan window, sphere radius^2, the band
     // of R^2 within which the FP64 test decides, the FP32 bound beyond
     // which no node is inside a neighbour, and the spheroid form's
-    // constants R^2, c^2, R^2 c^2 and band
+    // constants R^2, c^2, R^2 c^2 and band; the bounding radius in FP32
     float det_reach2, det_R2, det_band, det_qlim;
+    float det_rb;
     float det_sR2, det_sc2, det_sR2c2, det_sband;
 };
 
@@ -338,8 +339,9 @@ struct Pop {
         }
     }
     // both components through a pair pointer
-    __device__ __forceinline__ void ld2(const S2* p, int i, R& a, R& b) const {
-        const S2 v = *p;
+    __device__ __forceinline__ void ld2(const S2* p, int i, R& a, R& b) const { cvt2(*p, i, a, b); }
+    // both components of a stored pair v of direction i
+    __device__ __forceinline__ void cvt2(const S2 v, int i, R& a, R& b) const {
         if constexpr (P::dev) {
             const float2 d = to_f2(v);
             a = fmaf(wgt<float>(i), d.x, zr[0][is_axis(i) ? 0 : 1]);

@@ -31,7 +31,7 @@ constexpr int EV_GRID = 304, EV_BLOCK = 256, NODE_GRID = 1216, NODE_BLOCK = 256;
 template <int PAR, int TY, bool T1, bool BB>
 cudaError_t step_t(int ntiles, cudaStream_t st, const BoxDev* boxes, const TileDev* tiles, Shared sh, int rc, int rn,
                    int rz, int mslot) {
-    const size_t smem = StepSmem<RR, TY>::bytes;
+    const size_t smem = StepStage<PP, TY>::smem;
     k_step<PP, PAR, TY, T1, BB><<<ntiles, dim3(32, TY), smem, st>>>(boxes, tiles, sh, rc, rn, rz, mslot);
     return cudaGetLastError();
 }
@@ -39,7 +39,7 @@ cudaError_t step_t(int ntiles, cudaStream_t st, const BoxDev* boxes, const TileD
 template <int PAR, int TY, bool T1, bool BB>
 cudaError_t set_attr() {
     return cudaFuncSetAttribute(k_step<PP, PAR, TY, T1, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)StepSmem<RR, TY>::bytes);
+                                (int)StepStage<PP, TY>::smem);
 }
 
 template <int PAR, int TY, bool T1, bool BB>

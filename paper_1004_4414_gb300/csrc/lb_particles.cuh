@@ -183,6 +183,19 @@ static __global__ void __launch_bounds__(32 * NLIST_WARPS) k_nlist(const BoxDev*
 // plain sequential evaluation, decides.  FP64 is slow on this GPU, so it is
 // kept off the common path.
 constexpr int DETECT_WARPS = 4, DETECT_QUEUE = 256;
+// FP64 inside test of node (gx, gy, gz) for particle q: the squared centre
+// distance if the node is inside, else -1.  Out of line so that the rare
+// calls (FP32 undecided within a band of the surface, or a node near a second
+// particle) branch to it instead of being predicated into every candidate's
+// instruction stream: FP64 instructions issue at 1/16 of the FP32 rate here.
+static __device__ __noinline__ double exact_inside(const BoxDev& B, const PartState* __restrict__ part, int q,
+                                                   int gx, int gy, int gz) {
+    const double* C = part[q].X;
+    const double dx = mimg((double)gx - C[0], (double)B.nx), dy = mimg((double)gy - C[1], (double)B.ny),
+                 dz = mimg((double)gz - C[2], (double)B.nz);
+    return inside_shape(B, dx, dy, dz, part[q].E) ? dist2_nc(dx, dy, dz) : -1.0;
+}
+
 static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     __shared__ int s_queue[DETECT_WARPS][DETECT_QUEUE];  // annulus candidates of the fast path
     // the close list, built by each warp for itself
@@ -198,8 +211,7 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
     // FP32 distances (spheres) or quadratic forms (spheroids) decide away
     // from the surface, the FP64 test (inside_shape) within a band of it
     const bool sph = B.aspect == 1.0;
-    const double R = B.rb, R2 = B.radius * B.radius;
-    const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
+    const float R = B.det_rb;
     const float Lf[3] = {(float)B.nx, (float)B.ny, (float)B.nz};
     const int nn = sh.nlist_n[p];
     // A node inside p can also be inside q only if |X_q - X_p| <= 2R (R the
@@ -207,7 +219,7 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
     // covers the FP32 centres) decide the claims of nodes inside p.  A node
     // p owned but left may lie within 2R + 1.5 of q, so that rare case scans
     // the whole list.
-    const float rcl = 2.0f * (float)R + 0.05f;
+    const float rcl = 2.0f * R + 0.05f;
     int ncl = 0;
     {
         bool close = false;
@@ -231,7 +243,7 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
     // window: every node within R + 1.5 of the centre (a node owned before
     // the move lies within R + |U| <= R + 1 of the new centre; the 0.5 of
     // slack covers the FP32 centre)
-    const float reach = (float)R + 1.5f;
+    const float reach = R + 1.5f;
     int lo[3], span[3];
     float off[3];  // X_p - lo: node (lo + k) sits at k - off from the centre
     const int dims[3] = {B.nx, B.ny, B.nz};
@@ -284,25 +296,20 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
         if (!c.ok || c.own == OWN_WALL) return;
         const float fx = c.fx, fy = c.fy, fz = c.fz, d2f = c.d2f;
         const int gx = c.gx, gy = c.gy, gz = c.gz, own = c.own;
-        // FP64 inside test of this node for particle q; d2 = squared
-        // centre distance (the claim goes to the nearest centre)
-        auto exact_in = [&](int q, double& d2) {
-            const double* C = sh.part[q].X;
-            const double dx = mimg((double)gx - C[0], L[0]), dy = mimg((double)gy - C[1], L[1]),
-                         dz = mimg((double)gz - C[2], L[2]);
-            d2 = dist2_nc(dx, dy, dz);
-            return inside_shape(B, dx, dy, dz, sh.part[q].E);
-        };
+        // FP64 inside tests (exact_inside) where FP32 cannot decide; d2p is
+        // the squared centre distance to p once known (the claim goes to the
+        // nearest centre)
         double d2p = -1.0;
         bool inside;
-        if (sph) {
-            if (fabsf(d2f - R2f) > band) inside = d2f < R2f;
-            else inside = exact_in(p, d2p);
-        } else {
+        const float gap = sph ? d2f - R2f : [&] {
             const float sf = fx * ex_ + fy * ey_ + fz * ez_;
-            const float Ff = R2s * sf * sf + c2s * (d2f - sf * sf);
-            if (fabsf(Ff - R2c2) > sband) inside = Ff < R2c2;
-            else inside = exact_in(p, d2p);
+            return R2s * sf * sf + c2s * (d2f - sf * sf) - R2c2;
+        }();
+        if (fabsf(gap) > (sph ? band : sband)) {
+            inside = gap < 0.0f;
+        } else {
+            d2p = exact_inside(B, sh.part, p, gx, gy, gz);
+            inside = d2p >= 0.0;
         }
         if (!(inside || own == p)) return;
         bool other = false, anyone = false;
@@ -314,11 +321,11 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
             const float ez = mimgf(fz - s_rq[wib][k][2], Lf[2]);
             if (ex * ex + ey * ey + ez * ez > qlim) continue;
             const int q = s_nid[wib][k];
-            double d2q;
-            if (exact_in(q, d2q)) {
+            const double d2q = exact_inside(B, sh.part, q, gx, gy, gz);
+            if (d2q >= 0.0) {
                 anyone = true;
                 if (inside) {
-                    if (d2p < 0.0) exact_in(p, d2p);
+                    if (d2p < 0.0) d2p = exact_inside(B, sh.part, p, gx, gy, gz);
                     if (d2q < d2p || (d2q == d2p && q < p)) other = true;
                 }
             }
@@ -401,7 +408,7 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
     } else {
         // rows (ky, kz) of the window, one per lane; the annulus crosses a
         // row in at most two x intervals, whose nodes go to a per-warp queue
-        const float r_out = (float)R + delta + 0.1f, r_in = fmaxf((float)R - delta - 0.1f, 0.0f);
+        const float r_out = R + delta + 0.1f, r_in = fmaxf(R - delta - 0.1f, 0.0f);
         int* q = s_queue[wib];
         const int nrows = span[1] * span[2];
         for (int rb = wib * 32; rb < nrows; rb += 32 * DETECT_WARPS) {

@@ -136,6 +136,28 @@ struct StepSmem {
     static constexpr size_t bytes = (psi_elems + yb_elems) * sizeof(R) + (size_t)3 * PLANE + 64;
 };
 
+// Staging of the next plane's populations (16-bit storage): each thread
+// copies the 18 pairs its node reads in plane z + 1 into its own column of
+// a [18][32 TY] shared array with cp.async while plane z is computed, so
+// that the population loads of the step overlap the work of the plane
+// before (the 16-byte-aligned array follows the window).  Measured at
+// 256^3: 3 % faster for FP16 storage, 2 % slower for FP32, which keeps
+// its loads in registers.
+template <class P, int TY>
+struct StepStage {
+    static constexpr bool on = P::dev;
+    static constexpr size_t offset = (StepSmem<typename P::real, TY>::bytes + 15) & ~(size_t)15;
+    static constexpr size_t bytes = on ? (size_t)18 * 32 * TY * sizeof(typename P::st2) : 0;
+    static constexpr size_t smem = offset + bytes;
+};
+__device__ __forceinline__ void cp_async_sz(void* sdst, const void* gsrc, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // T1: every box has tau^r = tau^b = 1, where BGK gives f* = f^eq: the
 // loaded populations then only feed the moments and need not stay live.
 // Resident CTAs per SM: three for the FP32 / 16-bit tau = 1 kernel (80
@@ -276,6 +298,29 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
     R2 msum = p2(R(0));  // fluid mass sent (own precision: Eq. masscorr uses small differences)
     __syncthreads();
 
+    // this thread's 18 staged pairs: s_stage[(i - 1) * 32 TY + tid]
+    using ST = StepStage<P, TY>;
+    S2* const s_stage = reinterpret_cast<S2*>(smem_raw + ST::offset);
+    // issue the copies of the pairs node (x, y, zz) reads (if it is fluid)
+    auto stage = [&](int zz, bool fl) {
+        if constexpr (ST::on) {
+            if (fl) {
+                const int zm = (zz == 0) ? (nz - 1) * nxy : -nxy, zp = (zz == nz - 1) ? -(nz - 1) * nxy : nxy;
+                const int nn = nxyc + nxy * zz;
+#pragma unroll
+                for (int i = 1; i < 19; i++) {
+                    const int j = opp(i);
+                    const int o = (cx(j) < 0 ? oxm : (cx(j) > 0 ? oxp : 0)) + (cy(j) < 0 ? oym : (cy(j) > 0 ? oyp : 0)) +
+                                  (cz(j) < 0 ? zm : (cz(j) > 0 ? zp : 0));
+                    const S2* p = PAR == 0 ? pop.pair(i, nn) : pop.pair(j, nn + o);
+                    cp_async_sz(s_stage + (i - 1) * (32 * TY) + tid, p, (int)sizeof(S2));
+                }
+            }
+            cp_async_commit();
+        }
+    };
+    stage(z0, active && !(FLG(sc_, ly + 1, lx + 1) & FL_SOLID));
+
     for (int z = z0; z < z0 + d; z++) {
         // window of plane z + 2, fetched now and stored at the end of this
         // plane, so that its load latency hides behind the plane's work
@@ -314,11 +359,18 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
                 for (int i = 1; i < 19; i++)
                     smask |= (unsigned)(wf[cz(i) + 1][cy(i) * W2 + cx(i)] & FL_SOLID) << i;
             }
+            if constexpr (ST::on) {
+                // staged during the previous plane (this thread's own copies)
+                cp_async_wait_all();
 #pragma unroll
-            for (int i = 1; i < 19; i++) {
-                // even steps: own slot i; odd steps: slot opp(i) of x - c_i
-                const S2* p = PAR == 0 ? pop.pair(i, n) : pop.pair(opp(i), n + off(opp(i)));
-                pop.ld2(p, i, f[i].x, f[i].y);
+                for (int i = 1; i < 19; i++) pop.cvt2(s_stage[(i - 1) * (32 * TY) + tid], i, f[i].x, f[i].y);
+            } else {
+#pragma unroll
+                for (int i = 1; i < 19; i++) {
+                    // even steps: own slot i; odd steps: slot opp(i) of x - c_i
+                    const S2* p = PAR == 0 ? pop.pair(i, n) : pop.pair(opp(i), n + off(opp(i)));
+                    pop.ld2(p, i, f[i].x, f[i].y);
+                }
             }
             // rho^c is the density field (the sum of the values the previous
             // step sent here); the rest population is rho^c minus the 18
@@ -373,6 +425,9 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
             if (!(rho.x > R(0)) || !(rho.y > R(0)) || !(vx * vx + vy * vy + vz * vz < R(0.25) * rtot * rtot))
                 set_err(sh.err, ERR_UNSTABLE);
         }
+        // the moments have consumed every staged pair of this node: stage
+        // plane z + 1 (its flags are in the window) behind this plane's work
+        if (more) stage(z + 1, active && !(wf[2][0] & FL_SOLID));
 
         const unsigned FULL = 0xffffffffu;
         // per-group partial sums of the pairs this node sends (mid: no x
@@ -540,6 +595,7 @@ static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
 
         __syncthreads();
     }
+    if constexpr (StepStage<P, TY>::on) cp_async_wait_all();  // none left in flight at exit
     // last own plane and the ring plane above the chunk
     if (active) {
 #pragma unroll
