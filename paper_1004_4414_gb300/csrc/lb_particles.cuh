@@ -735,6 +735,9 @@ static __global__ void k_remap_finish(const BoxDev* __restrict__ boxes, Shared s
 // list (node, mask of fluid neighbours, x | y << 16, z) is kept across steps
 // and rebuilt only when an event touched the particle (shell_dirty).
 constexpr int SHELL_WARPS = 4;
+constexpr int SHELL_CUBE = 8192;  // flag bytes of a rebuild window with its one-node ring
+constexpr int SHELL_QW = 256;     // shell-flagged candidates a warp can queue in a rebuild
+constexpr int SHELL_KQ = 4;       // queued candidates per thread whose owner loads are in flight together
 template <class R>
 static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const BoxDev* __restrict__ boxes, Shared sh,
                                                                           int rc, int NP) {
@@ -818,6 +821,138 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
     }
     const int total = span[0] * span[1] * span[2];
     const float lim = reach * reach;
+    constexpr int NT = 32 * SHELL_WARPS;
+    // Rebuild from a shared-memory copy of the window's flags (windows of
+    // up to SHELL_CUBE nodes with their ring, which covers R + 0.5 <= 8 or
+    // so): the candidates are tested in shared memory, and only the shell-
+    // flagged ones within reach go to a queue, in window order.  Their
+    // owners are loaded together, a block-wide prefix gives each shell node
+    // of p its list position (window order again, so the list does not
+    // depend on timing), and the fluid-neighbour masks come from the copy.
+    // Three dependent rounds of global loads (flags, owners, densities)
+    // instead of one per candidate.  Larger windows, or a queue that would
+    // overflow, take the two-pass scan below.
+    const int wx = span[0] + 2, wy = span[1] + 2, wz = span[2] + 2;
+    if (wx * wy * wz <= SHELL_CUBE) {
+        __shared__ uint8_t s_fl[SHELL_CUBE];
+        __shared__ int s_q[SHELL_WARPS][SHELL_QW];
+        __shared__ int s_qn[SHELL_WARPS];
+        __shared__ int s_kc[SHELL_KQ][SHELL_WARPS];
+        const int cube = wx * wy * wz;
+        for (int i = threadIdx.x; i < cube; i += NT) {
+            const int a = i % wx, b = (i / wx) % wy, c = i / (wx * wy);
+            const int gx = wrapi(lo[0] - 1 + a, nx), gy = wrapi(lo[1] - 1 + b, ny), gz = wrapi(lo[2] - 1 + c, nz);
+            s_fl[i] = __ldg(flags + gx + nx * (gy + ny * gz));
+        }
+        __syncthreads();
+        // warp w queues the candidates of the contiguous range [beg, end)
+        const int per = (total + SHELL_WARPS - 1) / SHELL_WARPS;
+        const int beg = wib * per, end = min(total, beg + per);
+        int qn = 0;
+        for (int b0 = beg; b0 < end; b0 += 32) {
+            const int idx = b0 + lane;
+            bool c = false;
+            if (idx < end) {
+                const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+                const float dx = mimgf((float)kx - off[0], (float)nx), dy = mimgf((float)ky - off[1], (float)ny),
+                            dz = mimgf((float)kz - off[2], (float)nz);
+                c = dx * dx + dy * dy + dz * dz <= lim && (s_fl[(kx + 1) + wx * ((ky + 1) + wy * (kz + 1))] & FL_SHELL);
+            }
+            const unsigned m = __ballot_sync(FULL, c);
+            const int at = qn + __popc(m & ((1u << lane) - 1u));
+            if (c && at < SHELL_QW) s_q[wib][at] = idx;
+            qn += __popc(m);
+        }
+        if (lane == 0) s_qn[wib] = qn;
+        __syncthreads();
+        int qoff[SHELL_WARPS + 1];
+        bool fits = true;
+        qoff[0] = 0;
+#pragma unroll
+        for (int w = 0; w < SHELL_WARPS; w++) {
+            fits = fits && s_qn[w] <= SHELL_QW;
+            qoff[w + 1] = qoff[w] + s_qn[w];
+        }
+        if (fits) {  // the same for the whole block
+            const int nq = qoff[SHELL_WARPS];
+            int listed = 0;  // shell nodes of p listed so far
+            for (int q0 = 0; q0 < nq; q0 += SHELL_KQ * NT) {
+                int kidx[SHELL_KQ];
+                bool tk[SHELL_KQ];
+#pragma unroll
+                for (int k = 0; k < SHELL_KQ; k++) {
+                    const int q = q0 + k * NT + threadIdx.x;
+                    kidx[k] = -1;
+                    tk[k] = false;
+                    if (q < nq) {
+                        int w = 0;
+#pragma unroll
+                        for (int v = 1; v < SHELL_WARPS; v++) w += q >= qoff[v];
+                        const int idx = s_q[w][q - qoff[w]];
+                        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+                        const int gx = wrapi(lo[0] + kx, nx), gy = wrapi(lo[1] + ky, ny), gz = wrapi(lo[2] + kz, nz);
+                        kidx[k] = idx;
+                        tk[k] = __ldg(owner + gx + nx * (gy + ny * gz)) == p;
+                    }
+                }
+                unsigned bm[SHELL_KQ];
+#pragma unroll
+                for (int k = 0; k < SHELL_KQ; k++) {
+                    bm[k] = __ballot_sync(FULL, tk[k]);
+                    if (lane == 0) s_kc[k][wib] = __popc(bm[k]);
+                }
+                __syncthreads();
+                int before = listed, round = 0;
+#pragma unroll
+                for (int k = 0; k < SHELL_KQ; k++)
+#pragma unroll
+                    for (int w = 0; w < SHELL_WARPS; w++) round += s_kc[k][w];
+#pragma unroll
+                for (int k = 0; k < SHELL_KQ; k++) {
+                    int pos = before;
+#pragma unroll
+                    for (int w = 0; w < SHELL_WARPS; w++)
+                        if (w < wib) pos += s_kc[k][w];
+                    pos += __popc(bm[k] & ((1u << lane) - 1u));
+                    if (tk[k]) {
+                        // virtual density and list entry of the shell node
+                        const int idx = kidx[k];
+                        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+                        const int gx = wrapi(lo[0] + kx, nx), gy = wrapi(lo[1] + ky, ny), gz = wrapi(lo[2] + kz, nz);
+                        const int n = gx + nx * (gy + ny * gz);
+                        const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
+                        const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
+                        const int ozm = gz == 0 ? (nz - 1) * nxy : -nxy, ozp = gz == nz - 1 ? -(nz - 1) * nxy : nxy;
+                        const uint8_t* const fc = s_fl + (kx + 1) + wx * ((ky + 1) + wy * (kz + 1));
+                        R s0 = R(0), s1 = R(0);
+                        unsigned fmask = 0;
+#pragma unroll
+                        for (int i = 1; i < 19; i++) {
+                            if (fc[cx(i) + wx * (cy(i) + wy * cz(i))] & FL_SOLID) continue;
+                            const int m = n + (cx(i) < 0 ? oxm : (cx(i) > 0 ? oxp : 0)) +
+                                          (cy(i) < 0 ? oym : (cy(i) > 0 ? oyp : 0)) + (cz(i) < 0 ? ozm : (cz(i) > 0 ? ozp : 0));
+                            const R2 v = r2[m];
+                            s0 += v.x;
+                            s1 += v.y;
+                            fmask |= 1u << i;
+                        }
+                        if (pos < scap) slist[pos] = make_int4(n, (int)fmask, (int)((unsigned)gx | ((unsigned)gy << 16)), gz);
+                        finish(n, s0, s1, __popc(fmask));
+                    }
+#pragma unroll
+                    for (int w = 0; w < SHELL_WARPS; w++) before += s_kc[k][w];
+                }
+                listed += round;
+                __syncthreads();  // s_kc is rewritten by the next round
+            }
+            if (threadIdx.x == 0) {
+                sh.shell_n[p] = listed < scap ? listed : scap;
+                if (listed > scap) set_err(sh.err, ERR_OVERFLOW);
+                else sh.shell_dirty[p] = 0;
+            }
+            return;
+        }
+    }
     // candidate idx of the window: a shell node of p?
     auto test = [&](int idx, int& n, int& cxy, int& cz) -> bool {
         if (idx >= total) return false;
