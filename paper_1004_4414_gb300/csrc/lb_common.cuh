@@ -415,6 +415,27 @@ __device__ __forceinline__ int wrapi(int a, int n) {
 }
 // a + d for |d| <= 1 on a periodic axis of length n (no division)
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+// Scan-window coordinates without integer division.  idx / d for
+// 0 <= idx < 2^16 and 1 <= d < 2^16 is the high word of idx * m with
+// m = floor((2^32 - 1) / d) + 1: m exceeds 2^32 / d by at most 1, which adds
+// less than 2^-16 to idx / d, and the fraction of idx / d is at most
+// 1 - 1/d < 1 - 2^-16.  When every window coordinate lies in [-n, 2n) the
+// periodic wrap is a compare.  (fast: both hold; otherwise the division.)
+struct WinDiv {
+    int d0, d1;
+    unsigned m0, m1;
+    bool fast;
+    __device__ __forceinline__ WinDiv(int a, int b, bool ok)
+        : d0(a), d1(b), m0(0xffffffffu / (unsigned)a + 1u), m1(0xffffffffu / (unsigned)b + 1u), fast(ok) {}
+    // idx = kx + d0 (ky + d1 kz)
+    __device__ __forceinline__ void split(int idx, int& kx, int& ky, int& kz) const {
+        const int q = fast ? (int)__umulhi((unsigned)idx, m0) : idx / d0;
+        kx = idx - q * d0;
+        kz = fast ? (int)__umulhi((unsigned)q, m1) : q / d1;
+        ky = q - kz * d1;
+    }
+    __device__ __forceinline__ int wrap(int a, int n) const { return fast ? wrap1(a, n) : wrapi(a, n); }
+};
 // minimum image of a displacement along an axis of length L
 __device__ __forceinline__ double mimg(double d, double L) {
     if (d > 0.5 * L) d -= L;

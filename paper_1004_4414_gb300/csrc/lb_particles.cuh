@@ -254,6 +254,9 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
+    // window coordinates by multiplies (the window lies within [-n, 2n) when
+    // the reach is below every box edge)
+    const WinDiv wd(span[0], span[1], total < 65536 && reach < (float)min(B.nx, min(B.ny, B.nz)));
     // FP32 decisions away from the surface, the FP64 test within a band of
     // it (the box constants are set on the host; FP64 is slow on this GPU)
     const float Rf2o = B.det_reach2, R2f = B.det_R2, band = B.det_band;
@@ -285,9 +288,9 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
         c.fz = mimgf((float)kz - off[2], Lf[2]);
         c.d2f = c.fx * c.fx + c.fy * c.fy + c.fz * c.fz;
         c.ok = c.d2f <= Rf2o;
-        c.gx = wrapi(lo[0] + kx, B.nx);
-        c.gy = wrapi(lo[1] + ky, B.ny);
-        c.gz = wrapi(lo[2] + kz, B.nz);
+        c.gx = wd.wrap(lo[0] + kx, B.nx);
+        c.gy = wd.wrap(lo[1] + ky, B.ny);
+        c.gz = wd.wrap(lo[2] + kz, B.nz);
         c.n = c.gx + B.nx * (c.gy + B.ny * c.gz);
         c.own = c.ok ? __ldg(B.owner + c.n) : OWN_WALL;
         return c;
@@ -391,7 +394,8 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
             for (int u = 0; u < SU; u++) {
                 const int idx = base + u * 32 + lane;
                 if (idx < total) {
-                    const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+                    int kx, ky, kz;
+                    wd.split(idx, kx, ky, kz);
                     c[u] = probe(kx, ky, kz);
                 } else {
                     c[u].ok = false;
@@ -416,8 +420,8 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
             int l0 = 0, h0 = -1, l1 = 0, h1 = -1;
             int ky = 0, kz = 0;
             if (row < nrows) {
-                ky = row % span[1];
-                kz = row / span[1];
+                int kx_;
+                wd.split(row * span[0], kx_, ky, kz);
                 const float fy = (float)ky - off[1], fz = (float)kz - off[2];
                 const float p2 = fy * fy + fz * fz;
                 const float o2 = r_out * r_out - p2;
@@ -833,15 +837,21 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
     // instead of one per candidate.  Larger windows, or a queue that would
     // overflow, take the two-pass scan below.
     const int wx = span[0] + 2, wy = span[1] + 2, wz = span[2] + 2;
+    // window (with its ring) coordinates by multiplies; the ring lies
+    // within [-n, 2n) when reach + 1 is below every box edge
+    const bool nodiv = total < 65536 && reach + 1.0f < (float)min(nx, min(ny, nz));
+    const WinDiv wd(span[0], span[1], nodiv);
     if (wx * wy * wz <= SHELL_CUBE) {
+        const WinDiv wc(wx, wy, nodiv);
         __shared__ uint8_t s_fl[SHELL_CUBE];
         __shared__ int s_q[SHELL_WARPS][SHELL_QW];
         __shared__ int s_qn[SHELL_WARPS];
         __shared__ int s_kc[SHELL_KQ][SHELL_WARPS];
         const int cube = wx * wy * wz;
         for (int i = threadIdx.x; i < cube; i += NT) {
-            const int a = i % wx, b = (i / wx) % wy, c = i / (wx * wy);
-            const int gx = wrapi(lo[0] - 1 + a, nx), gy = wrapi(lo[1] - 1 + b, ny), gz = wrapi(lo[2] - 1 + c, nz);
+            int a, b, c;
+            wc.split(i, a, b, c);
+            const int gx = wc.wrap(lo[0] - 1 + a, nx), gy = wc.wrap(lo[1] - 1 + b, ny), gz = wc.wrap(lo[2] - 1 + c, nz);
             s_fl[i] = __ldg(flags + gx + nx * (gy + ny * gz));
         }
         __syncthreads();
@@ -853,7 +863,8 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
             const int idx = b0 + lane;
             bool c = false;
             if (idx < end) {
-                const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
+                int kx, ky, kz;
+                wd.split(idx, kx, ky, kz);
                 const float dx = mimgf((float)kx - off[0], (float)nx), dy = mimgf((float)ky - off[1], (float)ny),
                             dz = mimgf((float)kz - off[2], (float)nz);
                 c = dx * dx + dy * dy + dz * dz <= lim && (s_fl[(kx + 1) + wx * ((ky + 1) + wy * (kz + 1))] & FL_SHELL);
@@ -889,8 +900,9 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
 #pragma unroll
                         for (int v = 1; v < SHELL_WARPS; v++) w += q >= qoff[v];
                         const int idx = s_q[w][q - qoff[w]];
-                        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-                        const int gx = wrapi(lo[0] + kx, nx), gy = wrapi(lo[1] + ky, ny), gz = wrapi(lo[2] + kz, nz);
+                        int kx, ky, kz;
+                        wd.split(idx, kx, ky, kz);
+                        const int gx = wd.wrap(lo[0] + kx, nx), gy = wd.wrap(lo[1] + ky, ny), gz = wd.wrap(lo[2] + kz, nz);
                         kidx[k] = idx;
                         tk[k] = __ldg(owner + gx + nx * (gy + ny * gz)) == p;
                     }
@@ -917,8 +929,9 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
                     if (tk[k]) {
                         // virtual density and list entry of the shell node
                         const int idx = kidx[k];
-                        const int kx = idx % span[0], ky = (idx / span[0]) % span[1], kz = idx / (span[0] * span[1]);
-                        const int gx = wrapi(lo[0] + kx, nx), gy = wrapi(lo[1] + ky, ny), gz = wrapi(lo[2] + kz, nz);
+                        int kx, ky, kz;
+                        wd.split(idx, kx, ky, kz);
+                        const int gx = wd.wrap(lo[0] + kx, nx), gy = wd.wrap(lo[1] + ky, ny), gz = wd.wrap(lo[2] + kz, nz);
                         const int n = gx + nx * (gy + ny * gz);
                         const int oxm = gx == 0 ? nx - 1 : -1, oxp = gx == nx - 1 ? -(nx - 1) : 1;
                         const int oym = gy == 0 ? (ny - 1) * nx : -nx, oyp = gy == ny - 1 ? -(ny - 1) * nx : nx;
