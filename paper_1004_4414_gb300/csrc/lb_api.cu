@@ -343,17 +343,22 @@ void fill_params(lb_handle* h) {
         B.nu = (1.0 / 3.0) * (0.5 * (p.tau[0] + p.tau[1]) - 0.5);
         B.c0 = p.mass_corr_c0;
         {
-            // FP32 positions near L are off by up to about L * 2^-24; the
-            // bands keep every FP32 remap decision at least twice that error
-            // away from the surface (the FP64 test decides within them)
+            // FP32 positions near L are off by up to about L * 2^-24 per
+            // axis (eps_pos / 2).  A squared distance d^2 <= (R + 1.5)^2
+            // from them is off by at most 2 |d| sqrt(3) eps_pos / 2 (under
+            // 11.3 eps_pos) plus the FP32 rounding of the window offsets and
+            // of the sum (under 1e-5 R^2).  The band keeps every FP32 remap
+            // decision more than twice that away from the surface (the FP64
+            // test decides within it); the neighbour bound qlim, whose
+            // distances carry the error of both centres, takes two bands.
             const double R = B.rb, R2 = B.radius * B.radius;
             const int nmax = p.nx > p.ny ? (p.nx > p.nz ? p.nx : p.nz) : (p.ny > p.nz ? p.ny : p.nz);
             const double eps_pos = 1.2e-7 * (double)nmax;
             B.det_reach2 = (float)((R + 1.5) * (R + 1.5));
             B.det_rb = (float)R;
             B.det_R2 = (float)R2;
-            B.det_band = (float)(0.02 + 2e-3 * R * R + 4.0 * (R + 1.5) * eps_pos);
-            B.det_qlim = (float)(R * R) + B.det_band;
+            B.det_band = (float)(1e-4 + 2e-5 * R * R + 4.0 * (R + 1.5) * eps_pos);
+            B.det_qlim = (float)(R * R) + 2.0f * B.det_band;
             // spheroid form F = R^2 (d.e)^2 + c^2 (|d|^2 - (d.e)^2) against
             // R^2 c^2: |grad F| <= 2 max(R^2, c^2) |d| within the window, so
             // the position error moves F by at most that times eps_pos; FP32
