@@ -343,9 +343,11 @@ struct Pop {
     // both components of a stored pair v of direction i
     __device__ __forceinline__ void cvt2(const S2 v, int i, R& a, R& b) const {
         if constexpr (P::dev) {
-            const float2 d = to_f2(v);
-            a = fmaf(wgt<float>(i), d.x, zr[0][is_axis(i) ? 0 : 1]);
-            b = fmaf(wgt<float>(i), d.y, zr[1][is_axis(i) ? 0 : 1]);
+            // both components in one packed FMA (the same rounding as two)
+            const int k = is_axis(i) ? 0 : 1;
+            const float2 r = __ffma2_rn(make_float2(wgt<float>(i), wgt<float>(i)), to_f2(v), make_float2(zr[0][k], zr[1][k]));
+            a = r.x;
+            b = r.y;
         } else {
             a = v.x;
             b = v.y;
@@ -354,12 +356,14 @@ struct Pop {
     // stores (a, b); qa, qb: the values the next load will see
     __device__ __forceinline__ void st2(S2* p, int i, R a, R b, R& qa, R& qb) const {
         if constexpr (P::dev) {
-            const S2 q = from_f2<S2>(fmaf(a, 1.0f / wgt<float>(i), -(float)ref[0]),
-                                     fmaf(b, 1.0f / wgt<float>(i), -(float)ref[1]));
+            const int k = is_axis(i) ? 0 : 1;
+            const float iw = 1.0f / wgt<float>(i);
+            const float2 e = __ffma2_rn(make_float2(a, b), make_float2(iw, iw), make_float2(-(float)ref[0], -(float)ref[1]));
+            const S2 q = from_f2<S2>(e.x, e.y);
             *p = q;
-            const float2 d = to_f2(q);
-            qa = fmaf(wgt<float>(i), d.x, zr[0][is_axis(i) ? 0 : 1]);
-            qb = fmaf(wgt<float>(i), d.y, zr[1][is_axis(i) ? 0 : 1]);
+            const float2 r = __ffma2_rn(make_float2(wgt<float>(i), wgt<float>(i)), to_f2(q), make_float2(zr[0][k], zr[1][k]));
+            qa = r.x;
+            qb = r.y;
         } else {
             *p = mk2<S2>(a, b);
             qa = a;
