@@ -360,16 +360,18 @@ void fill_params(lb_handle* h) {
             B.det_band = (float)(1e-4 + 2e-5 * R * R + 4.0 * (R + 1.5) * eps_pos);
             B.det_qlim = (float)(R * R) + 2.0f * B.det_band;
             // spheroid form F = R^2 (d.e)^2 + c^2 (|d|^2 - (d.e)^2) against
-            // R^2 c^2: |grad F| <= 2 max(R^2, c^2) |d| within the window, so
-            // the position error moves F by at most that times eps_pos; FP32
-            // rounding of F adds a few ulps of R^2 c^2
+            // R^2 c^2: |grad F| <= gmax = 2 max(R^2, c^2) |d| within the
+            // window, so the position error (sqrt(3) eps_pos / 2) moves F by
+            // under 0.87 gmax eps_pos; the FP32 axis and the rounding of F's
+            // terms (each below max(R^2, c^2) |d|^2 near the surface) add
+            // under 1e-3 + 1e-6 R^2 c^2.  The band is twice that.
             const double cRd = B.aspect * B.radius;
             const double gmax = 2.0 * (R2 > cRd * cRd ? R2 : cRd * cRd) * (R + 1.5);
             const float cR = (float)cRd;
             B.det_sR2 = (float)R2;
             B.det_sc2 = cR * cR;
             B.det_sR2c2 = B.det_sR2 * B.det_sc2;
-            B.det_sband = (float)(0.05 + 4.0 * gmax * eps_pos + 1e-6 * R2 * cRd * cRd);
+            B.det_sband = (float)(2e-3 + 2.0 * gmax * eps_pos + 2e-6 * R2 * cRd * cRd);
         }
     }
 }
