@@ -8,9 +8,13 @@ controller on the drift dM^c, so the drift must stay well below the
 uncorrected run's over the same steps.
 
 Setup: 64^3, 50:50 of total density 0.7, alpha = 0.15, R = 5, neutral
-wetting, particle density 3, seed 2; 4000 steps.  Measured on a GB300:
-C0 = 0 drifts by -2.9e-3 / -3.8e-3 (red / blue), C0 = 10 by
--1.1e-3 / -1.8e-3 (ratios 0.39 / 0.47)."""
+wetting, particle density 3, seed 2; 4000 steps.  The flow is chaotic and
+the kernels' floating-point reductions are unordered, so the drift of one
+run differs from the next by tens of percent.  Over five runs on GB300s
+C0 = 0 drifted by -2.3e-3 to -3.0e-3 (red) and -3.1e-3 to -3.8e-3 (blue);
+C0 = 10 kept 0.29 to 0.49 (red) and 0.38 to 0.67 (blue) of that, C0 = 20
+kept 0.16 to 0.31.  The test takes C0 = 20, whose reduction stays clear
+of the 60 % bound from run to run."""
 import numpy as np
 import pytest
 
@@ -39,8 +43,8 @@ def test_mass_correction_reduces_the_drift():
     from paper_1004_4414_gb300 import build
 
     build.build()
-    d0, d10 = drift(0.0), drift(10.0)
+    d0, d20 = drift(0.0), drift(20.0)
     # the uncorrected drift is a loss well above FP32 rounding (~1e-6)
     assert np.all(d0 < -1e-4), d0
-    # the controller keeps the same sign but at most 60 % of the magnitude
-    assert np.all(np.abs(d10) < 0.6 * np.abs(d0)), (d0, d10)
+    # the controller keeps at most 60 % of the magnitude
+    assert np.all(np.abs(d20) < 0.6 * np.abs(d0)), (d0, d20)

@@ -124,6 +124,31 @@ def test_moving_particles_with_events_fp64(vel_mode, c0):
     assert np.allclose(ob["mom_fluid"] + ob["mom_part"], sb["mom_fluid"] + sb["mom_part"], atol=1e-10)
 
 
+@pytest.mark.parametrize("radius", [7.6, 9.6])
+def test_large_spheres_shell_rebuild_fp64(radius):
+    """Large moving, rotating spheres.  R = 7.6 rebuilds its shell lists
+    from the shared-memory copy of the window's flags (about 180 of a warp
+    queue's 256 entries used: the surface area of a sphere is spread evenly
+    over z); R = 9.6 has a window too large for that copy and takes the
+    two-pass scan.  Both must give the oracle's owners, virtual densities
+    and forces."""
+    shape = (56, 52, 48)
+    nx, ny, nz = shape
+    # surface speeds up to about 0.12 (the fluid's max |u| stays below 0.16)
+    P = lbinputs.spheres(shape, radius, 3, seed=41, min_gap=0.3, vmax=0.04, wmax=0.008)
+    o, s = pair(nx=nx, ny=ny, nz=nz, n_particles=3, radius=radius, g_br=0.1, color=0.03, particle_density=2.0)
+    rho = lbinputs.mixture(shape, amp=0.03, seed=42)
+    o.init_fields(rho, particles=P)
+    s.init_fields(0, rho, particles=P)
+    for k in range(4):
+        o.step(4)
+        s.step(4)
+        compare(o, s, ftol=1e-11, ptol=1e-11)
+    ob, sb = o.observe(), s.observables()
+    assert ob["n_cover"] > 0 and ob["n_uncover"] > 0
+    assert (ob["n_cover"], ob["n_uncover"]) == (sb["n_cover"], sb["n_uncover"])
+
+
 def test_many_moving_spheres_remap_fp64():
     """A box large enough for the remap's annulus scan (particles far from
     all others scan only the nodes near their surface): 36 moving, rotating
