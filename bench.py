@@ -17,7 +17,8 @@ and 64-box batch legs with the same fields (the batch also with
 batch_vs_sequential).  Two roofline fractions are reported per leg:
   roofline.frac       the fused stream-collide kernel alone: its algorithmic
                       bytes per launch over its CUDA-event launch time, against
-                      the measured HBM copy bandwidth;
+                      the measured HBM copy bandwidth (the 6800 GB/s
+                      fallback when no measurement is available);
   roofline.step_frac  the whole step: MLUPS over the roofline MLUPS of the
                       ideal byte count per node (2 components x 19
                       populations read and written: 304 B in FP32, 152 B in
@@ -30,6 +31,7 @@ Workloads (seeded, synthetic; the paper's runs are synthetic as well):
   c256  256^3, fluid ratio 60:40 of total density 0.7, alpha = 0.20, R = 5,
         contact angle 77 deg (colour -0.0294), g = 0.08 (default)
   c256p the c256 parameters on a 128^3 box (small case for profiler captures)
+  c256s 256^3 with 5007 prolate spheroids (semi-axes 4, 4, 6), alpha = 0.12
   c128  128^3, 50:50, alpha = 0.15, R = 5, 90 deg
   c512  512^3, 50:50, alpha = 0.20, R = 5, 90 deg
   c32   32^3, 0.7 / 0.7, 16 spheres R = 4 (parity configuration)
