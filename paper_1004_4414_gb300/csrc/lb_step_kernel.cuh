@@ -12,7 +12,7 @@
 //
 // GB300 design:
 //   * Populations stay in place with the AA pattern.  Even steps: a node
-//     reads its own 19 slots and writes f*_j to slot opp(j) of itself.  Odd
+//     reads its own 18 slots and writes f*_j to slot opp(j) of itself.  Odd
 //     steps: it reads f_i from slot opp(i) of x - c_i and writes f*_j to slot
 //     j of x + c_j.  A population whose stream target y = x + c_j is solid
 //     belongs, reflected, in the slot the next step reads it from: slot j
@@ -24,6 +24,10 @@
 //   * The two components of a direction and node form one pair in memory
 //     (8 bytes in FP32, 4 in 16-bit storage), so one load or store moves
 //     both: a warp moves 32 consecutive pairs of one direction per access.
+//     Every operation that is the same for both components is one packed
+//     FP32 instruction on the pair (FADD2 / FMUL2 / FFMA2).  16-bit storage
+//     stages the next plane's pairs in shared memory with cp.async while the
+//     current plane is computed (StepStage below).
 //   * Only the 18 moving populations are stored.  A node's rho^c is the
 //     density field of the current step (the window fetches it for Psi
 //     anyway), and its rest population f_0 = rho^c - sum_{i>=1} f_i stays at

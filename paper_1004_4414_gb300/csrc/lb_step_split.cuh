@@ -12,7 +12,7 @@
 // a warp hold the red component and lanes 16-31 the blue component of the
 // same 16 nodes of an x row.  Inside a node the components meet only in
 // u', which needs the partner's density and momentum: four shuffles.  A
-// thread holds 19 populations instead of 38, so it needs about half the
+// thread holds 18 populations instead of 36, so it needs about half the
 // registers and an SM keeps twice the warps resident to hide load and store
 // latency.  Tiles are 16 nodes wide.  The two components of a direction and
 // node are one pair in memory, so a warp's access covers the 16 pairs of its
