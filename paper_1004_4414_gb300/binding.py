@@ -285,9 +285,9 @@ class Simulation:
                     n_uncover=o.n_uncover, n_fluid=o.n_fluid, n_solid=o.n_solid, error=o.error,
                     n_particles=o.n_particles, L=np.array(o.L[:]), coverage=o.coverage)
 
-    def export_state(self, box=0, f=True, f_out=None):
-        """Canonical state; f_out: optional C-contiguous float64 array
-        (2, 19, N) to fill (e.g. pinned host memory)."""
+    def export_state(self, box=0, f=True, f_out=None, owner_out=None):
+        """Canonical state; f_out / owner_out: optional C-contiguous float64
+        (2, 19, N) / int32 (N,) arrays to fill (e.g. pinned host memory)."""
         N = self.n_nodes[box]
         if f_out is not None:
             if f_out.dtype != np.float64 or f_out.size != 2 * 19 * N or not f_out.flags.c_contiguous:
@@ -295,7 +295,12 @@ class Simulation:
             fa = f_out
         else:
             fa = np.zeros((2, 19, N)) if f else None
-        owner = np.zeros(N, np.int32)
+        if owner_out is not None:
+            if owner_out.dtype != np.int32 or owner_out.size != N or not owner_out.flags.c_contiguous:
+                raise ValueError("owner_out must be a C-contiguous int32 array of N values")
+            owner = owner_out
+        else:
+            owner = np.zeros(N, np.int32)
         parts = np.zeros((max(self.n_particles[box], 1), 9))
         meta = np.zeros(4)
         _ck(load_library().lb_export_state(self._h, box, None if fa is None else _dp(fa), _ip(owner), _dp(parts),
