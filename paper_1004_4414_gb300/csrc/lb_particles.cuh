@@ -88,6 +88,13 @@ static __global__ void k_cell_fill(const BoxDev* __restrict__ boxes, Shared sh, 
     sh.cell_list[pos] = p;
 }
 
+// The particle a block (or warp) of a per-particle kernel takes: the i-th
+// entry of the cell-sorted list, so that the blocks resident at one time
+// work on neighbouring particles and share their cached fluid lines (a
+// permutation of all particles from the first step on: the lists are built
+// in every step after an init or import).
+__device__ __forceinline__ int particle_at(const Shared& sh, int i) { return sh.cell_list[i]; }
+
 // Neighbour list of p: every particle whose centre lies within nl_reach (a
 // node owned before the move lies within R + |U| <= R + 1 of the new
 // centre, lubrication acts below a gap of lub_cut, NL_SKIN of slack for the
@@ -203,6 +210,7 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
     __shared__ int s_nid[DETECT_WARPS][NL_MAX];
     __shared__ int s_cl[DETECT_WARPS][NL_MAX];  // entries of neighbours within 2R (+ slack)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // in index order: the cell-sorted order measured 3 % slower here
     const int p = blockIdx.x;
     if (p >= NP) return;  // the whole block leaves together
     const int b = sh.pbox[p];
@@ -749,8 +757,8 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
     __shared__ int s_cnt[SHELL_WARPS];
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x;
-    if (p >= NP) return;  // the whole block leaves together
+    if ((int)blockIdx.x >= NP) return;  // the whole block leaves together
+    const int p = particle_at(sh, blockIdx.x);
     const BoxDev& B = boxes[sh.pbox[p]];
     const PartStateF pf = sh.partf[p];
     R2* __restrict__ r2 = rpair<R>(B.rho[rc]);
@@ -1089,7 +1097,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NRED = 8 + (IMPL ? NZ : 0);
     __shared__ R s_red[COUPLE_THREADS / 32][NRED];
-    const int p = blockIdx.x;
+    const int p = particle_at(sh, blockIdx.x);
     const BoxDev& B = boxes[sh.pbox[p]];
     const Pop<P> pop(B);
     const auto& ps = part_ptr<R>(sh)[p];
@@ -1291,7 +1299,7 @@ static __global__ void __launch_bounds__(COUPLE_THREADS)
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ R s_red[COUPLE_THREADS / 32][2];
-    const int p = blockIdx.x;
+    const int p = particle_at(sh, blockIdx.x);
     const BoxDev& B = boxes[sh.pbox[p]];
     if (!B.implicit || B.fixed) return;  // the whole block leaves together
     const Pop<P> pop(B);
@@ -1436,8 +1444,8 @@ constexpr int MD_WARPS = 4;
 static __global__ void __launch_bounds__(32 * MD_WARPS) k_md_forces(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * MD_WARPS + wib;
-    if (p >= NP) return;  // the whole warp leaves together
+    if ((int)(blockIdx.x * MD_WARPS + wib) >= NP) return;  // the whole warp leaves together
+    const int p = particle_at(sh, blockIdx.x * MD_WARPS + wib);
     const BoxDev& B = boxes[sh.pbox[p]];
     double* fp = &sh.force[(size_t)p * 6];
     const double mine = lane < 6 ? fp[lane] : 0.0;
