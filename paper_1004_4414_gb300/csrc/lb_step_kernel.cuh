@@ -164,11 +164,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // T1: every box has tau^r = tau^b = 1, where BGK gives f* = f^eq: the
 // loaded populations then only feed the moments and need not stay live.
-// Resident CTAs per SM: three for the FP32 / 16-bit tau = 1 kernel (80
-// registers, no spills: 24 warps hide the population loads), else two.
+// Resident CTAs per SM for the FP32 / 16-bit tau = 1 kernel: five of 128
+// threads at TY = 4 (96 registers, 20 warps), three of 256 at TY = 8 (80
+// registers, 24 warps); measured at 256^3, five small CTAs beat three and
+// six (and four or more at TY = 8, which spills).  Otherwise two.
 template <class P, bool T1>
 constexpr int step_min_blocks(int ty) {
-    return ty <= 8 ? ((T1 && sizeof(typename P::real) == 4) ? 3 : 2) : 1;
+    return ty > 8 ? 1 : (!(T1 && sizeof(typename P::real) == 4) ? 2 : (ty == 4 ? 5 : 3));
 }
 template <class P, int PAR, int TY, bool T1, bool BB>
 static __global__ void __launch_bounds__(32 * TY, step_min_blocks<P, T1>(TY))
