@@ -1088,9 +1088,10 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
 constexpr int COUPLE_THREADS = 128;
 constexpr int NZ = 21;  // entries of the symmetric 6 x 6 drag tensor
 // five resident blocks per SM without the implicit update's drag tensor (96
-// registers, 16 B of spills): 2 % faster than the compiler's 124 registers
+// registers, 16 B of spills): 2 % faster than the compiler's 124 registers;
+// three with it (154 registers)
 template <class P, bool IMPL>
-static __global__ void __launch_bounds__(COUPLE_THREADS, IMPL ? 1 : 5)
+static __global__ void __launch_bounds__(COUPLE_THREADS, IMPL ? 3 : 5)
     k_couple(const BoxDev* __restrict__ boxes, Shared sh, int rc, int rn, int mslot, int par, int reflect) {
     using R = typename P::real;
     using S2 = typename P::st2;
