@@ -424,7 +424,8 @@ __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >
 // m = floor((2^32 - 1) / d) + 1: m exceeds 2^32 / d by at most 1, which adds
 // less than 2^-16 to idx / d, and the fraction of idx / d is at most
 // 1 - 1/d < 1 - 2^-16.  When every window coordinate lies in [-n, 2n) the
-// periodic wrap is a compare.  (fast: both hold; otherwise the division.)
+// periodic wrap is a compare.  (fast: the caller has checked both;
+// otherwise the division and the modulo, valid for any coordinate.)
 struct WinDiv {
     int d0, d1;
     unsigned m0, m1;

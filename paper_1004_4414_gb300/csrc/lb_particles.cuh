@@ -262,9 +262,13 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
         if (span[a] > dims[a]) span[a] = dims[a];
     }
     const int total = span[0] * span[1] * span[2];
-    // window coordinates by multiplies (the window lies within [-n, 2n) when
-    // the reach is below every box edge)
-    const WinDiv wd(span[0], span[1], total < 65536 && reach < (float)min(B.nx, min(B.ny, B.nz)));
+    // window coordinates by multiplies when every coordinate of the window
+    // lies within [-n, 2n) (always for a centre in the box and a reach below
+    // the box edge; a centre that has run away, in an unstable state, takes
+    // the division, whose wrap is valid for any coordinate)
+    bool near = true;
+    for (int a = 0; a < 3; a++) near = near && lo[a] >= -dims[a] && lo[a] <= 2 * dims[a] - span[a];
+    const WinDiv wd(span[0], span[1], total < 65536 && near);
     // FP32 decisions away from the surface, the FP64 test within a band of
     // it (the box constants are set on the host; FP64 is slow on this GPU)
     const float Rf2o = B.det_reach2, R2f = B.det_R2, band = B.det_band;
@@ -845,9 +849,11 @@ static __global__ void __launch_bounds__(32 * SHELL_WARPS) k_shell_density(const
     // instead of one per candidate.  Larger windows, or a queue that would
     // overflow, take the two-pass scan below.
     const int wx = span[0] + 2, wy = span[1] + 2, wz = span[2] + 2;
-    // window (with its ring) coordinates by multiplies; the ring lies
-    // within [-n, 2n) when reach + 1 is below every box edge
-    const bool nodiv = total < 65536 && reach + 1.0f < (float)min(nx, min(ny, nz));
+    // window (with its ring) coordinates by multiplies when they all lie
+    // within [-n, 2n) (a centre that has run away takes the division)
+    bool near = true;
+    for (int a = 0; a < 3; a++) near = near && lo[a] - 1 >= -dims[a] && lo[a] + 1 <= 2 * dims[a] - span[a];
+    const bool nodiv = total < 65536 && near;
     const WinDiv wd(span[0], span[1], nodiv);
     if (wx * wy * wz <= SHELL_CUBE) {
         const WinDiv wc(wx, wy, nodiv);
