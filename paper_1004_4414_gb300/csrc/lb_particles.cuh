@@ -357,9 +357,6 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
         }
         node = c.n;
     };
-    auto handle = [&](int kx, int ky, int kz, bool& have, int& node, int& ev_old, int& ev_new) {
-        decide(probe(kx, ky, kz), have, node, ev_old, ev_new);
-    };
     // the events of 32 candidates, appended to the event list
     auto emit = [&](bool have, int node, int ev_old, int ev_new) {
         const unsigned m = __ballot_sync(0xffffffffu, have);
@@ -397,8 +394,10 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
     bool fits = true;  // the window covers less than half of each axis (no wrap onto itself)
     for (int a = 0; a < 3; a++) fits = fits && 2 * span[a] < dims[a] && span[a] < 1024;
     const bool fast = sph && fits && ncl == 0 && sh.exact[p] && delta < 0.5f;
-    if (!fast) {
-        // two candidates per lane per round, probed before either is decided
+    if (!fits) {
+        // a window that wraps onto itself (a box edge below twice the
+        // window): every window node, two candidates per lane per round,
+        // probed before either is decided
         constexpr int SU = 2;
         for (int base = wib * 32 * SU; base < total; base += 32 * SU * DETECT_WARPS) {
             Cand c[SU];
@@ -422,9 +421,12 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
             }
         }
     } else {
-        // rows (ky, kz) of the window, one per lane; the annulus crosses a
-        // row in at most two x intervals, whose nodes go to a per-warp queue
-        const float r_out = R + delta + 0.1f, r_in = fmaxf(R - delta - 0.1f, 0.0f);
+        // rows (ky, kz) of the window, one per lane; the shell to scan (the
+        // annulus of the fast path, else the ball of radius reach, with 0.01
+        // of slack over the FP32 reach test) crosses a row in at most two x
+        // intervals, whose nodes go to a per-warp queue
+        const float r_out = fast ? R + delta + 0.1f : reach + 0.01f;
+        const float r_in = fast ? fmaxf(R - delta - 0.1f, 0.0f) : 0.0f;
         int* q = s_queue[wib];
         const int nrows = span[1] * span[2];
         for (int rb = wib * 32; rb < nrows; rb += 32 * DETECT_WARPS) {
@@ -473,14 +475,26 @@ static __global__ void __launch_bounds__(32 * DETECT_WARPS, 6) k_remap_detect(co
                 }
                 __syncwarp();
                 const int nq = min(DETECT_QUEUE, tot - done);
-                for (int base = 0; base < nq; base += 32) {
-                    int ev_old = 0, ev_new = 0, node = 0;
-                    bool have = false;
-                    if (base + lane < nq) {
-                        const int e = q[base + lane];
-                        handle(e & 1023, (e >> 10) & 1023, e >> 20, have, node, ev_old, ev_new);
+                // two entries per lane per round, probed before either is decided
+                for (int base = 0; base < nq; base += 64) {
+                    Cand c[2];
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int j = base + u * 32 + lane;
+                        if (j < nq) {
+                            const int e = q[j];
+                            c[u] = probe(e & 1023, (e >> 10) & 1023, e >> 20);
+                        } else {
+                            c[u].ok = false;
+                        }
                     }
-                    emit(have, node, ev_old, ev_new);
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        int ev_old = 0, ev_new = 0, node = 0;
+                        bool have = false;
+                        decide(c[u], have, node, ev_old, ev_new);
+                        emit(have, node, ev_old, ev_new);
+                    }
                 }
                 __syncwarp();
             }
