@@ -35,7 +35,9 @@
  *   - Host pointers are plain host memory (pageable or pinned); the library
  *     copies what it needs before the call returns unless stated otherwise.
  *   - A handle is not thread-safe; one host thread drives it at a time.
- *   - All device work goes to the CUDA stream given to lb_create.
+ *   - All device work is ordered on the CUDA stream given to lb_create: the
+ *     handle's own second streams (state copies, the MD pair forces) fork
+ *     from it and join it again within the same call or step.
  */
 #ifndef LBPART_H
 #define LBPART_H
@@ -247,7 +249,9 @@ int lb_kernel_time(lb_handle* h, double* ms_fused, int64_t* launches_fused, int6
  *   0 cell and neighbour lists, 1 remap detection, 2 cover / uncover
  *   (marks, refills, shell flags), 3 shell virtual densities, 4 fused
  *   stream-collide kernel, 5 coupling pass (links, momentum exchange,
- *   Shan-Chen force on the particles), 6 MD.
+ *   Shan-Chen force on the particles), 6 MD velocity and position update.
+ * The MD pair forces run on a second stream of the handle beside phases
+ * 1-5 and are counted in none of them.
  * Each phase also carries its share of launch gaps. */
 #define LB_NPHASES 7
 int lb_phase_times(lb_handle* h, double* ms, int32_t n);

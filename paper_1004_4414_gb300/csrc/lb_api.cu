@@ -189,6 +189,11 @@ struct lb_handle {
     // ev_c[b] = copy of staging half b done
     cudaStream_t xstream = nullptr;
     cudaEvent_t ev_k[2] = {nullptr, nullptr}, ev_c[2] = {nullptr, nullptr};
+    // the pair forces of a step (k_md_pair) run on mdstream beside the
+    // remap, shell, fused and coupling kernels: forked after the neighbour
+    // list (ev_fork), joined before the velocity update (ev_join)
+    cudaStream_t mdstream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<int> graph_walls;  // the per-box wall flags the graphs were captured with
 };
 
@@ -255,6 +260,7 @@ size_t layout(lb_handle* h, const lb_params* bx, int nb, char* base) {
     sh.partf = cv.take<PartStateF>(NPa);
     sh.force = cv.take<double>((size_t)NPa * 6);
     sh.force_last = cv.take<double>((size_t)NPa * 6);
+    sh.fpair = cv.take<double>((size_t)NPa * 3);
     sh.color = cv.take<double>(NPa);
     sh.pbox = cv.take<int>(NPa);
     sh.cell_count = cv.take<int>(cells);
@@ -450,6 +456,12 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         k_cell_scan<<<h->nb, 1024, 0, st>>>(h->d_boxes, h->sh, par);
         k_cell_fill<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP, par);
         k_nlist<<<(NP + NLIST_WARPS - 1) / NLIST_WARPS, 32 * NLIST_WARPS, 0, st>>>(h->d_boxes, h->sh, NP, par);
+        // the pair forces read only the positions, velocities and
+        // neighbour lists, which nothing changes before the velocity update
+        CK(cudaEventRecord(h->ev_fork, st));
+        CK(cudaStreamWaitEvent(h->mdstream, h->ev_fork, 0));
+        k_md_pair<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, h->mdstream>>>(h->d_boxes, h->sh, NP);
+        CK(cudaEventRecord(h->ev_join, h->mdstream));
         if (mark(1) != LB_OK) return LB_ECUDA;
         k_remap_detect<<<NP, 32 * DETECT_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
         if (mark(2) != LB_OK) return LB_ECUDA;
@@ -459,7 +471,7 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         CK(h->ops->remap_finish(st, h->d_boxes, h->sh, rc));
         if (mark(3) != LB_OK) return LB_ECUDA;
         CK(h->ops->shell_density(st, h->d_boxes, h->sh, rc, NP));
-        launches += 9;
+        launches += 10;
     }
     for (int b = 0; b < h->nb; b++)
         if (h->has_walls[b]) {
@@ -477,16 +489,16 @@ int enqueue_step(lb_handle* h, int64_t t, bool prof) {
         for (const auto& p : h->params) impl |= p.implicit_update;
         CK(h->ops->couple(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, impl, NP));
         if (mark(6) != LB_OK) return LB_ECUDA;
-        k_md_forces<<<(NP + MD_WARPS - 1) / MD_WARPS, 32 * MD_WARPS, 0, st>>>(h->d_boxes, h->sh, NP);
+        CK(cudaStreamWaitEvent(st, h->ev_join, 0));
         if (impl) {
             // implicit update: velocities, the fluid's share on the links, positions
             k_md_solve<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP);
             CK(h->ops->couple_correct(st, h->d_boxes, h->sh, rc, rn, mnext, par, h->reflect, NP));
             k_md_move<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP, par);
-            launches += 5;
+            launches += 4;
         } else {
             k_md_integrate<<<pg, 256, 0, st>>>(h->d_boxes, h->sh, NP, par);
-            launches += 3;
+            launches += 2;
         }
     }
     if (mark(LB_NPHASES) != LB_OK) return LB_ECUDA;  // end of the step
@@ -838,7 +850,10 @@ int lb_create(const lb_params* boxes, int32_t n_boxes, void* d_workspace, size_t
         cudaEventCreateWithFlags(&h->ev_k[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_k[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_c[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_c[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_c[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->mdstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         lb_destroy(h);
         return LB_ECUDA;
     }
@@ -1313,6 +1328,12 @@ void lb_destroy(lb_handle* h) {
         if (h->ev_k[b]) cudaEventDestroy(h->ev_k[b]);
         if (h->ev_c[b]) cudaEventDestroy(h->ev_c[b]);
     }
+    if (h->mdstream) {
+        cudaStreamSynchronize(h->mdstream);
+        cudaStreamDestroy(h->mdstream);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->h_err) cudaFreeHost(h->h_err);
     delete h;
 }

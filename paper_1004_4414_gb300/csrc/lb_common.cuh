@@ -111,6 +111,7 @@ struct Shared {
     PartStateF* partf;          // [NP] FP32 copy of part, refreshed after every MD update
     double* force;              // [NP][6] F, T accumulators
     double* force_last;         // [NP][6] coupling forces of the last step
+    double* fpair;              // [NP][3] pair forces (Hertz contact, lubrication) of this step
     double* color;              // [NP]
     int* pbox;                  // [NP] box of each particle
     int* cell_count;            // [total cells]

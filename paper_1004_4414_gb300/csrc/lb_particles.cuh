@@ -1458,21 +1458,19 @@ static __global__ void k_part_to_float(Shared sh, int p0, int n) {
     sh.partf[p0 + k] = pf;
 }
 
-// coupling forces of the step are saved, then the pair forces are added
-// Pair forces (Hertz contact and lubrication) on p, added to the fluid
-// force; the fluid part is kept in force_last first.  One warp per particle,
-// lane k takes the k-th entry of the (sorted) neighbour list; a fixed
-// butterfly sums the lanes, so the result does not depend on timing.
+// Pair forces (Hertz contact and lubrication) on p into fpair; the velocity
+// update adds them to the fluid's force.  One warp per particle, lane k
+// takes the k-th entry of the (sorted) neighbour list; a fixed butterfly
+// sums the lanes, so the result does not depend on timing.  Reads only the
+// positions, velocities and neighbour lists, so it runs beside the fluid
+// kernels of the step.
 constexpr int MD_WARPS = 4;
-static __global__ void __launch_bounds__(32 * MD_WARPS) k_md_forces(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
+static __global__ void __launch_bounds__(32 * MD_WARPS) k_md_pair(const BoxDev* __restrict__ boxes, Shared sh, int NP) {
     const unsigned FULL = 0xffffffffu;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if ((int)(blockIdx.x * MD_WARPS + wib) >= NP) return;  // the whole warp leaves together
     const int p = particle_at(sh, blockIdx.x * MD_WARPS + wib);
     const BoxDev& B = boxes[sh.pbox[p]];
-    double* fp = &sh.force[(size_t)p * 6];
-    const double mine = lane < 6 ? fp[lane] : 0.0;
-    if (lane < 6) sh.force_last[(size_t)p * 6 + lane] = mine;
     double F[3] = {0.0, 0.0, 0.0};
     const int nn = sh.nlist_n[p];
     if (lane < nn) {
@@ -1490,7 +1488,18 @@ static __global__ void __launch_bounds__(32 * MD_WARPS) k_md_forces(const BoxDev
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
         for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(FULL, F[a], off);
-    if (lane < 3) fp[lane] = mine + F[lane];
+    if (lane < 3) sh.fpair[(size_t)p * 3 + lane] = F[lane];
+}
+
+// The force and torque on p of this step: the fluid's part (k_couple and
+// the remap events) is kept in force_last, then the pair forces are added.
+__device__ __forceinline__ void total_force(const Shared& sh, int p, double f[6]) {
+    const double* fp = &sh.force[(size_t)p * 6];
+    for (int a = 0; a < 6; a++) {
+        f[a] = fp[a];
+        sh.force_last[(size_t)p * 6 + a] = f[a];
+    }
+    for (int a = 0; a < 3; a++) f[a] += sh.fpair[(size_t)p * 3 + a];
 }
 
 // Rotation of a spheroid with torque T: L = I(e) omega, L += T, the axis
@@ -1570,6 +1579,8 @@ static __global__ void k_md_solve(const BoxDev* __restrict__ boxes, Shared sh, i
     if (p >= NP) return;
     const BoxDev& B = boxes[sh.pbox[p]];
     double* fp = &sh.force[(size_t)p * 6];
+    double ft[6];
+    total_force(sh, p, ft);
     PartState ps = sh.part[p];
     double dv[6] = {0, 0, 0, 0, 0, 0};
     if (!B.fixed) {
@@ -1585,8 +1596,8 @@ static __global__ void k_md_solve(const BoxDev* __restrict__ boxes, Shared sh, i
             for (int u = 0; u < 3; u++) {
                 A[7 * u] += B.mass;
                 A[7 * (u + 3)] += B.inertia;
-                b[u] = fp[u];
-                b[u + 3] = fp[3 + u];
+                b[u] = ft[u];
+                b[u + 3] = ft[3 + u];
             }
             solve6(A, b, dv);
             for (int a = 0; a < 3; a++) {
@@ -1594,10 +1605,10 @@ static __global__ void k_md_solve(const BoxDev* __restrict__ boxes, Shared sh, i
                 ps.W[a] += dv[3 + a];
             }
         } else {
-            if (B.aspect != 1.0) rotate_spheroid(B, ps.W, ps.E, fp + 3);
+            if (B.aspect != 1.0) rotate_spheroid(B, ps.W, ps.E, ft + 3);
             for (int a = 0; a < 3; a++) {
-                ps.U[a] += fp[a] / B.mass;
-                if (B.aspect == 1.0) ps.W[a] += fp[3 + a] / B.inertia;
+                ps.U[a] += ft[a] / B.mass;
+                if (B.aspect == 1.0) ps.W[a] += ft[3 + a] / B.inertia;
             }
         }
         if (!(ps.U[0] * ps.U[0] + ps.U[1] * ps.U[1] + ps.U[2] * ps.U[2] < 1.0)) set_err(sh.err, ERR_FAST_PARTICLE);
@@ -1638,13 +1649,15 @@ static __global__ void k_md_integrate(const BoxDev* __restrict__ boxes, Shared s
     if (p >= NP) return;
     const BoxDev& B = boxes[sh.pbox[p]];
     double* fp = &sh.force[(size_t)p * 6];
+    double ft[6];
+    total_force(sh, p, ft);
     PartState ps = sh.part[p];
     if (!B.fixed) {
         const double L[3] = {(double)B.nx, (double)B.ny, (double)B.nz};
-        if (B.aspect != 1.0) rotate_spheroid(B, ps.W, ps.E, fp + 3);
+        if (B.aspect != 1.0) rotate_spheroid(B, ps.W, ps.E, ft + 3);
         for (int a = 0; a < 3; a++) {
-            ps.U[a] += fp[a] / B.mass;
-            if (B.aspect == 1.0) ps.W[a] += fp[3 + a] / B.inertia;
+            ps.U[a] += ft[a] / B.mass;
+            if (B.aspect == 1.0) ps.W[a] += ft[3 + a] / B.inertia;
             double xn = ps.X[a] + ps.U[a];
             xn -= L[a] * floor(xn / L[a]);
             if (xn >= L[a]) xn -= L[a];
