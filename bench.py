@@ -25,7 +25,13 @@ batch_vs_sequential).  Two roofline fractions are reported per leg:
                       16-bit storage) at the measured HBM bandwidth.
 The timed steps replay the CUDA graphs exactly as lb_step does; the fused
 kernel's launch time comes from a separate pass of the same steps with
-per-launch CUDA events.
+per-launch CUDA events.  End to end through the C ABI with host buffers:
+  e2e             import of every box's storage-format state from pinned
+                  host memory (lb_import_state_native), the K steps, export
+                  into pinned host memory (lb_export_state_native);
+  e2e_fp64_state  the same with the FP64 canonical state (lb_import_state /
+                  lb_export_state): twice the population bytes of FP32
+                  storage, four times those of 16-bit storage.
 
 Workloads (seeded, synthetic; the paper's runs are synthetic as well):
   c256  256^3, fluid ratio 60:40 of total density 0.7, alpha = 0.20, R = 5,
@@ -355,10 +361,40 @@ def run_ours(args, rank, world, device):
     t1 = time.perf_counter()
     barrier()
     e2e_value, _ = job_throughput(nodes * args.steps, t1 - t0, world, device)
+    e2e_fp64 = {"value": e2e_value, "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": h2d / args.steps,
+                "what": "lb_import_state of every box (FP64 canonical state) from pinned host memory + lb_step(K) + "
+                        "lb_export_state of every box into pinned host memory"}
+
+    # ---- the same through the storage-format state (the checkpoint a run
+    # restarts from: the device's own population bytes, no FP64 conversion).
+    # Its bytes follow the step's parity, so the input is exported at the
+    # current step, where the import puts it.
+    nstates_in, nouts, nh2d = [], [], 0
+    for b in range(sim.nb):
+        st = sim.export_state_native(b)
+        nstates_in.append(dict(st, state=pinned_like(st["state"]), owner=pinned_like(st["owner"])))
+        nouts.append((pinned_like(st["state"]), pinned_like(st["owner"])))
+        nh2d += st["state"].nbytes + st["owner"].nbytes + st["particles"].nbytes
+    for b in range(sim.nb):
+        sim.import_state_native(b, nstates_in[b])
+        sim.export_state_native(b, state_out=nouts[b][0], owner_out=nouts[b][1])
+    barrier()
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for b in range(sim.nb):
+        sim.import_state_native(b, nstates_in[b])
+    sim.step(args.steps)
+    sim.sync()
+    for b in range(sim.nb):
+        sim.export_state_native(b, state_out=nouts[b][0], owner_out=nouts[b][1])
+    t1 = time.perf_counter()
+    barrier()
+    e2e_value, _ = job_throughput(nodes * args.steps, t1 - t0, world, device)
     e2e = {"value": e2e_value, "unit": "MLUPS",
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": h2d / args.steps,
-           "what": "lb_import_state of every box from pinned host memory + lb_step(K) + "
-                   "lb_export_state of every box into pinned host memory"}
+           "h2d_bytes_per_step": nh2d / args.steps, "d2h_bytes_per_step": nh2d / args.steps,
+           "what": "lb_import_state_native of every box (storage-format state) from pinned host memory + "
+                   "lb_step(K) + lb_export_state_native of every box into pinned host memory"}
     ob = sim.observables(0)
     n_fluid = sum(sim.observables(b)["n_fluid"] for b in range(sim.nb))
     seq = None
@@ -367,7 +403,8 @@ def run_ours(args, rank, world, device):
         seq = {"sequential_mlups": seq_value, "batched_mlups": value, "ratio": value / seq_value,
                "sequential_ms": seq_ms, "what": "the same boxes and states, one handle per box, run one after another"}
     return dict(value=value, ms=ms_max, fused_ms=avg_ms, fused_n=fused_n, bytes=bytes_launch, achieved=achieved,
-                peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, launches=launches, nodes=nodes, phases=phases,
+                peak=peak, peak_kind=peak_kind, clocks=clocks, e2e=e2e, e2e_fp64=e2e_fp64, launches=launches,
+                nodes=nodes, phases=phases,
                 n_particles=sum(sim.n_particles), error=ob["error"], n_fluid=n_fluid, tiling=tiling, seq=seq)
 
 
@@ -489,6 +526,7 @@ def leg_fields(args, r):
         "fluid_mlups": r["value"] * r["n_fluid"] / r["nodes"],
         "phases_ms_per_step": r["phases"],
         "e2e": r["e2e"],
+        "e2e_fp64_state": r["e2e_fp64"],
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],
         "batch_vs_sequential": r["seq"],

@@ -197,6 +197,35 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
 int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* owner,
                     const double* particles, const double* meta);
 
+/* State of one box in the handle's storage format, for checkpoints that
+ * skip the conversion to FP64 and move half (FP32 storage) or a quarter
+ * (16-bit storage) of lb_export_state's population bytes.  state (host,
+ * lb_state_native_bytes bytes): the 18 stored population pairs of every
+ * node exactly as the device holds them for the current step (in-place
+ * streaming order, so the bytes depend on the step's parity), then the
+ * density field rho^c of the current step.  owner and particles as in
+ * lb_export_state (either may be NULL); meta[LB_NATIVE_META]: step, the two
+ * initial component masses, n_particles, the storage type (lb_params
+ * precision), the node count, and the fluid mass of each component that
+ * the current step starts from.  LB_EINVAL before an init or for a wrong
+ * byte count.  Pinned host buffers give the full host-link rate.
+ * Synchronises the stream. */
+#define LB_NATIVE_META 8
+int lb_state_native_bytes(lb_handle* h, int32_t box, size_t* bytes);
+int lb_export_state_native(lb_handle* h, int32_t box, void* state, size_t bytes, int32_t* owner,
+                           double* particles, double* meta);
+
+/* Replace the state of one box from lb_export_state_native of a box with
+ * the same parameters (state, owner, particles and meta are required): the
+ * bytes are copied back as they are.  The particle shell, cell and
+ * neighbour lists are rebuilt, so stepping on agrees with the exporting run
+ * up to the summation order of the particle forces.
+ * LB_EINVAL for a byte count, storage type or node count that differs from
+ * this box's, and, before anything of the box changes, for an owner entry
+ * outside [-2, n_particles).  Synchronous. */
+int lb_import_state_native(lb_handle* h, int32_t box, const void* state, size_t bytes,
+                           const int32_t* owner, const double* particles, const double* meta);
+
 /* Densities rho[2][N] of one box (rho^c = sum of the populations on fluid
  * nodes, 0 on solid nodes). */
 int lb_export_rho(lb_handle* h, int32_t box, double* rho);

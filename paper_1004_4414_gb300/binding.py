@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblbpart.so")
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_EPLACE, LB_ETIMEOUT, LB_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6, -7
 LB_FP64, LB_FP32, LB_FP16_DEV, LB_BF16_DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "fp16": LB_FP16_DEV, "bf16": LB_BF16_DEV}
+NATIVE_META = 8  # LB_NATIVE_META
 
 
 class LbParams(C.Structure):
@@ -78,7 +79,8 @@ DEFAULTS = dict(
 
 ABI_FUNCTIONS = (
     "lb_workspace_bytes", "lb_create", "lb_init_from_seed", "lb_init_fields", "lb_step", "lb_sync",
-    "lb_observables", "lb_export_state", "lb_import_state", "lb_export_rho", "lb_export_phi",
+    "lb_observables", "lb_export_state", "lb_import_state", "lb_state_native_bytes", "lb_export_state_native",
+    "lb_import_state_native", "lb_export_rho", "lb_export_phi",
     "lb_set_particle_colors",
     "lb_set_axes", "lb_get_axes",
     "lb_particle_forces", "lb_box_info", "lb_set_tiling", "lb_set_profiling", "lb_kernel_time", "lb_phase_times",
@@ -113,6 +115,9 @@ def load_library(path=LIB_PATH):
     L.lb_observables.argtypes = [vp, C.c_int32, C.POINTER(LbObs)]
     L.lb_export_state.argtypes = [vp, C.c_int32, dp, ip, dp, dp]
     L.lb_import_state.argtypes = [vp, C.c_int32, dp, ip, dp, dp]
+    L.lb_state_native_bytes.argtypes = [vp, C.c_int32, C.POINTER(C.c_size_t)]
+    L.lb_export_state_native.argtypes = [vp, C.c_int32, vp, C.c_size_t, ip, dp, dp]
+    L.lb_import_state_native.argtypes = [vp, C.c_int32, vp, C.c_size_t, ip, dp, dp]
     L.lb_export_rho.argtypes = [vp, C.c_int32, dp]
     L.lb_export_phi.argtypes = [vp, C.c_int32, dp, dp, dp]
     L.lb_set_particle_colors.argtypes = [vp, C.c_int32, dp]
@@ -316,6 +321,48 @@ class Simulation:
         meta = np.ascontiguousarray(st["meta"], np.float64)
         _ck(load_library().lb_import_state(self._h, box, _dp(f), _ip(owner), _dp(parts), _dp(meta)),
             "lb_import_state")
+
+    def native_bytes(self, box=0):
+        n = C.c_size_t(0)
+        _ck(load_library().lb_state_native_bytes(self._h, box, C.byref(n)), "lb_state_native_bytes")
+        return n.value
+
+    def export_state_native(self, box=0, state_out=None, owner_out=None):
+        """Storage-format state (lb_export_state_native): state is a uint8
+        array of native_bytes(box); state_out / owner_out: optional
+        C-contiguous uint8 / int32 arrays to fill (e.g. pinned host memory)."""
+        N, nb = self.n_nodes[box], self.native_bytes(box)
+        if state_out is not None:
+            if state_out.dtype != np.uint8 or state_out.size != nb or not state_out.flags.c_contiguous:
+                raise ValueError("state_out must be a C-contiguous uint8 array of native_bytes() bytes")
+            sa = state_out
+        else:
+            sa = np.zeros(nb, np.uint8)
+        if owner_out is not None:
+            if owner_out.dtype != np.int32 or owner_out.size != N or not owner_out.flags.c_contiguous:
+                raise ValueError("owner_out must be a C-contiguous int32 array of N values")
+            owner = owner_out
+        else:
+            owner = np.zeros(N, np.int32)
+        parts = np.zeros((max(self.n_particles[box], 1), 9))
+        meta = np.zeros(NATIVE_META)
+        _ck(load_library().lb_export_state_native(self._h, box, sa.ctypes.data_as(C.c_void_p), sa.size, _ip(owner),
+                                                  _dp(parts), _dp(meta)), "lb_export_state_native")
+        return dict(state=sa, owner=owner, particles=parts[: self.n_particles[box]], meta=meta)
+
+    def import_state_native(self, box, st):
+        sa = st["state"]
+        if sa.dtype != np.uint8 or not sa.flags.c_contiguous:
+            raise ValueError("state must be a C-contiguous uint8 array")
+        owner = np.ascontiguousarray(st["owner"], np.int32)
+        parts = np.ascontiguousarray(st["particles"], np.float64).reshape(-1, 9)
+        if parts.shape[0] == 0:
+            parts = np.zeros((1, 9))
+        meta = np.ascontiguousarray(st["meta"], np.float64)
+        if meta.size != NATIVE_META:
+            raise ValueError("meta must hold %d values" % NATIVE_META)
+        _ck(load_library().lb_import_state_native(self._h, box, sa.ctypes.data_as(C.c_void_p), sa.size, _ip(owner),
+                                                  _dp(parts), _dp(meta)), "lb_import_state_native")
 
     def rho(self, box=0):
         r = np.zeros((2, self.n_nodes[box]))

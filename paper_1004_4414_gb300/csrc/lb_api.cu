@@ -1075,9 +1075,13 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
     return LB_OK;
 }
 
-int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* owner, const double* particles,
-                    const double* meta) {
-    if (!h || box < 0 || box >= h->nb || !f || !owner || !meta) return LB_EINVAL;
+// The part of an import that both state formats share: the checks, the
+// owner map (validated and remapped on the device before anything of the
+// box changes), the particles, the node and shell flags.  The populations
+// and densities are left to the caller.  *t_out: the step of the state.
+static int import_begin(lb_handle* h, int32_t box, const int32_t* owner, const double* particles, const double* meta,
+                        int64_t* t_out) {
+    if (!owner || !meta) return LB_EINVAL;
     BoxDev& B = h->hbox[box];
     if (B.np > 0 && !particles) return LB_EINVAL;
     if ((int)meta[3] != B.np) return LB_EINVAL;
@@ -1140,6 +1144,19 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
     k_flags_from_owner<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, box);
     k_shell_all<<<SMALL_GRID * 4, 256, 0, st>>>(h->d_boxes, box);
     CK(cudaGetLastError());
+    *t_out = t;
+    return LB_OK;
+}
+
+int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* owner, const double* particles,
+                    const double* meta) {
+    if (!h || box < 0 || box >= h->nb || !f) return LB_EINVAL;
+    int64_t t = 0;
+    int rc0 = import_begin(h, box, owner, particles, meta, &t);
+    if (rc0 != LB_OK) return rc0;
+    BoxDev& B = h->hbox[box];
+    cudaStream_t st = h->stream;
+    const int N = B.N;
     const int par = (int)(t & 1), rcs = (int)(t % 3);
     // direction d (both components, 2N doubles) is copied into staging slot
     // d % 2 on xstream and converted on the handle's stream, so the copy of
@@ -1164,6 +1181,83 @@ int lb_import_state(lb_handle* h, int32_t box, const double* f, const int32_t* o
     CK(cudaMemsetAsync(h->mass_tmp, 0, 2 * sizeof(double), st));
     CK(h->ops->rho_from_pop(st, h->d_boxes, box, par, -1, rcs, nullptr, h->mass_tmp));
     CK(cudaMemcpyAsync(B.mass_acc + 2 * par, h->mass_tmp, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(h->sh.counters + 2 * box, 0, 2 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(h->sh.err, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    return after_init(h, t);
+}
+
+// Storage-format state of a box: the 18 stored population pairs of every
+// node as the device holds them (slots 1..18 for FP64 / FP32 storage, after
+// the rest slot that only an FP64-format import uses; the whole population
+// array in 16-bit storage), then the density field of the current step.
+static void native_layout(const lb_handle* h, const BoxDev& B, size_t* pop_off, size_t* pop_bytes,
+                          size_t* rho_bytes) {
+    const size_t N = (size_t)B.N, rs = h->ops->real_size;
+    const bool dev = h->ops->id >= 2;
+    *pop_off = dev ? 0 : 2 * N * rs;
+    *pop_bytes = dev ? 2 * 18 * N * sizeof(uint16_t) : 2 * 18 * N * rs;
+    *rho_bytes = 2 * N * rs;
+}
+
+int lb_state_native_bytes(lb_handle* h, int32_t box, size_t* bytes) {
+    if (!h || !bytes || box < 0 || box >= h->nb) return LB_EINVAL;
+    size_t po, pb, rb;
+    native_layout(h, h->hbox[box], &po, &pb, &rb);
+    *bytes = pb + rb;
+    return LB_OK;
+}
+
+int lb_export_state_native(lb_handle* h, int32_t box, void* state, size_t bytes, int32_t* owner, double* particles,
+                           double* meta) {
+    if (!h || box < 0 || box >= h->nb) return LB_EINVAL;
+    if (!h->initialised) return LB_EINVAL;
+    const BoxDev& B = h->hbox[box];
+    size_t po, pb, rb;
+    native_layout(h, B, &po, &pb, &rb);
+    if (state && bytes != pb + rb) return LB_EINVAL;
+    cudaStream_t st = h->stream;
+    if (state) {
+        CK(cudaMemcpyAsync(state, reinterpret_cast<const char*>(B.f) + po, pb, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(reinterpret_cast<char*>(state) + pb, B.rho[h->t % 3], rb, cudaMemcpyDeviceToHost, st));
+    }
+    double macc[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(macc, B.mass_acc + 2 * (h->t & 1), sizeof(macc), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int rc = lb_export_state(h, box, nullptr, owner, particles, nullptr);
+    if (rc != LB_OK) return rc;
+    if (meta) {
+        meta[0] = (double)h->t;
+        meta[1] = B.mass0[0];
+        meta[2] = B.mass0[1];
+        meta[3] = (double)B.np;
+        meta[4] = (double)h->ops->id;
+        meta[5] = (double)B.N;
+        meta[6] = macc[0];
+        meta[7] = macc[1];
+    }
+    return LB_OK;
+}
+
+int lb_import_state_native(lb_handle* h, int32_t box, const void* state, size_t bytes, const int32_t* owner,
+                           const double* particles, const double* meta) {
+    if (!h || box < 0 || box >= h->nb || !state || !meta) return LB_EINVAL;
+    BoxDev& B = h->hbox[box];
+    size_t po, pb, rb;
+    native_layout(h, B, &po, &pb, &rb);
+    if (bytes != pb + rb || (int)meta[4] != h->ops->id || (int64_t)meta[5] != (int64_t)B.N) return LB_EINVAL;
+    int64_t t = 0;
+    int rc0 = import_begin(h, box, owner, particles, meta, &t);
+    if (rc0 != LB_OK) return rc0;
+    cudaStream_t st = h->stream;
+    const int par = (int)(t & 1), rcs = (int)(t % 3);
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(B.f) + po, state, pb, cudaMemcpyHostToDevice, st));
+    // the ring slots of the next steps start zeroed (the fused kernel adds
+    // into the nodes at tile edges of the slot it fills)
+    for (int k = 0; k < 3; k++) CK(cudaMemsetAsync(B.rho[k], 0, rb, st));
+    CK(cudaMemcpyAsync(B.rho[rcs], reinterpret_cast<const char*>(state) + pb, rb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(B.evmark, 0, sizeof(int32_t) * B.N, st));
+    CK(cudaMemcpyAsync(B.mass_acc + 2 * par, meta + 6, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->sh.counters + 2 * box, 0, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(h->sh.err, 0, sizeof(int), st));
     CK(cudaStreamSynchronize(st));

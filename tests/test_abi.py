@@ -143,3 +143,17 @@ def test_contact_angle_mapping_default_is_nan():
     from paper_1004_4414_gb300 import binding
 
     assert math.isnan(binding.make_params().contact_angle_deg)
+
+
+def test_native_state_calls_reject_a_missing_handle(lib):
+    """The storage-format state calls check their arguments before any CUDA
+    call, and the binding's meta length is the header's LB_NATIVE_META."""
+    from paper_1004_4414_gb300 import binding
+
+    m = re.search(r"#define\s+LB_NATIVE_META\s+(\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == binding.NATIVE_META
+    n = C.c_size_t(0)
+    meta = (C.c_double * binding.NATIVE_META)()
+    assert lib.lb_state_native_bytes(None, 0, C.byref(n)) == binding.LB_EINVAL
+    assert lib.lb_export_state_native(None, 0, None, 0, None, None, meta) == binding.LB_EINVAL
+    assert lib.lb_import_state_native(None, 0, None, 0, None, None, meta) == binding.LB_EINVAL
