@@ -1049,11 +1049,17 @@ int lb_export_state(lb_handle* h, int32_t box, double* f, int32_t* owner, double
         CK(cudaStreamSynchronize(st));
     }
     if (owner) {
-        CK(cudaMemcpyAsync(owner, B.owner, sizeof(int32_t) * B.N, cudaMemcpyDeviceToHost, st));
+        // box-local particle indices, remapped on the device (staging
+        // scratch) for every box after the first
+        const int32_t* src = B.owner;
+        if (B.pstart != 0) {
+            int32_t* tmp = reinterpret_cast<int32_t*>(h->stage);
+            k_owner_export<<<SMALL_GRID * 4, 256, 0, st>>>(B.owner, tmp, B.N, B.pstart);
+            CK(cudaGetLastError());
+            src = tmp;
+        }
+        CK(cudaMemcpyAsync(owner, src, sizeof(int32_t) * B.N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (B.pstart != 0)
-            for (int n = 0; n < B.N; n++)
-                if (owner[n] >= 0) owner[n] -= B.pstart;
     }
     if (particles && B.np > 0) {
         std::vector<PartState> ps(B.np);

@@ -85,6 +85,14 @@ static __global__ void k_owner_import(const int32_t* __restrict__ in, int32_t* _
     if ((threadIdx.x & 31) == 0 && (bad | wall)) atomicOr(flags, bad | (wall << 1));
 }
 
+// box-local owner map for export: particle indices minus the box's first
+static __global__ void k_owner_export(const int32_t* __restrict__ in, int32_t* __restrict__ out, int N, int pstart) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const int o = in[n];
+        out[n] = o >= 0 ? o - pstart : o;
+    }
+}
+
 // owner map given by the caller (global particle indices already applied)
 static __global__ void k_flags_from_owner(const BoxDev* __restrict__ boxes, int b) {
     const BoxDev& B = boxes[b];

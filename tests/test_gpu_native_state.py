@@ -12,6 +12,8 @@ density field.  Checked here:
 - in FP32 storage, the continued run stays with the uninterrupted one to
   the FP32 parity tolerance (the two differ only in the summation order of
   the particle forces, since the import rebuilds the shell lists);
+- the same for the uneven boxes of one batched handle (box-local particle
+  indices in the owner map);
 - a byte count, storage type or node count that does not match, an owner
   entry out of range, and an export before any init are rejected, the
   first four before anything of the box changes.
@@ -152,3 +154,51 @@ def test_mismatches_rejected_without_changes():
     with pytest.raises(binding.LbError) as e:
         c.export_state_native()
     assert e.value.code == binding.LB_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp16"])
+def test_batched_boxes_roundtrip(precision):
+    """Uneven boxes of one handle: each box's storage-format state (with
+    box-local particle indices in the owner map) returns every byte through
+    a second handle at the shared step, and the continued batch follows the
+    FP64 oracle box by box."""
+    from paper_1004_4414_gb300 import Simulation
+
+    specs = [dict(nx=16, ny=16, nz=16, n_particles=2, radius=3.0, color=0.03),
+             dict(nx=24, ny=20, nz=12, n_particles=3, radius=2.5, color=-0.02, g_br=0.1),
+             dict(nx=12, ny=12, nz=20, n_particles=0)]
+    mk = lambda: Simulation([dict(sp, precision=precision, particle_density=2.0) for sp in specs])
+    a, b = mk(), mk()
+    oracles = []
+    for k, sp in enumerate(specs):
+        shape = (sp["nx"], sp["ny"], sp["nz"])
+        P = lbinputs.spheres(shape, sp.get("radius", 5.0), sp["n_particles"], seed=50 + k, min_gap=0.5,
+                             vmax=0.04, wmax=0.02) if sp["n_particles"] else None
+        rho = lbinputs.mixture(shape, amp=0.04, seed=60 + k)
+        o = ref.Oracle(**dict(sp, particle_density=2.0))
+        o.init_fields(rho, particles=P)
+        oracles.append(o)
+        a.init_fields(k, rho, particles=P)
+        b.init_fields(k, rho, particles=P)
+    a.step(5)
+    b.step(5)
+    states = [a.export_state_native(k) for k in range(len(specs))]
+    assert max(int(np.max(st["owner"])) for st in states) < 3  # box-local indices
+    for k, st in enumerate(states):
+        b.import_state_native(k, st)
+    for k, st in enumerate(states):
+        back = b.export_state_native(k)
+        assert np.array_equal(back["state"], st["state"])
+        assert np.array_equal(back["owner"], st["owner"])
+        assert np.array_equal(back["particles"], st["particles"])
+        assert np.array_equal(b.export_state(k)["owner"], a.export_state(k)["owner"])
+    if precision == "fp64":
+        for o in oracles:
+            o.step(15)
+        b.step(10)
+        for k, o in enumerate(oracles):
+            got, want = b.export_state(k), o.get_state()
+            assert np.array_equal(got["owner"], want["owner"])
+            assert np.max(np.abs(got["f"] - want["f"])) < 1e-11
+            if want["particles"].size:
+                assert np.max(np.abs(got["particles"] - want["particles"])) < 1e-11
