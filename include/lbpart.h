@@ -231,8 +231,9 @@ int lb_import_state_native(lb_handle* h, int32_t box, const void* state, size_t 
 int lb_export_rho(lb_handle* h, int32_t box, double* rho);
 
 /* Per-particle colour Delta rho of one box (host array of n_particles).
- * lb_init_from_seed, lb_init_fields and lb_import_state give every particle
- * the box colour, so call this after them. */
+ * lb_init_from_seed, lb_init_fields, lb_import_state and
+ * lb_import_state_native give every particle the box colour, so call this
+ * after them. */
 int lb_set_particle_colors(lb_handle* h, int32_t box, const double* colors);
 
 /* Body axes of the particles of one box, e[n_particles][3] unit vectors
