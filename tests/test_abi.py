@@ -1,7 +1,6 @@
 """CPU checks of the C ABI: the library loads, exports every function that
 include/lbpart.h declares, sizes workspaces and rejects invalid parameters
 without touching a GPU."""
-import ast
 import ctypes as C
 import math
 import os
@@ -159,19 +158,3 @@ def test_native_state_calls_reject_a_missing_handle(lib):
     assert lib.lb_export_state_native(None, 0, None, 0, None, None, meta) == binding.LB_EINVAL
     assert lib.lb_import_state_native(None, 0, None, 0, None, None, meta) == binding.LB_EINVAL
 
-
-def test_readme_example_parameters_are_accepted(lib):
-    """The quick-start box of README.md passes the library's parameter
-    checks and needs a workspace of the expected size (FP32 populations of
-    19 slots, three density buffers, node metadata)."""
-    from paper_1004_4414_gb300 import binding
-
-    src = open(os.path.join(ROOT, "README.md")).read()
-    m = re.search(r"Simulation\((dict\(.*?\))\)", src, flags=re.S)
-    assert m, "README example not found"
-    call = ast.parse(m.group(1), mode="eval").body
-    kw = {k.arg: ast.literal_eval(k.value) for k in call.keywords}
-    p = binding.make_params(**kw)
-    n = binding.workspace_bytes([p])
-    N = kw["nx"] * kw["ny"] * kw["nz"]
-    assert n >= (2 * 19 * 4 + 3 * 2 * 4 + 1 + 4 + 4) * N
