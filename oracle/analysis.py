@@ -30,7 +30,9 @@ def domain_size(phi):
         k2 = (k ** 2).reshape(shape)
         tot = S.sum()
         m2 = (k2 * S).sum() / tot
-        out.append(2.0 * np.pi / np.sqrt(m2))
+        # a field uniform along this axis has no spectrum there: L = inf
+        with np.errstate(divide="ignore"):
+            out.append(2.0 * np.pi / np.sqrt(m2))
     return tuple(out)
 
 
